@@ -1,0 +1,165 @@
+/* Monte Carlo integration driver of the oracle (test infrastructure; see oracle.h).
+ *
+ * Per item (event x jet permutation): n_adapt_iters VEGAS iterations of
+ * adapt_points points each refine the grid and are excluded from the estimate;
+ * the remaining points run on the frozen grid and give the plain MC mean
+ * S_N = mean(f) with error sqrt(sum (f - mean)^2 / (N - 1)) / sqrt(N) (Sec. 2,
+ * Eq. "sum" and the error estimate after it, read with the square root).
+ * Event result: average over permutations (Sec. 4 averages over jet
+ * assignments), errors added in quadrature. Points are counted over all
+ * iterations. Sums use Neumaier's compensated summation.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "oracle.h"
+
+typedef struct {
+  double s, c;
+} nsum_t;
+
+static void nadd(nsum_t* a, double x) {
+  double t = a->s + x;
+  if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+  else a->c += (x - t) + a->s;
+  a->s = t;
+}
+static double nval(const nsum_t* a) { return a->s + a->c; }
+
+void ora_eval_points(const ora_process* P, const ora_tf* T, const float* rec,
+                     uint64_t event_id, int perm, uint64_t seed, uint64_t point0, int64_t n,
+                     const double* grid, double* w_out) {
+  int d = ora_dims(P->kind);
+  double gbuf[ORA_MAXD * (ORA_NG + 1)];
+  if (!grid) {
+    ora_grid_uniform(d, gbuf);
+    grid = gbuf;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    double u[ORA_MAXD], x[ORA_MAXD];
+    ora_point_u(seed, event_id, perm, point0 + (uint64_t)i, d, u);
+    double J = ora_vegas_map(d, grid, u, x, NULL);
+    w_out[i] = ora_integrand(P, T, rec, perm, x) * J;
+  }
+}
+
+typedef struct {
+  const ora_process* P;
+  const ora_tf* T;
+  const float* recs;
+  int64_t n_items;
+  uint64_t seed, n_points;
+  const ora_opts* opt;
+  double* item_mean;
+  double* item_var;
+  double* grid_out;
+  int64_t next;
+  pthread_mutex_t lock;
+} job_t;
+
+static void run_item(job_t* J, int64_t item) {
+  const ora_process* P = J->P;
+  int d = ora_dims(P->kind), np = ora_nperm(P->kind);
+  int64_t ev = item / np;
+  int perm = (int)(item % np);
+  const float* rec = J->recs + ev * ORA_REC;
+  uint64_t eid = J->opt->event_id_base + (uint64_t)ev;
+  double grid[ORA_MAXD * (ORA_NG + 1)], grid2[ORA_MAXD * (ORA_NG + 1)];
+  if (J->opt->grid_in) memcpy(grid, J->opt->grid_in, sizeof(double) * d * (ORA_NG + 1));
+  else ora_grid_uniform(d, grid);
+  uint64_t n = J->n_points;
+  uint64_t na = J->opt->adapt_points;
+  if (na == 0) na = n / 8 < 16384 ? n / 8 : 16384;
+  int iters = J->opt->n_adapt_iters;
+  uint64_t idx = 0;
+  double* hist = (double*)malloc(sizeof(double) * d * ORA_NG);
+  for (int it = 0; it < iters; ++it) {
+    memset(hist, 0, sizeof(double) * d * ORA_NG);
+    for (uint64_t k = 0; k < na; ++k, ++idx) {
+      double u[ORA_MAXD], x[ORA_MAXD];
+      int bins[ORA_MAXD];
+      ora_point_u(J->seed, eid, perm, idx, d, u);
+      double jac = ora_vegas_map(d, grid, u, x, bins);
+      double w = ora_integrand(P, J->T, rec, perm, x) * jac;
+      for (int j = 0; j < d; ++j) hist[j * ORA_NG + bins[j]] += w * w;
+    }
+    ora_vegas_refine(d, hist, grid, J->opt->alpha, grid2);
+    memcpy(grid, grid2, sizeof(double) * d * (ORA_NG + 1));
+  }
+  free(hist);
+  uint64_t nm = n - idx;
+  nsum_t s1 = {0, 0}, s2 = {0, 0};
+  for (uint64_t k = 0; k < nm; ++k, ++idx) {
+    double u[ORA_MAXD], x[ORA_MAXD];
+    ora_point_u(J->seed, eid, perm, idx, d, u);
+    double jac = ora_vegas_map(d, grid, u, x, NULL);
+    double w = ora_integrand(P, J->T, rec, perm, x) * jac;
+    nadd(&s1, w);
+    nadd(&s2, w * w);
+  }
+  double mean = nval(&s1) / (double)nm;
+  double var = (nval(&s2) / (double)nm - mean * mean) / (double)(nm - 1);
+  if (var < 0.0) var = 0.0;
+  J->item_mean[item] = mean;
+  J->item_var[item] = var;
+  if (J->grid_out) memcpy(J->grid_out + item * d * (ORA_NG + 1), grid, sizeof(double) * d * (ORA_NG + 1));
+}
+
+static void* worker(void* arg) {
+  job_t* J = (job_t*)arg;
+  for (;;) {
+    pthread_mutex_lock(&J->lock);
+    int64_t item = J->next++;
+    pthread_mutex_unlock(&J->lock);
+    if (item >= J->n_items) break;
+    run_item(J, item);
+  }
+  return NULL;
+}
+
+int ora_integrate(const ora_process* P, const ora_tf* T, const float* recs, int64_t n_events,
+                  uint64_t seed, uint64_t n_points, const ora_opts* opt, double* prob,
+                  double* err, uint64_t* n_used, double* item_mean, double* item_err,
+                  double* grid_out) {
+  int np = ora_nperm(P->kind);
+  int64_t n_items = n_events * np;
+  uint64_t na = opt->adapt_points ? opt->adapt_points : (n_points / 8 < 16384 ? n_points / 8 : 16384);
+  if (n_points < (uint64_t)opt->n_adapt_iters * na + 2) return 1;
+  job_t J;
+  J.P = P;
+  J.T = T;
+  J.recs = recs;
+  J.n_items = n_items;
+  J.seed = seed;
+  J.n_points = n_points;
+  J.opt = opt;
+  J.item_mean = (double*)malloc(sizeof(double) * n_items);
+  J.item_var = (double*)malloc(sizeof(double) * n_items);
+  J.grid_out = grid_out;
+  J.next = 0;
+  pthread_mutex_init(&J.lock, NULL);
+  int nt = opt->n_threads > 0 ? opt->n_threads : 1;
+  pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * nt);
+  for (int t = 0; t < nt; ++t) pthread_create(&th[t], NULL, worker, &J);
+  for (int t = 0; t < nt; ++t) pthread_join(th[t], NULL);
+  free(th);
+  pthread_mutex_destroy(&J.lock);
+  for (int64_t e = 0; e < n_events; ++e) {
+    nsum_t m = {0, 0}, v = {0, 0};
+    for (int p = 0; p < np; ++p) {
+      nadd(&m, J.item_mean[e * np + p]);
+      nadd(&v, J.item_var[e * np + p]);
+    }
+    prob[e] = nval(&m) / np;
+    err[e] = sqrt(nval(&v)) / np;
+    if (n_used) n_used[e] = n_points * (uint64_t)np;
+  }
+  if (item_mean) memcpy(item_mean, J.item_mean, sizeof(double) * n_items);
+  if (item_err)
+    for (int64_t i = 0; i < n_items; ++i) item_err[i] = sqrt(J.item_var[i]);
+  free(J.item_mean);
+  free(J.item_var);
+  return 0;
+}

@@ -1,0 +1,391 @@
+/* Physics map, Jacobians, PDFs and transfer functions of the oracle
+ * (test infrastructure; see oracle.h). Direct FP64 restatement:
+ *
+ * - MEM density (Sec. 1, Eq. "mem_def"): sum over flavours of |M|^2 f1 f2/(|q1||q2|)
+ *   times the n-body phase-space element (Sec. 1, phase-space equation); the
+ *   momentum-conserving delta consumes dx1 dx2 through E and p_z (Jacobian 2/s);
+ *   the transverse imbalance is removed by a transverse boost of the final state.
+ * - Transfer-function convolution (Sec. 1): delta functions in all directions and
+ *   in the ttbar lepton energy, Gaussian lepton energies, double-Gaussian jet
+ *   energies, and a Gaussian on the missing transverse momentum for the neutrino.
+ * - Jets and energy-integrated leptons carry E^2 sin(theta) dE (Sec. 3, after
+ *   Eq. "integrand"), with E = |p| (massless).
+ * - Propagator virtualities as integration variables (Sec. 3, the paragraph before
+ *   Eq. "dilepsolv"): Breit-Wigner arctan maps for W and top masses; the neutrino
+ *   p_z follows from the W mass constraint (both quadratic roots summed).
+ */
+#include <math.h>
+#include <string.h>
+
+#include "oracle.h"
+#include "ora_dirac.h"
+
+int ora_dims(int kind) { return kind == 0 ? 2 : kind == 1 ? 4 : 7; }
+int ora_nperm(int kind) { return kind == 2 ? 24 : 1; }
+
+double ora_pdf(const ora_process* P, int type, double x) {
+  if (!(x > 0.0 && x < 1.0)) return 0.0;
+  return P->pdf_A[type] * pow(x, P->pdf_a[type]) * pow(1.0 - x, P->pdf_b[type]);
+}
+
+static double gauss(double x, double mu, double sig) {
+  double z = (x - mu) / sig;
+  return exp(-0.5 * z * z) / (sqrt(2.0 * M_PI) * sig);
+}
+
+/* Double-Gaussian jet response: (1-w) N(x; E, c E) + w N(x; E, t E). */
+static double dgauss(const ora_tf* T, double x, double E) {
+  return (1.0 - T->jet_tail_w) * gauss(x, E, T->jet_core * E) +
+         T->jet_tail_w * gauss(x, E, T->jet_tail * E);
+}
+
+typedef struct {
+  double E, eta, phi, kind;
+  double n[3];
+  double sin_theta;
+} obj_t;
+
+static obj_t get_obj(const float* rec, int o) {
+  obj_t a;
+  a.E = rec[4 * o + 0];
+  a.eta = rec[4 * o + 1];
+  a.phi = rec[4 * o + 2];
+  a.kind = rec[4 * o + 3];
+  double ch = cosh(a.eta);
+  a.n[0] = cos(a.phi) / ch;
+  a.n[1] = sin(a.phi) / ch;
+  a.n[2] = tanh(a.eta);
+  a.sin_theta = 1.0 / ch;
+  return a;
+}
+
+static rv4 massless(double E, const double* n) { return rv(E, E * n[0], E * n[1], E * n[2]); }
+
+/* Breit-Wigner map of v in [0,1] onto q^2 in [lo, hi]:
+ * q^2 = m^2 + m w tan(th), th uniform between atan((lo-m^2)/(m w)) and
+ * atan((hi-m^2)/(m w)). Returns q^2, writes dq^2/dv. */
+static double bw_map(double lo, double hi, double m, double w, double v, double* jac) {
+  double tlo = atan((lo - m * m) / (m * w));
+  double thi = atan((hi - m * m) / (m * w));
+  double th = tlo + (thi - tlo) * v;
+  double c = cos(th);
+  *jac = (thi - tlo) * m * w / (c * c);
+  return m * m + m * w * tan(th);
+}
+
+/* General Lorentz boost into the frame moving with velocity b. */
+static rv4 boost(rv4 p, double bx, double by, double bz) {
+  double b2 = bx * bx + by * by + bz * bz;
+  if (b2 == 0.0) return p;
+  double g = 1.0 / sqrt(1.0 - b2);
+  double bp = bx * p.v[1] + by * p.v[2] + bz * p.v[3];
+  double c = (g - 1.0) * bp / b2 - g * p.v[0];
+  return rv(g * (p.v[0] - bp), p.v[1] + c * bx, p.v[2] + c * by, p.v[3] + c * bz);
+}
+
+/* Neutrino p_z from q^2 = (p_l + p_nu)^2 with massless lepton and neutrino and
+ * known neutrino p_T. Squaring E_l E_nu - p_l.p_nu = q^2/2 gives
+ *   pT_l^2 pz^2 - 2 a pz_l pz + (E_l^2 pT_nu^2 - a^2) = 0,  a = q^2/2 + pT_l.pT_nu.
+ * Roots by the quadratic formula; jac = 1 / |d q^2 / d pz| with
+ * d q^2/d pz = 2 (E_l pz / E_nu - pz_l). Roots that fail the unsquared
+ * equation are dropped. */
+static int nu_roots(rv4 pl, double nx, double ny, double q2, double* pz, double* jac) {
+  double pTl2 = pl.v[1] * pl.v[1] + pl.v[2] * pl.v[2];
+  double pTn2 = nx * nx + ny * ny;
+  double a = 0.5 * q2 + pl.v[1] * nx + pl.v[2] * ny;
+  double A = pTl2, B = -2.0 * a * pl.v[3], C = pl.v[0] * pl.v[0] * pTn2 - a * a;
+  double disc = B * B - 4.0 * A * C;
+  if (disc < 0.0 || A <= 0.0) return 0;
+  double sq = sqrt(disc);
+  double cand[2] = {(-B + sq) / (2.0 * A), (-B - sq) / (2.0 * A)};
+  int n = 0;
+  for (int r = 0; r < 2; ++r) {
+    double En = sqrt(pTn2 + cand[r] * cand[r]);
+    double q2r = 2.0 * (pl.v[0] * En - pl.v[1] * nx - pl.v[2] * ny - pl.v[3] * cand[r]);
+    if (fabs(q2r - q2) > 1e-6 * (fabs(q2) + 1.0)) continue;
+    double d = 2.0 * (pl.v[0] * cand[r] / En - pl.v[3]);
+    pz[n] = cand[r];
+    jac[n] = 1.0 / fabs(d);
+    ++n;
+  }
+  return n;
+}
+
+typedef struct {
+  int nfs;
+  rv4 lab[6];
+  double jac;   /* product of the physics-map Jacobians */
+  double meas;  /* prod 1/((2pi)^3 2E) and E^2 sin(theta) measure factors */
+  double tf;    /* product of transfer functions */
+  double aux[8];
+} state_t;
+
+static const double TWO_PI = 2.0 * M_PI;
+static double inv_ps(double E) { return 1.0 / (pow(TWO_PI, 3) * 2.0 * E); }
+
+/* Lepton energy with a Gaussian TF: log-uniform over the +- k sigma window
+ * [Em/(1+k r), Em/(1-k r)]. */
+static double lepton_energy(const ora_tf* T, double Em, double x, double* jac) {
+  double r = T->lep_rel, k = T->window_k;
+  double lo = Em / (1.0 + k * r), hi = Em / (1.0 - k * r);
+  double L = log(hi / lo);
+  double E = lo * exp(x * L);
+  *jac = E * L;
+  return E;
+}
+
+static void jet_window(const ora_process* P, const ora_tf* T, double Em, double* lo,
+                       double* hi) {
+  *lo = Em / T->jet_lo_div;
+  *hi = fmin(Em * T->jet_hi_mul, 0.5 * P->sqrt_s);
+}
+
+static void met_box(const ora_tf* T, const float* rec, double x1, double x2, double* nx,
+                    double* ny, double* jac, double* tf) {
+  double B = T->met_box_k * T->met_sigma;
+  *nx = rec[24] + B * (2.0 * x1 - 1.0);
+  *ny = rec[25] + B * (2.0 * x2 - 1.0);
+  *jac = (2.0 * B) * (2.0 * B);
+  *tf = gauss(rec[24], *nx, T->met_sigma) * gauss(rec[25], *ny, T->met_sigma);
+}
+
+/* Squared transverse mass of a massless lepton and a neutrino of given pT. */
+static double mt2(rv4 pl, double nx, double ny) {
+  double pTl = hypot(pl.v[1], pl.v[2]), pTn = hypot(nx, ny);
+  return 2.0 * (pTl * pTn - pl.v[1] * nx - pl.v[2] * ny);
+}
+
+static int states_dy(const ora_process* P, const ora_tf* T, const float* rec,
+                     const double* x, state_t* st) {
+  obj_t o[2] = {get_obj(rec, 0), get_obj(rec, 1)}; /* mu-, mu+ */
+  st->nfs = 2;
+  st->jac = 1.0;
+  st->meas = 1.0;
+  st->tf = 1.0;
+  for (int i = 0; i < 2; ++i) {
+    double J;
+    double E = lepton_energy(T, o[i].E, x[i], &J);
+    st->jac *= J;
+    st->lab[i] = massless(E, o[i].n);
+    st->meas *= E * E * o[i].sin_theta * inv_ps(E);
+    st->tf *= gauss(o[i].E, E, T->lep_rel * E);
+    st->aux[i] = E;
+  }
+  return 1;
+}
+
+static int states_w(const ora_process* P, const ora_tf* T, const float* rec, const double* x,
+                    state_t* st) {
+  obj_t e = get_obj(rec, 0);
+  double Je;
+  double Ee = lepton_energy(T, e.E, x[0], &Je);
+  rv4 pe = massless(Ee, e.n);
+  double nx, ny, Jbox, tfm;
+  met_box(T, rec, x[1], x[2], &nx, &ny, &Jbox, &tfm);
+  double s = P->sqrt_s * P->sqrt_s;
+  double lo = mt2(pe, nx, ny), hi = s;
+  if (!(lo < hi)) return 0;
+  double t = x[3], dq2;
+  double q2 = bw_map(lo, hi, P->mw, P->ww, t * t, &dq2);
+  double Jq = dq2 * 2.0 * t;
+  double pz[2], jpz[2];
+  int n = nu_roots(pe, nx, ny, q2, pz, jpz);
+  for (int r = 0; r < n; ++r) {
+    double En = sqrt(nx * nx + ny * ny + pz[r] * pz[r]);
+    state_t* S = &st[r];
+    S->nfs = 2;
+    S->lab[0] = pe;
+    S->lab[1] = rv(En, nx, ny, pz[r]);
+    S->jac = Je * Jbox * Jq * jpz[r];
+    S->meas = Ee * Ee * e.sin_theta * inv_ps(Ee) * inv_ps(En);
+    S->tf = gauss(e.E, Ee, T->lep_rel * Ee) * tfm;
+    rv4 w = rv_add(S->lab[0], S->lab[1]);
+    S->aux[0] = q2;
+    S->aux[1] = rv_dot(w, w);
+    S->aux[2] = Ee;
+    S->aux[3] = pz[r];
+  }
+  return n;
+}
+
+static int states_tt(const ora_process* P, const ora_tf* T, const float* rec, int perm,
+                     const double* x, state_t* st) {
+  static const int perms[24][4] = {
+      {0, 1, 2, 3}, {0, 1, 3, 2}, {0, 2, 1, 3}, {0, 2, 3, 1}, {0, 3, 1, 2}, {0, 3, 2, 1},
+      {1, 0, 2, 3}, {1, 0, 3, 2}, {1, 2, 0, 3}, {1, 2, 3, 0}, {1, 3, 0, 2}, {1, 3, 2, 0},
+      {2, 0, 1, 3}, {2, 0, 3, 1}, {2, 1, 0, 3}, {2, 1, 3, 0}, {2, 3, 0, 1}, {2, 3, 1, 0},
+      {3, 0, 1, 2}, {3, 0, 2, 1}, {3, 1, 0, 2}, {3, 1, 2, 0}, {3, 2, 0, 1}, {3, 2, 1, 0}};
+  obj_t lep = get_obj(rec, 0);
+  obj_t jb = get_obj(rec, 1 + perms[perm][0]);
+  obj_t jbb = get_obj(rec, 1 + perms[perm][1]);
+  obj_t jd = get_obj(rec, 1 + perms[perm][2]);
+  obj_t ju = get_obj(rec, 1 + perms[perm][3]);
+  double s = P->sqrt_s * P->sqrt_s;
+  double lo, hi, dq2;
+  /* d-quark energy: log-uniform over its jet window */
+  jet_window(P, T, jd.E, &lo, &hi);
+  double L = log(hi / lo);
+  double Ed = lo * exp(x[0] * L);
+  double J0 = Ed * L;
+  rv4 pd = massless(Ed, jd.n);
+  /* hadronic W mass -> ubar energy, q^2 range from the ubar jet window */
+  double omc = 1.0 - (jd.n[0] * ju.n[0] + jd.n[1] * ju.n[1] + jd.n[2] * ju.n[2]);
+  jet_window(P, T, ju.E, &lo, &hi);
+  double q2wh = bw_map(2.0 * Ed * lo * omc, 2.0 * Ed * hi * omc, P->mw, P->ww, x[1], &dq2);
+  double Eu = q2wh / (2.0 * Ed * omc);
+  double J1 = dq2 / (2.0 * Ed * omc);
+  rv4 pu = massless(Eu, ju.n);
+  rv4 pwh = rv_add(pd, pu);
+  /* antitop mass -> bbar energy */
+  double K = pwh.v[0] - (jbb.n[0] * pwh.v[1] + jbb.n[1] * pwh.v[2] + jbb.n[2] * pwh.v[3]);
+  jet_window(P, T, jbb.E, &lo, &hi);
+  double q2tb = bw_map(q2wh + 2.0 * lo * K, q2wh + 2.0 * hi * K, P->mt, P->wt, x[2], &dq2);
+  double Ebb = (q2tb - q2wh) / (2.0 * K);
+  double J2 = dq2 / (2.0 * K);
+  rv4 pbb = massless(Ebb, jbb.n);
+  /* neutrino transverse momentum */
+  double nx, ny, Jbox, tfm;
+  met_box(T, rec, x[3], x[4], &nx, &ny, &Jbox, &tfm);
+  /* leptonic W mass -> neutrino pz (two roots) */
+  rv4 pl = massless(lep.E, lep.n);
+  double wlo = mt2(pl, nx, ny);
+  if (!(wlo < s)) return 0;
+  double t = x[5];
+  double q2wl = bw_map(wlo, s, P->mw, P->ww, t * t, &dq2);
+  double J5 = dq2 * 2.0 * t;
+  double pz[2], jpz[2];
+  int n = nu_roots(pl, nx, ny, q2wl, pz, jpz);
+  for (int r = 0; r < n; ++r) {
+    state_t* S = &st[r];
+    double En = sqrt(nx * nx + ny * ny + pz[r] * pz[r]);
+    rv4 pn = rv(En, nx, ny, pz[r]);
+    rv4 pwl = rv_add(pl, pn);
+    /* top mass -> b energy */
+    double Kb = pwl.v[0] - (jb.n[0] * pwl.v[1] + jb.n[1] * pwl.v[2] + jb.n[2] * pwl.v[3]);
+    jet_window(P, T, jb.E, &lo, &hi);
+    double q2t = bw_map(q2wl + 2.0 * lo * Kb, q2wl + 2.0 * hi * Kb, P->mt, P->wt, x[6], &dq2);
+    double Eb = (q2t - q2wl) / (2.0 * Kb);
+    double J6 = dq2 / (2.0 * Kb);
+    rv4 pb = massless(Eb, jb.n);
+    S->nfs = 6;
+    S->lab[0] = pb;
+    S->lab[1] = pl;
+    S->lab[2] = pn;
+    S->lab[3] = pbb;
+    S->lab[4] = pd;
+    S->lab[5] = pu;
+    S->jac = J0 * J1 * J2 * Jbox * J5 * jpz[r] * J6;
+    double Ej[4] = {Eb, Ebb, Ed, Eu};
+    const obj_t* oj[4] = {&jb, &jbb, &jd, &ju};
+    S->meas = inv_ps(pl.v[0]) * inv_ps(En);
+    S->tf = tfm;
+    for (int k = 0; k < 4; ++k) {
+      S->meas *= Ej[k] * Ej[k] * oj[k]->sin_theta * inv_ps(Ej[k]);
+      S->tf *= dgauss(T, oj[k]->E, Ej[k]);
+    }
+    S->aux[0] = q2wh;
+    S->aux[1] = q2tb;
+    S->aux[2] = q2wl;
+    S->aux[3] = q2t;
+  }
+  return n;
+}
+
+static int build_states(const ora_process* P, const ora_tf* T, const float* rec, int perm,
+                        const double* x, state_t* st) {
+  memset(st, 0, 2 * sizeof(state_t));
+  switch (P->kind) {
+    case 0: return states_dy(P, T, rec, x, st);
+    case 1: return states_w(P, T, rec, x, st);
+    case 2: return states_tt(P, T, rec, perm, x, st);
+  }
+  return 0;
+}
+
+/* Transverse boost of the final state to zero total pT, parton momenta and
+ * momentum fractions x1 = (E + pz)/sqrt(s), x2 = (E - pz)/sqrt(s). */
+static void to_parton_frame(const ora_process* P, const state_t* S, rv4* boo, rv4* k1, rv4* k2,
+                            double* x1, double* x2) {
+  rv4 tot = rv(0, 0, 0, 0);
+  for (int i = 0; i < S->nfs; ++i) tot = rv_add(tot, S->lab[i]);
+  double bx = tot.v[1] / tot.v[0], by = tot.v[2] / tot.v[0];
+  for (int i = 0; i < S->nfs; ++i) boo[i] = boost(S->lab[i], bx, by, 0.0);
+  rv4 T = boost(tot, bx, by, 0.0);
+  double rs = P->sqrt_s;
+  *x1 = (T.v[0] + T.v[3]) / rs;
+  *x2 = (T.v[0] - T.v[3]) / rs;
+  *k1 = rv(0.5 * *x1 * rs, 0, 0, 0.5 * *x1 * rs);
+  *k2 = rv(0.5 * *x2 * rs, 0, 0, -0.5 * *x2 * rs);
+}
+
+/* PDF-weighted, flavour- and orientation-summed |M|^2 (Eq. "mem_def"). */
+static double flavour_sum(const ora_process* P, const rv4* b, rv4 k1, rv4 k2, double x1,
+                          double x2, const float* rec) {
+  double fq1 = ora_pdf(P, 0, x1), fqb1 = ora_pdf(P, 1, x1), fg1 = ora_pdf(P, 2, x1);
+  double fq2 = ora_pdf(P, 0, x2), fqb2 = ora_pdf(P, 1, x2), fg2 = ora_pdf(P, 2, x2);
+  double sum = 0.0;
+  if (P->kind == 0) {
+    for (int fl = 0; fl < 2; ++fl) {
+      sum += fq1 * fqb2 * ora_msq_dy(P, fl, k1.v, k2.v, b[0].v, b[1].v);
+      sum += fqb1 * fq2 * ora_msq_dy(P, fl, k2.v, k1.v, b[0].v, b[1].v);
+    }
+  } else if (P->kind == 1) {
+    int charge = rec[3] == 4.0f ? +1 : -1;
+    sum += fq1 * fqb2 * ora_msq_w(P, charge, k1.v, k2.v, b[0].v, b[1].v);
+    sum += fqb1 * fq2 * ora_msq_w(P, charge, k2.v, k1.v, b[0].v, b[1].v);
+  } else {
+    sum += fg1 * fg2 *
+           ora_msq_ttbar(P, 0, k1.v, k2.v, b[0].v, b[1].v, b[2].v, b[3].v, b[4].v, b[5].v);
+    for (int fl = 0; fl < 2; ++fl) { /* u ubar and d dbar */
+      sum += fq1 * fqb2 *
+             ora_msq_ttbar(P, 1, k1.v, k2.v, b[0].v, b[1].v, b[2].v, b[3].v, b[4].v, b[5].v);
+      sum += fqb1 * fq2 *
+             ora_msq_ttbar(P, 1, k2.v, k1.v, b[0].v, b[1].v, b[2].v, b[3].v, b[4].v, b[5].v);
+    }
+  }
+  return sum;
+}
+
+double ora_integrand(const ora_process* P, const ora_tf* T, const float* rec, int perm,
+                     const double* x) {
+  state_t st[2];
+  int n = build_states(P, T, rec, perm, x, st);
+  double s = P->sqrt_s * P->sqrt_s;
+  double total = 0.0;
+  for (int r = 0; r < n; ++r) {
+    rv4 b[6], k1, k2;
+    double x1, x2;
+    to_parton_frame(P, &st[r], b, &k1, &k2, &x1, &x2);
+    if (!(x1 > 0.0 && x1 < 1.0 && x2 > 0.0 && x2 < 1.0)) continue;
+    double msq = flavour_sum(P, b, k1, k2, x1, x2, rec);
+    double flux = 1.0 / (k1.v[0] * k2.v[0]); /* 1/(|q1||q2|) */
+    total += msq * flux * pow(TWO_PI, 4) * (2.0 / s) * st[r].meas * st[r].tf * st[r].jac;
+  }
+  return total;
+}
+
+int ora_kinematics(const ora_process* P, const ora_tf* T, const float* rec, int perm,
+                   const double* x, int root, double* fs, double* fs_lab, double* k12,
+                   double* aux) {
+  state_t st[2];
+  int n = build_states(P, T, rec, perm, x, st);
+  if (root >= n) return n;
+  rv4 b[6], k1, k2;
+  double x1, x2;
+  to_parton_frame(P, &st[root], b, &k1, &k2, &x1, &x2);
+  for (int i = 0; i < st[root].nfs; ++i)
+    for (int m = 0; m < 4; ++m) {
+      fs[4 * i + m] = b[i].v[m];
+      fs_lab[4 * i + m] = st[root].lab[i].v[m];
+    }
+  for (int m = 0; m < 4; ++m) {
+    k12[m] = k1.v[m];
+    k12[4 + m] = k2.v[m];
+  }
+  for (int i = 0; i < 4; ++i) aux[i] = st[root].aux[i];
+  aux[4] = x1;
+  aux[5] = x2;
+  aux[6] = st[root].jac;
+  aux[7] = st[root].tf;
+  return n;
+}

@@ -1,0 +1,139 @@
+/* FP64 CPU oracle for the matrix-element-method integral.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load or call this library.
+ * The product path (the CUDA library) never routes through it, and the two
+ * share no code, headers or tables.
+ *
+ * What it computes (Sec. 1, Eq. "mem_def", the transfer-function convolution
+ * for p_hat, and Eq. "integrand" of Sec. 3): for each event X and jet
+ * permutation,
+ *   p_hat(X) = (1/N_perm) sum_perm  int du  sum_roots F(Y(u)) J(u)
+ * with F = sum_flavour f_a(x1) f_b(x2) |M|^2 / (|q1||q2|) * (2pi)^4 (2/s)
+ *          * prod_i 1/((2pi)^3 2E_i) * prod_{energy-integrated i} E_i^2 sin(theta_i)
+ *          * prod T(X|Y)
+ * and the plain Monte Carlo estimator with its standard error (Sec. 2,
+ * Eq. "sum" and the error formula that follows it), on a VEGAS-adapted map
+ * (Sec. 2, Lepage's algorithm).
+ *
+ * Everything is written in the most direct form: 4x4 complex Dirac matrices,
+ * explicit spinor sums, textbook quadratic roots, explicit Lorentz boosts.
+ */
+#ifndef MEM_ORACLE_H
+#define MEM_ORACLE_H
+#include <stdint.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int32_t kind; /* 0 Drell-Yan, 1 W -> e nu, 2 semileptonic ttbar */
+  int32_t pad;
+  double sqrt_s;
+  double mz, wz, mw, ww, mt, wt;
+  double alpha, sw2, alpha_s;
+  double pdf_A[3], pdf_a[3], pdf_b[3]; /* quark, antiquark, gluon */
+} ora_process;
+
+typedef struct {
+  double lep_rel;     /* Gaussian sigma/E for lepton energies */
+  double window_k;    /* single-Gaussian integration window: +- k sigma */
+  double jet_core;    /* double Gaussian: core sigma/E */
+  double jet_tail;    /* tail sigma/E */
+  double jet_tail_w;  /* tail weight */
+  double jet_lo_div;  /* jet window [E/lo_div, min(E*hi_mul, sqrt_s/2)] */
+  double jet_hi_mul;
+  double met_sigma;   /* MET Gaussian sigma per component */
+  double met_box_k;   /* neutrino px,py box: MET +- k sigma */
+} ora_tf;
+
+#define ORA_NG 128      /* VEGAS bins per dimension */
+#define ORA_MAXD 8
+#define ORA_REC 32
+
+int ora_dims(int kind);
+int ora_nperm(int kind);
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */
+void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* Uniform in (0,1) from a 32-bit word: ((x >> 8) + 0.5) * 2^-24. */
+double ora_u01(uint32_t x);
+/* Unit-cube point for (event_id, perm, point index) from the integration stream. */
+void ora_point_u(uint64_t seed, uint64_t event_id, int perm, uint64_t idx, int d, double* u);
+
+/* Integrand on the unit cube (physics map + Jacobians, no VEGAS map). */
+double ora_integrand(const ora_process* P, const ora_tf* T, const float* rec, int perm,
+                     const double* x);
+
+/* Kinematics at one point for tests: writes boosted momenta of the final
+ * state (n_fs x 4, in the process's particle order) and the partons k1, k2.
+ * fs_lab receives the same momenta before the boost (lab frame).
+ * Returns the number of root branches (0 if the point has no solution).
+ * `root` picks the branch. Extra diagnostics in aux (process dependent). */
+int ora_kinematics(const ora_process* P, const ora_tf* T, const float* rec, int perm,
+                   const double* x, int root, double* fs, double* fs_lab, double* k12,
+                   double* aux);
+
+/* Spin/colour averaged |M|^2 at given momenta (4-vectors E,px,py,pz). */
+double ora_msq_dy(const ora_process* P, int flavour /*0 u, 1 d*/, const double* kq,
+                  const double* kqb, const double* pl_minus, const double* pl_plus);
+double ora_msq_w(const ora_process* P, int charge, const double* kq, const double* kqb,
+                 const double* pl, const double* pn);
+/* channel 0: g(k1) g(k2); channel 1: q(k1) qbar(k2). Final state b l+ nu bbar d ubar. */
+double ora_msq_ttbar(const ora_process* P, int channel, const double* k1, const double* k2,
+                     const double* pb, const double* pl, const double* pn, const double* pbb,
+                     const double* pd, const double* pu);
+/* Production only, on-shell tops, summed over top spins (for closed-form pins). */
+double ora_msq_ttbar_production(const ora_process* P, int channel, const double* k1,
+                                const double* k2, const double* pt, const double* ptb);
+/* Gauge check: |A1|^2+|A2|^2 for on-shell tops, with gluon `which` polarisation
+ * replaced by its momentum and the other gluon of helicity index `hel`. */
+double ora_ttbar_gauge_probe(const ora_process* P, const double* k1, const double* k2,
+                             const double* pt, const double* ptb, int which, int hel);
+/* Decay-chain pins. Top at rest (p_t = (m,0,0,0)): for basis spin s (0 up, 1 down
+ * along z), out[s] = sum over b, nu, l spins of |row . u_t(s)|^2 where row is the
+ * top-side row spinor used by ora_msq_ttbar. Antitop similarly with v_tbar(s). */
+void ora_top_decay_probe(const ora_process* P, const double* pb, const double* pl,
+                         const double* pn, double* out2);
+void ora_antitop_decay_probe(const ora_process* P, const double* pbb, const double* pd,
+                             const double* pu, double* out2);
+
+/* Parametric PDF f(x) = A x^a (1-x)^b, zero outside (0,1). type 0 q, 1 qbar, 2 g. */
+double ora_pdf(const ora_process* P, int type, double x);
+
+/* VEGAS */
+void ora_grid_uniform(int d, double* grid /* d x (NG+1) */);
+double ora_vegas_map(int d, const double* grid, const double* u, double* x, int* bins);
+void ora_vegas_refine(int d, const double* hist /* d x NG */, const double* grid_in,
+                      double alpha, double* grid_out);
+
+/* Weights at consecutive points (with grid; NULL grid = uniform). */
+void ora_eval_points(const ora_process* P, const ora_tf* T, const float* rec,
+                     uint64_t event_id, int perm, uint64_t seed, uint64_t point0, int64_t n,
+                     const double* grid, double* w_out);
+
+typedef struct {
+  int32_t n_adapt_iters;   /* VEGAS adaptation iterations (excluded from the estimate) */
+  int32_t n_threads;       /* worker threads over items */
+  uint64_t adapt_points;   /* points per adaptation iteration; 0 = min(2^14, n/8) */
+  double alpha;            /* grid compression exponent */
+  const double* grid_in;   /* optional starting grid shared by all items (d x (NG+1)) */
+  uint64_t event_id_base;  /* id of event 0 in the Philox counter */
+} ora_opts;
+
+/* Integrate n_events records with n_points per item (item = event x perm).
+ * prob/err per event; item_mean/item_err/grid_out optional (per item). */
+int ora_integrate(const ora_process* P, const ora_tf* T, const float* recs, int64_t n_events,
+                  uint64_t seed, uint64_t n_points, const ora_opts* opt, double* prob,
+                  double* err, uint64_t* n_used, double* item_mean, double* item_err,
+                  double* grid_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

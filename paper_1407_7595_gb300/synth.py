@@ -1,0 +1,266 @@
+"""Seeded synthetic inputs: event records and default parameter sets.
+
+This module is input data only. It holds none of the integrand's arithmetic
+(no maps, matrix elements, PDFs, transfer functions or VEGAS); both the CUDA
+path and the FP64 oracle consume what it produces, and neither is imported here.
+
+The paper evaluates the matrix element method on MadGraph+Pythia samples of
+ttH(bb) and ttbb (Sec. 3, Sec. 4); those samples are not available, so seeded
+generators of the same kind of final states stand in for them: resonant
+Drell-Yan and W events and semileptonic ttbar events with double-Gaussian
+jet-energy smearing (the transfer-function form of Sec. 1 and Fig. "tf_jet").
+
+Event record: 32 float32 values per event.
+  [4*o + 0..3] for object o = 0..5 : (E_measured [GeV], eta, phi, kind)
+  [24], [25]                        : missing transverse momentum (x, y) [GeV]
+  [26]                              : number of objects
+  [27]                              : process kind (0 DY, 1 W, 2 ttbar)
+  [28]                              : generator truth, ttbar only: index of the
+                                      jet permutation that matches the partons
+                                      (diagnostic only, never read by the method)
+  [29..31]                          : zero
+Object kinds: 1 mu-, 2 mu+, 3 e-, 4 e+, 5 jet.
+Object order: DY (mu-, mu+); W (charged lepton); ttbar (l+, 4 jets by
+decreasing measured energy).
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+
+RECORD_FLOATS = 32
+KIND_NONE, KIND_MU_MINUS, KIND_MU_PLUS, KIND_E_MINUS, KIND_E_PLUS, KIND_JET = range(6)
+PROC_DY, PROC_W, PROC_TTBAR = 0, 1, 2
+
+SQRT_S = 13000.0
+
+# Physical parameters of the three processes (masses/widths from the workload
+# definitions; couplings are a fixed electroweak/QCD parameter set).
+DEFAULT_PROCESS = {
+    "sqrt_s": SQRT_S,
+    "mz": 91.19, "wz": 2.50,
+    "mw": 80.4, "ww": 2.09,
+    "mt": 173.0, "wt": 1.4,
+    "alpha": 1.0 / 128.0, "sw2": 0.2312, "alpha_s": 0.118,
+    # parametric PDFs f(x) = A x^a (1-x)^b for (quark, antiquark, gluon)
+    "pdf_A": (1.0, 1.0, 1.0),
+    "pdf_a": (-0.5, -0.5, -1.0),
+    "pdf_b": (3.0, 5.0, 5.0),
+}
+
+# Transfer-function parameters per process.
+DEFAULT_TF = {
+    PROC_DY: {"lep_rel": 0.02, "window_k": 5.0, "jet_core": 0.1, "jet_tail": 0.3,
+              "jet_tail_w": 0.2, "jet_lo_div": 1.9, "jet_hi_mul": 10.0,
+              "met_sigma": 15.0, "met_box_k": 4.0},
+    PROC_W: {"lep_rel": 0.03, "window_k": 5.0, "jet_core": 0.1, "jet_tail": 0.3,
+             "jet_tail_w": 0.2, "jet_lo_div": 1.9, "jet_hi_mul": 10.0,
+             "met_sigma": 15.0, "met_box_k": 4.0},
+    PROC_TTBAR: {"lep_rel": 0.0, "window_k": 5.0, "jet_core": 0.1, "jet_tail": 0.3,
+                 "jet_tail_w": 0.2, "jet_lo_div": 1.9, "jet_hi_mul": 10.0,
+                 "met_sigma": 15.0, "met_box_k": 4.0},
+}
+
+DIMS = {PROC_DY: 2, PROC_W: 4, PROC_TTBAR: 7}
+NPERM = {PROC_DY: 1, PROC_W: 1, PROC_TTBAR: 24}
+
+# The five workloads: (process, events, points per event, base seed).
+SEED_BASE = 0x4D454D00
+WORKLOADS = {
+    "dy": dict(proc=PROC_DY, n_events=64, n_points=1 << 16, seed=SEED_BASE + 0),
+    "w": dict(proc=PROC_W, n_events=1024, n_points=1 << 20, seed=SEED_BASE + 1),
+    "ttbar": dict(proc=PROC_TTBAR, n_events=4096, n_points=1 << 22, seed=SEED_BASE + 2),
+    "mix": dict(proc=None, n_events=16384, n_points=1 << 24, seed=SEED_BASE + 3),
+    "flow": dict(proc=PROC_TTBAR, n_events=4096, n_points=1 << 22, seed=SEED_BASE + 4),
+}
+
+
+def jet_permutations():
+    """The 24 assignments of 4 measured jets to the partons (b, bbar, d, ubar),
+    in lexicographic order: entry p[k] is the jet taking parton slot k."""
+    return list(itertools.permutations(range(4)))
+
+
+# ---------------------------------------------------------------- kinematics
+def _bw_mass(rng, m, w, lo, hi, size=None):
+    """Breit-Wigner (Cauchy in m^2) mass, truncated to [lo, hi]."""
+    a = math.atan((lo * lo - m * m) / (m * w))
+    b = math.atan((hi * hi - m * m) / (m * w))
+    t = rng.uniform(a, b, size)
+    return np.sqrt(m * m + m * w * np.tan(t))
+
+
+def _two_body(rng, M, m1, m2):
+    """Isotropic two-body decay at rest; returns the 4-momenta of both daughters."""
+    lam = (M * M - (m1 + m2) ** 2) * (M * M - (m1 - m2) ** 2)
+    p = math.sqrt(max(lam, 0.0)) / (2.0 * M)
+    c = rng.uniform(-1.0, 1.0)
+    s = math.sqrt(max(0.0, 1.0 - c * c))
+    ph = rng.uniform(0.0, 2.0 * math.pi)
+    d = np.array([s * math.cos(ph), s * math.sin(ph), c])
+    p1 = np.concatenate([[math.sqrt(p * p + m1 * m1)], p * d])
+    p2 = np.concatenate([[math.sqrt(p * p + m2 * m2)], -p * d])
+    return p1, p2
+
+
+def _boost_to_lab(p, parent):
+    """Boost 4-vector p from the rest frame of `parent` into the frame where
+    `parent` has the given 4-momentum."""
+    E, px, py, pz = parent
+    m = math.sqrt(max(E * E - px * px - py * py - pz * pz, 0.0))
+    bx, by, bz = px / E, py / E, pz / E
+    b2 = bx * bx + by * by + bz * bz
+    if b2 == 0.0:
+        return np.array(p, dtype=float)
+    g = E / m
+    bp = bx * p[1] + by * p[2] + bz * p[3]
+    g2 = (g - 1.0) / b2
+    return np.array([g * (p[0] + bp),
+                     p[1] + g2 * bp * bx + g * bx * p[0],
+                     p[2] + g2 * bp * by + g * by * p[0],
+                     p[3] + g2 * bp * bz + g * bz * p[0]])
+
+
+def _eta_phi(p):
+    pt = math.hypot(p[1], p[2])
+    pabs = math.sqrt(pt * pt + p[3] * p[3])
+    eta = 0.5 * math.log((pabs + p[3]) / (pabs - p[3])) if pt > 0 else math.copysign(1e9, p[3])
+    return eta, math.atan2(p[2], p[1])
+
+
+def _drell_yan_like(rng, m, rap, lep_kinds):
+    """Resonance of mass m at rest in the transverse plane with rapidity rap,
+    decaying isotropically into two massless leptons."""
+    E = m * math.cosh(rap)
+    pz = m * math.sinh(rap)
+    p1, p2 = _two_body(rng, m, 0.0, 0.0)
+    par = np.array([E, 0.0, 0.0, pz])
+    return _boost_to_lab(p1, par), _boost_to_lab(p2, par)
+
+
+def gen_dy(n, seed, tf=None):
+    tf = tf or DEFAULT_TF[PROC_DY]
+    P = DEFAULT_PROCESS
+    rng = np.random.Generator(np.random.Philox(seed))
+    out = np.zeros((n, RECORD_FLOATS), dtype=np.float32)
+    i = 0
+    while i < n:
+        m = _bw_mass(rng, P["mz"], P["wz"], 60.0, 120.0)
+        y = rng.uniform(-2.0, 2.0)
+        lm, lp = _drell_yan_like(rng, m, y, None)
+        eta_m, phi_m = _eta_phi(lm)
+        eta_p, phi_p = _eta_phi(lp)
+        if abs(eta_m) > 2.5 or abs(eta_p) > 2.5:
+            continue
+        Em = lm[0] * (1.0 + tf["lep_rel"] * rng.standard_normal())
+        Ep = lp[0] * (1.0 + tf["lep_rel"] * rng.standard_normal())
+        r = out[i]
+        r[0:4] = (Em, eta_m, phi_m, KIND_MU_MINUS)
+        r[4:8] = (Ep, eta_p, phi_p, KIND_MU_PLUS)
+        r[26] = 2
+        r[27] = PROC_DY
+        i += 1
+    return out
+
+
+def gen_w(n, seed, tf=None):
+    tf = tf or DEFAULT_TF[PROC_W]
+    P = DEFAULT_PROCESS
+    rng = np.random.Generator(np.random.Philox(seed))
+    out = np.zeros((n, RECORD_FLOATS), dtype=np.float32)
+    i = 0
+    while i < n:
+        m = _bw_mass(rng, P["mw"], P["ww"], 50.0, 110.0)
+        y = rng.uniform(-2.0, 2.0)
+        e, nu = _drell_yan_like(rng, m, y, None)
+        eta, phi = _eta_phi(e)
+        if abs(eta) > 2.5:
+            continue
+        Em = e[0] * (1.0 + tf["lep_rel"] * rng.standard_normal())
+        r = out[i]
+        r[0:4] = (Em, eta, phi, KIND_E_PLUS)
+        r[24] = nu[1] + tf["met_sigma"] * rng.standard_normal()
+        r[25] = nu[2] + tf["met_sigma"] * rng.standard_normal()
+        r[26] = 1
+        r[27] = PROC_W
+        i += 1
+    return out
+
+
+def gen_ttbar(n, seed, tf=None):
+    tf = tf or DEFAULT_TF[PROC_TTBAR]
+    P = DEFAULT_PROCESS
+    rng = np.random.Generator(np.random.Philox(seed))
+    out = np.zeros((n, RECORD_FLOATS), dtype=np.float32)
+    perms = jet_permutations()
+    i = 0
+    while i < n:
+        mtt = rng.uniform(350.0, 1000.0)
+        mt1 = _bw_mass(rng, P["mt"], P["wt"], P["mt"] - 15 * P["wt"], P["mt"] + 15 * P["wt"])
+        mt2 = _bw_mass(rng, P["mt"], P["wt"], P["mt"] - 15 * P["wt"], P["mt"] + 15 * P["wt"])
+        if mt1 + mt2 >= mtt:
+            continue
+        mw1 = _bw_mass(rng, P["mw"], P["ww"], P["mw"] - 15 * P["ww"], P["mw"] + 15 * P["ww"])
+        mw2 = _bw_mass(rng, P["mw"], P["ww"], P["mw"] - 15 * P["ww"], P["mw"] + 15 * P["ww"])
+        y = rng.uniform(-1.5, 1.5)
+        sysp = np.array([mtt * math.cosh(y), 0.0, 0.0, mtt * math.sinh(y)])
+        t, tb = _two_body(rng, mtt, mt1, mt2)
+        t, tb = _boost_to_lab(t, sysp), _boost_to_lab(tb, sysp)
+        b, wp = _two_body(rng, mt1, 0.0, mw1)
+        b, wp = _boost_to_lab(b, t), _boost_to_lab(wp, t)
+        lep, nu = _two_body(rng, mw1, 0.0, 0.0)
+        lep, nu = _boost_to_lab(lep, wp), _boost_to_lab(nu, wp)
+        bb, wm = _two_body(rng, mt2, 0.0, mw2)
+        bb, wm = _boost_to_lab(bb, tb), _boost_to_lab(wm, tb)
+        d, ub = _two_body(rng, mw2, 0.0, 0.0)
+        d, ub = _boost_to_lab(d, wm), _boost_to_lab(ub, wm)
+        eta_l, phi_l = _eta_phi(lep)
+        if abs(eta_l) > 2.5:
+            continue
+        partons = [b, bb, d, ub]
+        jets = []
+        ok = True
+        for p in partons:
+            eta, phi = _eta_phi(p)
+            rel = tf["jet_tail"] if rng.uniform() < tf["jet_tail_w"] else tf["jet_core"]
+            Em = p[0] * (1.0 + rel * rng.standard_normal())
+            if abs(eta) > 2.5 or Em < 20.0:
+                ok = False
+                break
+            jets.append((Em, eta, phi))
+        if not ok:
+            continue
+        order = sorted(range(4), key=lambda k: -jets[k][0])  # jet slot -> parton
+        # truth permutation: parton slot k sits in jet position order.index(k)
+        truth = tuple(order.index(k) for k in range(4))
+        r = out[i]
+        r[0:4] = (lep[0], eta_l, phi_l, KIND_E_PLUS)
+        for slot, k in enumerate(order):
+            r[4 + 4 * slot: 8 + 4 * slot] = (jets[k][0], jets[k][1], jets[k][2], KIND_JET)
+        r[24] = nu[1] + tf["met_sigma"] * rng.standard_normal()
+        r[25] = nu[2] + tf["met_sigma"] * rng.standard_normal()
+        r[26] = 5
+        r[27] = PROC_TTBAR
+        r[28] = perms.index(truth)
+        i += 1
+    return out
+
+
+GENERATORS = {PROC_DY: gen_dy, PROC_W: gen_w, PROC_TTBAR: gen_ttbar}
+
+
+def gen_events(proc, n, seed):
+    return GENERATORS[proc](n, seed)
+
+
+def gen_mix(n, seed, fractions=(0.5, 0.3, 0.2)):
+    """Uneven batch: events drawn from the three processes with the given
+    fractions, shuffled with a seeded permutation."""
+    counts = [int(round(f * n)) for f in fractions]
+    counts[0] += n - sum(counts)
+    parts = [gen_events(p, c, seed + 1000 * (p + 1)) for p, c in enumerate(counts)]
+    recs = np.concatenate(parts, axis=0)
+    perm = np.random.Generator(np.random.Philox(seed)).permutation(n)
+    return recs[perm]
