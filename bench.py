@@ -1,0 +1,323 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 matrix-element-method integrator.
+
+Default workload: W -> e nu, 1024 synthetic events, 2^20 integrand evaluations
+per event, 4-dimensional integral (5 VEGAS adaptation iterations of 2^14
+points, then the frozen-grid phase). One step = one mem_integrate call over
+all events with the event records resident on the device.
+
+Metric: integrand evaluations per second (whole job over all ranks).
+Also reported: the end-to-end figure through the public C ABI with host
+buffers (upload + integrate + result copy inside the timed region), a live
+roofline of the dominant kernel (the frozen-grid sampling kernel, FP32-ALU
+bound) timed with CUDA events on its own stream, the FP64 oracle timed on
+the host cores (cpu_baseline), and the SM clocks sampled during the timing.
+
+--impl reference times the FP64 CPU oracle on a bounded sample instead.
+Multi-GPU (torchrun): every rank integrates its own event sample (weak
+scaling, no collective on the data path); times are max-reduced.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1407_7595_gb300 import synth  # noqa: E402
+
+# FP32 flops (FADD, FMUL = 1; FFMA = 2) executed per integrand evaluation by the
+# frozen-grid kernel, counted with ncu instruction counters (see profiles/);
+# MUFU, integer (Philox) and memory instructions are not counted as flops.
+FLOPS_PER_EVAL = {synth.PROC_DY: None, synth.PROC_W: 406.0, synth.PROC_TTBAR: None}
+FP32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 FP32 lanes
+
+WORKLOAD_NAMES = {
+    "w": "W->e nu LO, 4-dim integral (E_e, nu px, nu py, q^2_W), 1024 events x 2^20 "
+         "evaluations/event, FP32 integrand + FP64 accumulation",
+    "dy": "Drell-Yan Z/photon->mu mu, 2-dim integral, 64 events x 2^16 evaluations/event",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["w", "dy"], default="w")
+    ap.add_argument("--events", type=int, default=None, help="override the event count")
+    ap.add_argument("--points", type=int, default=None, help="override points per event")
+    ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    w = dict(synth.WORKLOADS[args.workload])
+    if args.events:
+        w["n_events"] = args.events
+    if args.points:
+        w["n_points"] = args.points
+    return w
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling in the background (read-only)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(kind, seed):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload, all host cores."""
+    from oracle import oracle as O
+    n_ev, n_pts = {synth.PROC_W: (64, 1 << 16), synth.PROC_DY: (16, 1 << 15)}[kind]
+    recs = synth.gen_events(kind, n_ev, seed)
+    P = O.process(kind, synth.DEFAULT_PROCESS)
+    T = O.tf(synth.DEFAULT_TF[kind])
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    O.integrate(P, T, recs, seed=1, n_points=n_pts, n_threads=cores)
+    dt = time.perf_counter() - t
+    return {"value": n_ev * n_pts / dt, "unit": "integrand evals/s", "cores": cores,
+            "kind": "oracle", "sample": f"{n_ev} events x {n_pts} evaluations/event "
+                                       f"(same generator and VEGAS plan), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = workload(args)
+    kind = w["proc"]
+    from oracle import oracle as O
+    n_ev, n_pts = 16, 1 << 14
+    recs = synth.gen_events(kind, n_ev, w["seed"])
+    P = O.process(kind, synth.DEFAULT_PROCESS)
+    T = O.tf(synth.DEFAULT_TF[kind])
+    cores = os.cpu_count() or 1
+    for i in range(args.warmup):
+        O.integrate(P, T, recs[:2], seed=100 + i, n_points=n_pts, n_threads=cores)
+    times = []
+    for i in range(args.steps):
+        t = time.perf_counter()
+        O.integrate(P, T, recs, seed=i, n_points=n_pts, n_threads=cores)
+        times.append(time.perf_counter() - t)
+    step = sum(times) / len(times)
+    value = n_ev * n_pts / step
+    sample = f"{n_ev} events x {n_pts} evaluations/event per step of the {args.workload} workload"
+    out = {"impl": "reference", "metric": "integrand evaluations per second", "value": value,
+           "unit": "integrand evals/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD_NAMES[args.workload], "events": w["n_events"],
+                      "points_per_event": w["n_points"]},
+           "cpu_baseline": {"value": value, "unit": "integrand evals/s", "cores": cores,
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "integrand evals/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_1407_7595_gb300 import abi
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = workload(args)
+    kind, n_ev, n_pts = w["proc"], w["n_events"], w["n_points"]
+    seed_r = w["seed"] + 1000003 * rank
+    recs = synth.gen_events(kind, n_ev, seed_r)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    tf = abi.tf_desc(synth.DEFAULT_TF[kind])
+    proc = abi.mem_create_process(abi.process_desc(kind, synth.DEFAULT_PROCESS))
+    events = abi.mem_upload_events(proc, recs, sp)
+    dev = torch.device("cuda", local)
+    prob = torch.zeros(n_ev, dtype=torch.float64, device=dev)
+    err = torch.zeros_like(prob)
+    used = torch.zeros(n_ev, dtype=torch.int64, device=dev)
+    st = torch.zeros(n_ev, dtype=torch.int32, device=dev)
+    ph = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for e in ph:
+        e.record(stream)  # create the underlying CUDA events
+    opts = abi.make_opts(event_id_base=rank * n_ev, phase_events=ph)
+    n_adapt = min(1 << 14, n_pts // 8)
+    n_main = n_pts - 5 * n_adapt
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step(seed):
+        abi.mem_integrate(events, proc, tf, n_pts, seed, opts, prob, err, used, st, sp)
+
+    for i in range(args.warmup):
+        step(10_000 + i)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    step_ms, main_ms, adapt_ms = [], [], []
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))  # evict L2 between steps (outside the step's events)
+        t0.record(stream)
+        step(i)
+        t1.record(stream)
+        t1.synchronize()
+        step_ms.append(t0.elapsed_time(t1))
+        adapt_ms.append(ph[0].elapsed_time(ph[1]))
+        main_ms.append(ph[1].elapsed_time(ph[2]))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    clocks = sampler.stop() if rank == 0 else None
+    ms_step = total_ms / args.steps
+    value = world * n_ev * n_pts / (ms_step * 1e-3)
+    ok = bool(torch.all(st == 0).item())
+
+    # end to end through the public API with host buffers: pinned records in,
+    # host results out, upload + integrate + copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.from_numpy(recs).pin_memory()
+        hp = torch.zeros(n_ev, dtype=torch.float64).pin_memory()
+        he = torch.zeros_like(hp)
+        hu = torch.zeros(n_ev, dtype=torch.int64).pin_memory()
+        hs = torch.zeros(n_ev, dtype=torch.int32).pin_memory()
+        e2e_steps = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for i in range(e2e_steps):
+            ev2 = abi.mem_upload_events(proc, pinned, sp)
+            abi.mem_integrate(ev2, proc, tf, n_pts, 500 + i, abi.make_opts(event_id_base=rank * n_ev),
+                              hp.numpy(), he.numpy(), hu.numpy(), hs.numpy(), sp)
+            abi.mem_destroy(ev2)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t) / e2e_steps
+        if world > 1:
+            tt = torch.tensor([dt], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            dt = float(tt.item())
+        e2e = {"value": world * n_ev * n_pts / dt, "unit": "integrand evals/s",
+               "h2d_bytes_per_step": int(recs.nbytes),
+               "d2h_bytes_per_step": int(n_ev * (8 + 8 + 8 + 4)),
+               "ms_per_step": dt * 1e3}
+
+    if rank == 0:
+        props = torch.cuda.get_device_properties(local)
+        sms = props.multi_processor_count
+        max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+        peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+        fpe = FLOPS_PER_EVAL.get(kind)
+        t_main = statistics.mean(main_ms) * 1e-3
+        achieved = fpe * n_ev * n_main / t_main / 1e12 if fpe else None
+        roof = {"bound": "alu", "kernel": "k_main (frozen-grid sampling)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                               f"{max_mhz:.0f} MHz max SM clock",
+                "flops_per_eval": fpe, "kernel_ms": t_main * 1e3,
+                "kernel_share_of_step": t_main * 1e3 / statistics.mean(step_ms)}
+        out = {"metric": "integrand evaluations per second", "value": value,
+               "unit": "integrand evals/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic", "impl": "ours",
+               "config": {"workload": WORKLOAD_NAMES.get(args.workload, args.workload),
+                          "events_per_gpu": n_ev, "points_per_event": n_pts,
+                          "adapt": "5 x %d points (excluded from the estimate)" % n_adapt,
+                          "l2": "flushed (256 MB write) between timed steps",
+                          "parallelism": f"{world} independent event shards"},
+               "phases_ms": {"adapt": statistics.mean(adapt_ms), "main": statistics.mean(main_ms),
+                             "step": statistics.mean(step_ms)},
+               "status_ok": ok, "median_rel_err": float(torch.median(err / prob).item()),
+               "roofline": roof, "clocks": clocks, "e2e": e2e,
+               "gpu_launches": 3 * args.steps}
+        if not args.no_baseline and world >= 1:
+            out["cpu_baseline"] = cpu_baseline(kind, w["seed"])
+        print(json.dumps(out), flush=True)
+    abi.mem_destroy(events)
+    abi.mem_destroy(proc)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

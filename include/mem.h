@@ -1,0 +1,159 @@
+/* mem.h -- C ABI of the GB300 matrix-element-method integrator (libmem.so).
+ *
+ * The library computes, for each collision event X, the matrix-element-method
+ * probability density of Sec. 1 of arXiv:1407.7595 (Eq. "mem_def" convolved
+ * with the transfer functions as in the p_hat equation that follows it, and in
+ * the form of Eq. "integrand" of Sec. 3):
+ *
+ *   p_hat(X) = (1/N_perm) sum_perm int dY  sum_flavour |M|^2(Y) f1(x1) f2(x2)
+ *              / (|q1||q2|) dPhi_n(q1+q2; Y) T(X|Y)
+ *
+ * as a Monte Carlo integral (Sec. 2, Eq. "sum", with its error estimate) over
+ * the unmeasured degrees of freedom, importance-sampled with a VEGAS grid
+ * (Sec. 2) that is refined on the device. Every integrand evaluation runs in
+ * hand-written sm_103a CUDA; there is no CPU fallback.
+ *
+ * Conventions for every entry point:
+ *  - Every call returns a mem_status; on failure mem_last_error() gives a
+ *    thread-local message. Per-event problems go to ev_status and do not fail
+ *    the call.
+ *  - Handles (mem_process, mem_events) are owned by the library; release them
+ *    with mem_destroy. Arrays passed in are owned by the caller.
+ *  - Output arrays may be host or device memory (detected per pointer). With
+ *    device outputs the call is asynchronous on `stream`; with host outputs
+ *    it synchronises `stream` before returning.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Work runs on the CUDA device current on the calling thread.
+ */
+#ifndef MEM_H
+#define MEM_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MEM_OK = 0,
+  MEM_ERR_INVALID_ARG = 1, /* a pointer, size or descriptor field is invalid */
+  MEM_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  MEM_ERR_OOM = 3,         /* device allocation failed */
+  MEM_ERR_NONFINITE = 4,   /* per event: some integrand values were not finite */
+  MEM_NOT_CONVERGED = 5,   /* per event: the point cap was reached before the target */
+  MEM_ERR_TIMEOUT = 6      /* a bounded device wait ran out */
+} mem_status;
+
+/* Processes (the |M|^2 of Eq. "mem_def"). */
+enum {
+  MEM_PROC_DY = 0,    /* q qbar -> photon/Z -> mu- mu+ ; 2 integration dims, 1 permutation */
+  MEM_PROC_W = 1,     /* u dbar -> W+ -> e+ nu (or W-) ; 4 dims, 1 permutation */
+  MEM_PROC_TTBAR = 2  /* gg, q qbar -> t tbar -> b l+ nu bbar d ubar ; 7 dims, 24 jet permutations */
+};
+
+typedef struct mem_process mem_process; /* opaque, library-owned */
+typedef struct mem_events mem_events;   /* opaque, library-owned device copy of events */
+
+/* Physics parameters of a process (Sec. 1: |M|^2, PDFs f1, f2; sigma_i := 1).
+ * Energies in GeV. PDFs are f(x) = A x^a (1-x)^b for quark, antiquark, gluon. */
+typedef struct {
+  int32_t kind;       /* MEM_PROC_* */
+  int32_t reserved;   /* must be 0 */
+  double sqrt_s;      /* collider energy */
+  double mz, wz, mw, ww, mt, wt; /* masses and widths */
+  double alpha, sw2, alpha_s;    /* e^2/4pi, sin^2(theta_W), g_s^2/4pi */
+  double pdf_A[3], pdf_a[3], pdf_b[3];
+} mem_process_desc;
+
+/* Transfer functions T(X|Y) (Sec. 1): delta functions for all directions and
+ * the ttbar lepton energy; Gaussian lepton energies N(x; E, lep_rel E)
+ * integrated over +-window_k sigma; double-Gaussian jet energies
+ * (1-w) N(x; E, core E) + w N(x; E, tail E) integrated over
+ * [x/jet_lo_div, min(x jet_hi_mul, sqrt_s/2)]; Gaussian missing-pT resolution
+ * met_sigma per component, neutrino pT integrated over MET +- met_box_k sigma. */
+typedef struct {
+  double lep_rel, window_k;
+  double jet_core, jet_tail, jet_tail_w, jet_lo_div, jet_hi_mul;
+  double met_sigma, met_box_k;
+} mem_tf_desc;
+
+/* Integration options (NULL = defaults: fixed n_points per event, 5 VEGAS
+ * adaptation iterations of min(2^14, n/8) points, alpha = 1.5). */
+typedef struct {
+  double target_rel_err;  /* > 0: adaptive budget -- keep adding frozen-grid chunks
+                             until err/prob <= target or max_points (per event) */
+  uint64_t max_points;    /* cap per event in adaptive mode (0 = 2^24) */
+  uint64_t min_points;    /* minimum per event in adaptive mode (0 = n_points) */
+  int32_t n_adapt_iters;  /* VEGAS adaptation iterations, excluded from the estimate */
+  int32_t reserved0;      /* must be 0 */
+  uint64_t adapt_points;  /* points per item per adaptation iteration (0 = min(2^14, n/8)) */
+  double alpha;           /* grid compression exponent (0 = 1.5) */
+  const double* grid_in;  /* optional HOST array d x 129: starting grid shared by all items */
+  uint64_t event_id_base; /* Philox counter id of event 0 (for sharded runs) */
+  void* phase_events;     /* optional array of 4 cudaEvent_t recorded on `stream` before the
+                             adaptation kernel, before the frozen-grid kernel, before the
+                             finalisation kernel and after it (phase timing); NULL = none */
+} mem_opts;
+
+/* Number of integration dimensions / jet permutations of a process kind (-1 if invalid). */
+int32_t mem_process_dims(int32_t kind);
+int32_t mem_process_nperm(int32_t kind);
+
+/* Validate a process description and copy it into a library-owned handle.
+ * Errors: MEM_ERR_INVALID_ARG (NULL pointers, unknown kind, non-positive
+ * masses/widths/energy, reserved != 0). */
+mem_status mem_create_process(const mem_process_desc* desc, mem_process** out);
+
+/* Copy n_events event records (32 float32 each, layout in the package's
+ * synth module docs: 6 x (E, eta, phi, kind), MET x, y, n_obj, kind, ...)
+ * into library-owned device memory. `records` is host memory if
+ * records_on_device == 0, else device memory. The copy is enqueued on
+ * `stream` and completes before the call returns.
+ * Errors: MEM_ERR_INVALID_ARG (NULL, n_events < 1, records of another process
+ * kind), MEM_ERR_OOM, MEM_ERR_CUDA. */
+mem_status mem_upload_events(mem_process* proc, const float* records, int64_t n_events,
+                             int32_t records_on_device, void* stream, mem_events** out);
+
+/* Integrate every uploaded event with n_points integrand evaluations per
+ * (event, jet permutation) item, Philox key `seed`. Writes per event:
+ * prob (p_hat), err (MC standard error), n_used (evaluations, adaptation
+ * included) and ev_status (MEM_OK, MEM_ERR_NONFINITE, MEM_NOT_CONVERGED).
+ * Any of n_used / ev_status may be NULL. Each output holds n_events entries.
+ * Errors: MEM_ERR_INVALID_ARG (NULL, n_points too small for the adaptation
+ * plan or above 2^32, process mismatch), MEM_ERR_OOM, MEM_ERR_CUDA. */
+mem_status mem_integrate(const mem_events* ev, const mem_process* proc, const mem_tf_desc* tf,
+                         uint64_t n_points, uint64_t seed, const mem_opts* opts, double* prob,
+                         double* err, uint64_t* n_used, int32_t* ev_status, void* stream);
+
+/* Release a mem_process or mem_events handle (NULL is a no-op). Releasing a
+ * process does not release events uploaded with it. */
+void mem_destroy(void* handle);
+
+/* Thread-local description of the last error ("" if none). */
+const char* mem_last_error(void);
+
+/* ---- parts of the hot path exposed for parity tests ---------------------- */
+
+/* Integrand weight at points point0 .. point0+n-1 of item (event_index, perm)
+ * on the given HOST grid (d x 129 doubles; NULL = uniform), using exactly the
+ * generator, VEGAS map and integrand of mem_integrate, in FP32, times the
+ * process's FP64 constant prefactor. w_out: n doubles, host or device. */
+mem_status mem_eval_points(const mem_events* ev, const mem_process* proc, const mem_tf_desc* tf,
+                           int64_t event_index, int32_t perm, uint64_t seed, uint64_t point0,
+                           int64_t n, const double* grid, double* w_out, void* stream);
+
+/* The device Philox4x32-10 stream (Salmon et al., SC'11): uniforms of
+ * dimensions 0..d-1 for points point0.., counter (point, block<<8, event, perm).
+ * out: n*d floats (row-major), host or device. */
+mem_status mem_philox_uniforms(uint64_t seed, uint64_t event_id, int32_t perm, uint64_t point0,
+                               int64_t n, int32_t d, float* out, void* stream);
+
+/* Device VEGAS refinement (Sec. 2; Lepage 1978) of n_grids grids of d
+ * dimensions: hist n_grids x d x 128 (accumulated squared weights), grid_in
+ * and grid_out n_grids x d x 129 doubles, all HOST arrays. alpha = compression. */
+mem_status mem_vegas_refine(int32_t n_grids, int32_t d, const double* hist,
+                            const double* grid_in, double alpha, double* grid_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

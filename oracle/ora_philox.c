@@ -33,7 +33,9 @@ void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-double ora_u01(uint32_t x) { return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0); }
+/* 23 random bits: ((x >> 9) + 0.5) 2^-23 = (2k+1) 2^-24 is exactly representable
+ * in FP32 over all of (0,1) (a 24-bit version would need 25 mantissa bits above 1/2). */
+double ora_u01(uint32_t x) { return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 /* Counter layout: (point index, draw block << 8 | stream tag, event id, perm);
  * key = (seed low word, seed high word). Integration stream tag = 0. Draw block

@@ -61,7 +61,7 @@ int ora_nperm(int kind);
 
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */
 void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
-/* Uniform in (0,1) from a 32-bit word: ((x >> 8) + 0.5) * 2^-24. */
+/* Uniform in (0,1) from a 32-bit word: ((x >> 9) + 0.5) * 2^-23 (exact in FP32). */
 double ora_u01(uint32_t x);
 /* Unit-cube point for (event_id, perm, point index) from the integration stream. */
 void ora_point_u(uint64_t seed, uint64_t event_id, int perm, uint64_t idx, int d, double* u);

@@ -1,0 +1,240 @@
+"""Thin ctypes binding of libmem.so (declarations in include/mem.h).
+
+Argument marshalling only: every step of the integration runs in the CUDA
+library. Functions keep the C names (mem_create_process, mem_upload_events,
+mem_integrate, mem_destroy, ...). Device arrays are passed as torch CUDA
+tensors (data_ptr), host arrays as numpy arrays. If the library has not been
+built, lib() raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmem.so")
+
+MEM_OK, MEM_ERR_INVALID_ARG, MEM_ERR_CUDA, MEM_ERR_OOM, MEM_ERR_NONFINITE, \
+    MEM_NOT_CONVERGED, MEM_ERR_TIMEOUT = range(7)
+MEM_PROC_DY, MEM_PROC_W, MEM_PROC_TTBAR = 0, 1, 2
+NG = 128
+REC = 32
+
+
+class MemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"mem status {status}: {msg}")
+        self.status = status
+
+
+class mem_process_desc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("sqrt_s", C.c_double),
+                ("mz", C.c_double), ("wz", C.c_double), ("mw", C.c_double), ("ww", C.c_double),
+                ("mt", C.c_double), ("wt", C.c_double), ("alpha", C.c_double),
+                ("sw2", C.c_double), ("alpha_s", C.c_double), ("pdf_A", C.c_double * 3),
+                ("pdf_a", C.c_double * 3), ("pdf_b", C.c_double * 3)]
+
+
+class mem_tf_desc(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("lep_rel", "window_k", "jet_core", "jet_tail",
+                                          "jet_tail_w", "jet_lo_div", "jet_hi_mul",
+                                          "met_sigma", "met_box_k")]
+
+
+class mem_opts(C.Structure):
+    _fields_ = [("target_rel_err", C.c_double), ("max_points", C.c_uint64),
+                ("min_points", C.c_uint64), ("n_adapt_iters", C.c_int32),
+                ("reserved0", C.c_int32), ("adapt_points", C.c_uint64), ("alpha", C.c_double),
+                ("grid_in", C.POINTER(C.c_double)), ("event_id_base", C.c_uint64),
+                ("phase_events", C.c_void_p)]
+
+
+_lib = None
+_vp = C.c_void_p
+
+# (name, restype, argtypes) of every exported symbol declared in include/mem.h
+SIGNATURES = [
+    ("mem_process_dims", C.c_int32, [C.c_int32]),
+    ("mem_process_nperm", C.c_int32, [C.c_int32]),
+    ("mem_create_process", C.c_int, [C.POINTER(mem_process_desc), C.POINTER(_vp)]),
+    ("mem_upload_events", C.c_int, [_vp, _vp, C.c_int64, C.c_int32, _vp, C.POINTER(_vp)]),
+    ("mem_integrate", C.c_int, [_vp, _vp, C.POINTER(mem_tf_desc), C.c_uint64, C.c_uint64,
+                                C.POINTER(mem_opts), _vp, _vp, _vp, _vp, _vp]),
+    ("mem_destroy", None, [_vp]),
+    ("mem_last_error", C.c_char_p, []),
+    ("mem_eval_points", C.c_int, [_vp, _vp, C.POINTER(mem_tf_desc), C.c_int64, C.c_int32,
+                                  C.c_uint64, C.c_uint64, C.c_int64, _vp, _vp, _vp]),
+    ("mem_philox_uniforms", C.c_int, [C.c_uint64, C.c_uint64, C.c_int32, C.c_uint64, C.c_int64,
+                                      C.c_int32, _vp, _vp]),
+    ("mem_vegas_refine", C.c_int, [C.c_int32, C.c_int32, _vp, _vp, C.c_double, _vp]),
+]
+
+
+def lib():
+    """Load libmem.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != MEM_OK:
+        raise MemError(status, lib().mem_last_error().decode())
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def process_desc(kind, params):
+    d = mem_process_desc()
+    d.kind = kind
+    d.reserved = 0
+    for k in ("sqrt_s", "mz", "wz", "mw", "ww", "mt", "wt", "alpha", "sw2", "alpha_s"):
+        setattr(d, k, float(params[k]))
+    for k in ("pdf_A", "pdf_a", "pdf_b"):
+        getattr(d, k)[:] = [float(v) for v in params[k]]
+    return d
+
+
+def tf_desc(params):
+    t = mem_tf_desc()
+    for k, _ in mem_tf_desc._fields_:
+        setattr(t, k, float(params[k]))
+    return t
+
+
+def make_opts(n_adapt_iters=5, adapt_points=0, alpha=1.5, grid_in=None, event_id_base=0,
+              target_rel_err=0.0, max_points=0, min_points=0, phase_events=None):
+    """phase_events: optional list of 4 torch.cuda.Event (created with
+    enable_timing=True) recorded at the phase boundaries on the call's stream."""
+    o = mem_opts()
+    o.target_rel_err = target_rel_err
+    o.max_points = max_points
+    o.min_points = min_points
+    o.n_adapt_iters = n_adapt_iters
+    o.reserved0 = 0
+    o.adapt_points = adapt_points
+    o.alpha = alpha
+    keep = None
+    if grid_in is not None:
+        keep = np.ascontiguousarray(grid_in, dtype=np.float64)
+        o.grid_in = keep.ctypes.data_as(C.POINTER(C.c_double))
+    o.event_id_base = event_id_base
+    ev_arr = None
+    if phase_events is not None:
+        assert len(phase_events) == 4
+        ev_arr = (C.c_void_p * 4)(*[e.cuda_event for e in phase_events])
+        o.phase_events = C.cast(ev_arr, C.c_void_p)
+    o._keep = (keep, ev_arr)
+    return o
+
+
+def mem_process_dims(kind):
+    return lib().mem_process_dims(kind)
+
+
+def mem_process_nperm(kind):
+    return lib().mem_process_nperm(kind)
+
+
+def mem_create_process(desc):
+    h = _vp()
+    _check(lib().mem_create_process(C.byref(desc), C.byref(h)))
+    return h
+
+
+def mem_upload_events(proc, records, stream=None):
+    """records: host numpy (n, 32) float32 or device torch tensor."""
+    on_dev = int(hasattr(records, "is_cuda") and records.is_cuda)
+    n = records.shape[0]
+    h = _vp()
+    _check(lib().mem_upload_events(proc, _ptr(records), n, on_dev, stream, C.byref(h)))
+    return h
+
+
+def mem_integrate(events, proc, tf, n_points, seed, opts, prob, err, n_used=None,
+                  ev_status=None, stream=None):
+    _check(lib().mem_integrate(events, proc, C.byref(tf), n_points, seed,
+                               C.byref(opts) if opts is not None else None, _ptr(prob),
+                               _ptr(err), _ptr(n_used), _ptr(ev_status), stream))
+
+
+def mem_destroy(handle):
+    lib().mem_destroy(handle)
+
+
+def mem_eval_points(events, proc, tf, event_index, perm, seed, point0, n, grid, w_out,
+                    stream=None):
+    g = None if grid is None else np.ascontiguousarray(grid, dtype=np.float64)
+    _check(lib().mem_eval_points(events, proc, C.byref(tf), event_index, perm, seed, point0, n,
+                                 _ptr(g), _ptr(w_out), stream))
+
+
+def mem_philox_uniforms(seed, event_id, perm, point0, n, d, out, stream=None):
+    _check(lib().mem_philox_uniforms(seed, event_id, perm, point0, n, d, _ptr(out), stream))
+
+
+def mem_vegas_refine(hist, grid_in, alpha=1.5):
+    hist = np.ascontiguousarray(hist, dtype=np.float64)
+    grid_in = np.ascontiguousarray(grid_in, dtype=np.float64)
+    n, d = grid_in.shape[0], grid_in.shape[1]
+    out = np.zeros_like(grid_in)
+    _check(lib().mem_vegas_refine(n, d, _ptr(hist), _ptr(grid_in), alpha, _ptr(out)))
+    return out
+
+
+# ------------------------------------------------------------------ helpers
+class Integrator:
+    """Owns a process handle and uploaded events; integrate() returns numpy results."""
+
+    def __init__(self, kind, records, process_params, tf_params, stream=None):
+        self.kind = kind
+        self.tf = tf_desc(tf_params)
+        self.proc = mem_create_process(process_desc(kind, process_params))
+        self.events = mem_upload_events(self.proc, records, stream)
+        self.n = records.shape[0]
+
+    def integrate(self, n_points, seed, opts=None, stream=None):
+        prob = np.zeros(self.n)
+        err = np.zeros(self.n)
+        used = np.zeros(self.n, dtype=np.uint64)
+        st = np.zeros(self.n, dtype=np.int32)
+        mem_integrate(self.events, self.proc, self.tf, n_points, seed, opts, prob, err, used, st,
+                      stream)
+        return {"prob": prob, "err": err, "n_used": used, "status": st}
+
+    def eval_points(self, event_index, perm, seed, point0, n, grid=None):
+        w = np.zeros(n)
+        mem_eval_points(self.events, self.proc, self.tf, event_index, perm, seed, point0, n, grid,
+                        w)
+        return w
+
+    def close(self):
+        if self.events:
+            mem_destroy(self.events)
+            self.events = None
+        if self.proc:
+            mem_destroy(self.proc)
+            self.proc = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

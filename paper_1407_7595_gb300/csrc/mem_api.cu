@@ -1,0 +1,564 @@
+// C ABI of libmem.so (declared in include/mem.h): validation, process
+// constants, device memory, launches and result transfer.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mem.h"
+#include "mem_internal.h"
+#include "mem_kernels.cuh"
+
+namespace {
+
+constexpr uint32_t MAGIC_PROC = 0x4D454D50u;  // "MEMP"
+constexpr uint32_t MAGIC_EVT = 0x4D454D45u;   // "MEME"
+
+thread_local std::string g_err;
+
+mem_status fail(mem_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+mem_status cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? MEM_ERR_OOM : MEM_ERR_CUDA;
+}
+
+#define MEM_CK(call)                                  \
+  do {                                                \
+    cudaError_t e__ = (call);                         \
+    if (e__ != cudaSuccess) return cuda_fail(e__, #call); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct mem_process {
+  uint32_t magic;
+  mem_process_desc desc;
+  mem::ProcConst pc;
+};
+
+struct mem_events {
+  uint32_t magic;
+  int32_t kind;
+  int64_t n;
+  int device;
+  float* d_recs;
+};
+
+namespace mem {
+
+int dims_of(int kind) { return kind == PROC_DY ? 2 : kind == PROC_W ? 4 : kind == PROC_TTBAR ? 7 : -1; }
+int nperm_of(int kind) { return kind == PROC_TTBAR ? 24 : (kind == PROC_DY || kind == PROC_W) ? 1 : -1; }
+uint32_t chunk_points(int kind) {
+  return THREADS * (kind == PROC_DY ? 16u : kind == PROC_W ? 32u : 8u);
+}
+
+cudaError_t launch_integrate(int kind, const IntegrateArgs& a, cudaStream_t st) {
+  switch (kind) {
+    case PROC_DY: return launch_integrate_dy(a, st);
+    case PROC_W: return launch_integrate_w(a, st);
+    case PROC_TTBAR: return launch_integrate_tt(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+size_t cache_size(int kind) {
+  return kind == PROC_DY ? cache_size_dy() : kind == PROC_W ? cache_size_w() : cache_size_tt();
+}
+
+cudaError_t launch_eval(int kind, const EvalArgs& a, cudaStream_t st) {
+  switch (kind) {
+    case PROC_DY: return launch_eval_dy(a, st);
+    case PROC_W: return launch_eval_w(a, st);
+    case PROC_TTBAR: return launch_eval_tt(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+__device__ __forceinline__ void neu_add(double& s, double& c, double x) {
+  const double t = s + x;
+  if (fabs(s) >= fabs(x)) c += (s - t) + x;
+  else c += (x - t) + s;
+  s = t;
+}
+
+__global__ void k_final(const Slot* __restrict__ slots, int64_t n_events, int nperm,
+                        uint32_t cpi, uint32_t n_main, uint64_t n_per_item, double prefactor,
+                        double* __restrict__ prob, double* __restrict__ err,
+                        uint64_t* __restrict__ n_used, int32_t* __restrict__ status) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_events) return;
+  double ms = 0, mc = 0, vs = 0, vc = 0;
+  uint32_t nbad = 0;
+  bool invalid = false;
+  const double N = (double)n_main;
+  for (int p = 0; p < nperm; ++p) {
+    const Slot* sl = slots + ((uint64_t)e * nperm + p) * cpi;
+    double s1 = 0, c1 = 0, s2 = 0, c2 = 0;
+    for (uint32_t c = 0; c < cpi; ++c) {
+      const Slot q = sl[c];
+      neu_add(s1, c1, q.s1);
+      neu_add(s1, c1, q.c1);
+      neu_add(s2, c2, q.s2);
+      neu_add(s2, c2, q.c2);
+      nbad += q.n_bad & 0x7fffffffu;
+      invalid |= (q.n_bad >> 31) != 0;
+    }
+    const double mean = (s1 + c1) / N;
+    double var = ((s2 + c2) / N - mean * mean) / (N - 1.0);
+    var = var > 0.0 ? var : 0.0;
+    neu_add(ms, mc, mean);
+    neu_add(vs, vc, var);
+  }
+  prob[e] = prefactor * (ms + mc) / nperm;
+  err[e] = prefactor * sqrt(vs + vc) / nperm;
+  if (n_used) n_used[e] = n_per_item * (uint64_t)nperm;
+  if (status) status[e] = invalid ? MEM_ERR_INVALID_ARG : (nbad ? MEM_ERR_NONFINITE : MEM_OK);
+}
+
+cudaError_t launch_final(const Slot* slots, int64_t n_events, int nperm, uint32_t cpi,
+                         uint32_t n_main, uint64_t n_per_item, double prefactor, double* prob,
+                         double* err, uint64_t* n_used, int32_t* status, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((n_events + 127) / 128);
+  k_final<<<blocks, 128, 0, st>>>(slots, n_events, nperm, cpi, n_main, n_per_item, prefactor,
+                                  prob, err, n_used, status);
+  return cudaGetLastError();
+}
+
+__global__ void k_philox(uint64_t seed, uint32_t eid, uint32_t perm, uint32_t point0, int64_t n,
+                         int d, float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int b = 0; 4 * b < d; ++b) {
+    const u32x4 o = philox4x32_10(point0 + (uint32_t)i, (uint32_t)b << 8, eid, perm, k0, k1);
+    const uint32_t w[4] = {o.a, o.b, o.c, o.d};
+    for (int j = 0; j < 4 && 4 * b + j < d; ++j) out[i * d + 4 * b + j] = u01(w[j]);
+  }
+}
+
+__global__ void k_refine(int d, const double* __restrict__ hist, const double* __restrict__ gin,
+                         double alpha, double* __restrict__ gout) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  double* g = reinterpret_cast<double*>(raw);           // d x (NG+1)
+  double* h = g + d * (NG + 1);                         // d x NG
+  double* wk = h + d * NG;                              // d x NG
+  double* cum = wk + d * NG;                            // d x (NG+1)
+  double* ng = cum + d * (NG + 1);                      // d x (NG+1)
+  const size_t gi = blockIdx.x;
+  for (int t = threadIdx.x; t < d * (NG + 1); t += blockDim.x) g[t] = gin[gi * d * (NG + 1) + t];
+  for (int t = threadIdx.x; t < d * NG; t += blockDim.x) h[t] = hist[gi * d * NG + t];
+  __syncthreads();
+  const int j = threadIdx.x >> 5;
+  if (j < d)
+    refine_dim_warp(g + j * (NG + 1), h + j * NG, wk + j * NG, cum + j * (NG + 1),
+                    ng + j * (NG + 1), alpha);
+  __syncthreads();
+  for (int t = threadIdx.x; t < d * (NG + 1); t += blockDim.x) gout[gi * d * (NG + 1) + t] = g[t];
+}
+
+// Process constants in FP64, rounded once.
+ProcConst make_proc_const(const mem_process_desc& d) {
+  ProcConst P;
+  std::memset(&P, 0, sizeof(P));
+  P.kind = d.kind;
+  const double s = d.sqrt_s * d.sqrt_s;
+  P.sqrt_s = (float)d.sqrt_s;
+  P.s = (float)s;
+  P.mz2 = (float)(d.mz * d.mz);
+  P.mz2_lo = (float)(d.mz * d.mz - (double)P.mz2);
+  P.mzgz = (float)(d.mz * d.wz);
+  P.mw2 = (float)(d.mw * d.mw);
+  P.mwgw = (float)(d.mw * d.ww);
+  P.mt2 = (float)(d.mt * d.mt);
+  P.mtgt = (float)(d.mt * d.wt);
+  const double e2 = 4.0 * PI_D * d.alpha;
+  const double gz = std::sqrt(e2 / (d.sw2 * (1.0 - d.sw2)));
+  const double Ql = -1.0, T3l = -0.5;
+  const double gl[2] = {gz * (T3l - Ql * d.sw2), gz * (-Ql * d.sw2)};
+  double same[3] = {0, 0, 0}, opp[3] = {0, 0, 0};
+  for (int fl = 0; fl < 2; ++fl) {
+    const double Qq = fl == 0 ? 2.0 / 3.0 : -1.0 / 3.0, T3q = fl == 0 ? 0.5 : -0.5;
+    const double gq[2] = {gz * (T3q - Qq * d.sw2), gz * (-Qq * d.sw2)};
+    const double cg = e2 * Qq * Ql;
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        double* acc = (a == b) ? same : opp;
+        acc[0] += cg * cg;
+        acc[1] += 2.0 * cg * gq[a] * gl[b];
+        acc[2] += (gq[a] * gl[b]) * (gq[a] * gl[b]);
+      }
+  }
+  for (int i = 0; i < 3; ++i) {
+    P.dy_same[i] = (float)same[i];
+    P.dy_opp[i] = (float)opp[i];
+  }
+  const double g2 = e2 / d.sw2;
+  P.w_coup = (float)(g2 * g2 / 12.0);
+  const double gs2 = 4.0 * PI_D * d.alpha_s;
+  // ttbar: g_s^4 (g^2/2)^4 x 64 (Fierz) x 6 (W- -> q qbar': colour x 2 generations) x averages
+  const double tt = gs2 * gs2 * std::pow(0.5 * g2, 4) * 64.0 * 6.0;
+  P.tt_gg = (float)(tt / (4.0 * 64.0));
+  P.tt_qq = (float)(tt / (4.0 * 9.0));
+  for (int t = 0; t < 3; ++t) {
+    P.pdfA[t] = (float)d.pdf_A[t];
+    P.pdfa[t] = (float)d.pdf_a[t];
+    P.pdfb[t] = (float)d.pdf_b[t];
+    P.pdf_amode[t] = d.pdf_a[t] == -0.5 ? 1 : (d.pdf_a[t] == -1.0 ? 2 : 0);
+    const double b = d.pdf_b[t];
+    P.pdf_bint[t] = (b >= 0.0 && b <= 16.0 && b == std::floor(b)) ? (int)b : -1;
+  }
+  const double tp = 2.0 * PI_D;
+  if (d.kind == PROC_DY) P.prefactor = (2.0 / s) / (4.0 * tp * tp);
+  else if (d.kind == PROC_W) P.prefactor = (2.0 / s) / (8.0 * tp * tp);
+  else P.prefactor = (2.0 / s) * std::pow(tp, 4.0 - 18.0) / 64.0;
+  return P;
+}
+
+TFConst make_tf_const(const mem_tf_desc& t) {
+  TFConst T;
+  T.lep_rel = (float)t.lep_rel;
+  T.window_k = (float)t.window_k;
+  T.jet_core = (float)t.jet_core;
+  T.jet_tail = (float)t.jet_tail;
+  T.jet_tail_w = (float)t.jet_tail_w;
+  T.jet_lo_div = (float)t.jet_lo_div;
+  T.jet_hi_mul = (float)t.jet_hi_mul;
+  T.met_sigma = (float)t.met_sigma;
+  T.met_box_k = (float)t.met_box_k;
+  return T;
+}
+
+}  // namespace mem
+
+using namespace mem;
+
+namespace {
+
+mem_status check_tf(const mem_tf_desc* tf, int kind) {
+  if (!tf) return fail(MEM_ERR_INVALID_ARG, "tf is NULL");
+  if (kind != PROC_TTBAR && !(tf->lep_rel > 0 && tf->window_k > 0 && tf->lep_rel * tf->window_k < 1))
+    return fail(MEM_ERR_INVALID_ARG, "lepton TF needs lep_rel > 0, window_k > 0, lep_rel*window_k < 1");
+  if (kind != PROC_DY && !(tf->met_sigma > 0 && tf->met_box_k > 0))
+    return fail(MEM_ERR_INVALID_ARG, "MET TF needs met_sigma > 0 and met_box_k > 0");
+  if (kind == PROC_TTBAR &&
+      !(tf->jet_core > 0 && tf->jet_tail > 0 && tf->jet_tail_w >= 0 && tf->jet_tail_w <= 1 &&
+        tf->jet_lo_div > 1 && tf->jet_hi_mul > 1))
+    return fail(MEM_ERR_INVALID_ARG, "invalid jet TF parameters");
+  return MEM_OK;
+}
+
+// Host grid d x 129 (FP64) -> device FP32 bins (left edge, width).
+std::vector<GridBin> host_bins(const double* grid, int d) {
+  std::vector<GridBin> gb((size_t)d * NG);
+  for (int j = 0; j < d; ++j)
+    for (int i = 0; i < NG; ++i) {
+      const double a = grid ? grid[j * (NG + 1) + i] : (double)i / NG;
+      const double b = grid ? grid[j * (NG + 1) + i + 1] : (double)(i + 1) / NG;
+      gb[(size_t)j * NG + i] = {(float)a, (float)(b - a), (float)(1.0 - b), 0.f};
+    }
+  return gb;
+}
+
+bool grid_valid(const double* grid, int d) {
+  for (int j = 0; j < d; ++j) {
+    const double* g = grid + j * (NG + 1);
+    if (g[0] != 0.0 || g[NG] != 1.0) return false;
+    for (int i = 0; i < NG; ++i)
+      if (!(g[i + 1] > g[i])) return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t mem_process_dims(int32_t kind) { return dims_of(kind); }
+int32_t mem_process_nperm(int32_t kind) { return nperm_of(kind); }
+
+const char* mem_last_error(void) { return g_err.c_str(); }
+
+mem_status mem_create_process(const mem_process_desc* desc, mem_process** out) {
+  if (!desc || !out) return fail(MEM_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (dims_of(desc->kind) < 0) return fail(MEM_ERR_INVALID_ARG, "unknown process kind");
+  if (desc->reserved != 0) return fail(MEM_ERR_INVALID_ARG, "reserved field must be 0");
+  const double v[] = {desc->sqrt_s, desc->mz, desc->wz, desc->mw, desc->ww, desc->mt,
+                      desc->wt, desc->alpha, desc->sw2, desc->alpha_s};
+  for (double x : v)
+    if (!(x > 0.0) || !std::isfinite(x)) return fail(MEM_ERR_INVALID_ARG, "masses, widths, couplings and sqrt_s must be positive");
+  if (!(desc->sw2 < 1.0)) return fail(MEM_ERR_INVALID_ARG, "sw2 must be < 1");
+  for (int t = 0; t < 3; ++t)
+    if (!(desc->pdf_A[t] > 0.0) || !std::isfinite(desc->pdf_a[t]) || !(desc->pdf_b[t] >= 0.0))
+      return fail(MEM_ERR_INVALID_ARG, "PDF parameters need A > 0, finite a, b >= 0");
+  mem_process* p = new mem_process;
+  p->magic = MAGIC_PROC;
+  p->desc = *desc;
+  p->pc = make_proc_const(*desc);
+  *out = p;
+  return MEM_OK;
+}
+
+mem_status mem_upload_events(mem_process* proc, const float* records, int64_t n_events,
+                             int32_t records_on_device, void* stream, mem_events** out) {
+  if (!proc || proc->magic != MAGIC_PROC || !records || !out)
+    return fail(MEM_ERR_INVALID_ARG, "NULL or invalid argument");
+  *out = nullptr;
+  if (n_events < 1) return fail(MEM_ERR_INVALID_ARG, "n_events must be >= 1");
+  if (n_events > (int64_t)1 << 31) return fail(MEM_ERR_INVALID_ARG, "n_events above 2^31");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)n_events * REC * sizeof(float);
+  if (!records_on_device) {
+    for (int64_t i = 0; i < n_events; ++i)
+      if (records[i * REC + 27] != (float)proc->desc.kind)
+        return fail(MEM_ERR_INVALID_ARG, "event " + std::to_string(i) + " is not of the process kind");
+  }
+  int dev = 0;
+  MEM_CK(cudaGetDevice(&dev));
+  float* d = nullptr;
+  MEM_CK(cudaMalloc(&d, bytes));
+  cudaError_t e = cudaMemcpyAsync(d, records, bytes,
+                                  records_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return cuda_fail(e, "event upload");
+  }
+  mem_events* ev = new mem_events;
+  ev->magic = MAGIC_EVT;
+  ev->kind = proc->desc.kind;
+  ev->n = n_events;
+  ev->device = dev;
+  ev->d_recs = d;
+  *out = ev;
+  return MEM_OK;
+}
+
+void mem_destroy(void* handle) {
+  if (!handle) return;
+  const uint32_t m = *reinterpret_cast<uint32_t*>(handle);
+  if (m == MAGIC_PROC) {
+    mem_process* p = reinterpret_cast<mem_process*>(handle);
+    p->magic = 0;
+    delete p;
+  } else if (m == MAGIC_EVT) {
+    mem_events* e = reinterpret_cast<mem_events*>(handle);
+    cudaFree(e->d_recs);
+    e->magic = 0;
+    delete e;
+  }
+}
+
+mem_status mem_integrate(const mem_events* ev, const mem_process* proc, const mem_tf_desc* tf,
+                         uint64_t n_points, uint64_t seed, const mem_opts* opts, double* prob,
+                         double* err, uint64_t* n_used, int32_t* ev_status, void* stream) {
+  if (!ev || ev->magic != MAGIC_EVT || !proc || proc->magic != MAGIC_PROC || !prob || !err)
+    return fail(MEM_ERR_INVALID_ARG, "NULL or invalid handle/output");
+  if (ev->kind != proc->desc.kind) return fail(MEM_ERR_INVALID_ARG, "events were uploaded for another process kind");
+  const int kind = proc->desc.kind;
+  mem_status s = check_tf(tf, kind);
+  if (s != MEM_OK) return s;
+  const int d = dims_of(kind), np = nperm_of(kind);
+  int iters = opts ? opts->n_adapt_iters : 5;
+  if (iters < 0 || iters > 64) return fail(MEM_ERR_INVALID_ARG, "n_adapt_iters out of range [0, 64]");
+  if (opts && opts->reserved0 != 0) return fail(MEM_ERR_INVALID_ARG, "reserved0 must be 0");
+  if (opts && opts->target_rel_err > 0.0) return fail(MEM_ERR_INVALID_ARG, "adaptive budgets are served by the batched integrator");
+  uint64_t na = opts && opts->adapt_points ? opts->adapt_points : (n_points / 8 < 16384 ? n_points / 8 : 16384);
+  if (iters == 0) na = 0;
+  if (n_points > ((uint64_t)1 << 32)) return fail(MEM_ERR_INVALID_ARG, "n_points above 2^32 per item");
+  if (iters > 0 && na < 1) return fail(MEM_ERR_INVALID_ARG, "adaptation needs >= 1 point per iteration");
+  if (n_points < (uint64_t)iters * na + 2)
+    return fail(MEM_ERR_INVALID_ARG, "n_points too small for the adaptation plan (need > iters*adapt_points + 1)");
+  const double alpha = opts && opts->alpha > 0.0 ? opts->alpha : 1.5;
+  const uint64_t eid_base = opts ? opts->event_id_base : 0;
+  if (opts && opts->grid_in && !grid_valid(opts->grid_in, d))
+    return fail(MEM_ERR_INVALID_ARG, "grid_in must have edges 0 = x0 < x1 < ... < x128 = 1 per dimension");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n_items = ev->n * np;
+  const uint32_t n_main = (uint32_t)(n_points - (uint64_t)iters * na);
+  const uint32_t cp = chunk_points(kind);
+  const uint32_t cpi = (n_main + cp - 1) / cp;
+
+  IntegrateArgs a;
+  a.recs = ev->d_recs;
+  a.n_events = ev->n;
+  a.n_items = n_items;
+  a.P = proc->pc;
+  a.T = make_tf_const(*tf);
+  a.seed = seed;
+  a.event_id_base = eid_base;
+  a.n_iters = iters;
+  a.n_adapt = (uint32_t)na;
+  a.alpha = alpha;
+  a.idx0 = (uint32_t)((uint64_t)iters * na);
+  a.n_main = n_main;
+  a.chunks_per_item = cpi;
+  a.phase_events = opts ? reinterpret_cast<cudaEvent_t*>(opts->phase_events) : nullptr;
+
+  const bool dev_out = is_device_ptr(prob);
+  const size_t grid_bytes = (size_t)n_items * d * NG * sizeof(GridBin);
+  const size_t slot_bytes = (size_t)n_items * cpi * sizeof(Slot);
+  const size_t out_bytes = dev_out ? 0 : (size_t)ev->n * (2 * sizeof(double) + sizeof(uint64_t) + sizeof(int32_t));
+  const size_t gin_bytes = opts && opts->grid_in ? (size_t)d * (NG + 1) * sizeof(double) : 0;
+  unsigned char* ws = nullptr;
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t out_each = dev_out ? 0 : up(ev->n * sizeof(double)) * 3 + up(ev->n * sizeof(int32_t));
+  const size_t cache_total = (size_t)n_items * cache_size(kind);
+  const size_t total = up(grid_bytes) + up(slot_bytes) + out_each + up(gin_bytes) + up(cache_total);
+  (void)out_bytes;
+  MEM_CK(cudaMallocAsync((void**)&ws, total, st));
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    unsigned char* p = ws + off;
+    off += (b + 255) & ~(size_t)255;
+    return p;
+  };
+  a.grid32 = reinterpret_cast<GridBin*>(take(grid_bytes));
+  a.slots = reinterpret_cast<Slot*>(take(slot_bytes));
+  a.caches = take(cache_total);
+  double* o_prob = prob;
+  double* o_err = err;
+  uint64_t* o_used = n_used;
+  int32_t* o_st = ev_status;
+  if (!dev_out) {
+    o_prob = reinterpret_cast<double*>(take(ev->n * sizeof(double)));
+    o_err = reinterpret_cast<double*>(take(ev->n * sizeof(double)));
+    o_used = reinterpret_cast<uint64_t*>(take(ev->n * sizeof(uint64_t)));
+    o_st = reinterpret_cast<int32_t*>(take(ev->n * sizeof(int32_t)));
+  }
+  a.grid_in = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (gin_bytes) {
+    double* g = reinterpret_cast<double*>(take(gin_bytes));
+    e = cudaMemcpyAsync(g, opts->grid_in, gin_bytes, cudaMemcpyHostToDevice, st);
+    a.grid_in = g;
+  }
+  if (e == cudaSuccess) e = launch_integrate(kind, a, st);
+  if (e == cudaSuccess && a.phase_events) e = cudaEventRecord(a.phase_events[2], st);
+  if (e == cudaSuccess)
+    e = launch_final(a.slots, ev->n, np, cpi, n_main, n_points, proc->pc.prefactor, o_prob, o_err,
+                     o_used, o_st, st);
+  if (e == cudaSuccess && a.phase_events) e = cudaEventRecord(a.phase_events[3], st);
+  if (e == cudaSuccess && !dev_out) {
+    e = cudaMemcpyAsync(prob, o_prob, ev->n * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(err, o_err, ev->n * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && n_used) e = cudaMemcpyAsync(n_used, o_used, ev->n * sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && ev_status) e = cudaMemcpyAsync(ev_status, o_st, ev->n * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  }
+  cudaError_t e2 = cudaFreeAsync(ws, st);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess && !dev_out) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "mem_integrate");
+  return MEM_OK;
+}
+
+mem_status mem_eval_points(const mem_events* ev, const mem_process* proc, const mem_tf_desc* tf,
+                           int64_t event_index, int32_t perm, uint64_t seed, uint64_t point0,
+                           int64_t n, const double* grid, double* w_out, void* stream) {
+  if (!ev || ev->magic != MAGIC_EVT || !proc || proc->magic != MAGIC_PROC || !w_out)
+    return fail(MEM_ERR_INVALID_ARG, "NULL or invalid handle/output");
+  if (ev->kind != proc->desc.kind) return fail(MEM_ERR_INVALID_ARG, "process kind mismatch");
+  const int kind = proc->desc.kind;
+  mem_status s = check_tf(tf, kind);
+  if (s != MEM_OK) return s;
+  if (event_index < 0 || event_index >= ev->n) return fail(MEM_ERR_INVALID_ARG, "event_index out of range");
+  if (perm < 0 || perm >= nperm_of(kind)) return fail(MEM_ERR_INVALID_ARG, "perm out of range");
+  if (n < 1 || point0 + (uint64_t)n > ((uint64_t)1 << 32)) return fail(MEM_ERR_INVALID_ARG, "bad point range");
+  const int d = dims_of(kind);
+  if (grid && !grid_valid(grid, d)) return fail(MEM_ERR_INVALID_ARG, "invalid grid");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<GridBin> gb = host_bins(grid, d);
+  const bool dev_out = is_device_ptr(w_out);
+  const size_t gbytes = gb.size() * sizeof(GridBin);
+  unsigned char* ws = nullptr;
+  MEM_CK(cudaMallocAsync((void**)&ws, gbytes + (dev_out ? 0 : n * sizeof(double)) + 256, st));
+  GridBin* dgb = reinterpret_cast<GridBin*>(ws);
+  double* dw = dev_out ? w_out : reinterpret_cast<double*>(ws + ((gbytes + 255) & ~(size_t)255));
+  cudaError_t e = cudaMemcpyAsync(dgb, gb.data(), gbytes, cudaMemcpyHostToDevice, st);
+  EvalArgs a;
+  a.rec = ev->d_recs + event_index * REC;
+  a.perm = perm;
+  a.P = proc->pc;
+  a.T = make_tf_const(*tf);
+  a.seed = seed;
+  a.event_id = (uint32_t)event_index;
+  a.point0 = (uint32_t)point0;
+  a.n = n;
+  a.gb = dgb;
+  a.w_out = dw;
+  if (e == cudaSuccess) e = launch_eval(kind, a, st);
+  if (e == cudaSuccess && !dev_out) e = cudaMemcpyAsync(w_out, dw, n * sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaError_t e2 = cudaFreeAsync(ws, st);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "mem_eval_points");
+  return MEM_OK;
+}
+
+mem_status mem_philox_uniforms(uint64_t seed, uint64_t event_id, int32_t perm, uint64_t point0,
+                               int64_t n, int32_t d, float* out, void* stream) {
+  if (!out || n < 1 || d < 1 || d > MAXD || perm < 0 || point0 + (uint64_t)n > ((uint64_t)1 << 32))
+    return fail(MEM_ERR_INVALID_ARG, "invalid argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool dev_out = is_device_ptr(out);
+  float* buf = out;
+  if (!dev_out) MEM_CK(cudaMallocAsync((void**)&buf, (size_t)n * d * sizeof(float), st));
+  k_philox<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(seed, (uint32_t)event_id, (uint32_t)perm,
+                                                        (uint32_t)point0, n, d, buf);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && !dev_out) {
+    e = cudaMemcpyAsync(out, buf, (size_t)n * d * sizeof(float), cudaMemcpyDeviceToHost, st);
+    cudaError_t e2 = cudaFreeAsync(buf, st);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "mem_philox_uniforms");
+  return MEM_OK;
+}
+
+mem_status mem_vegas_refine(int32_t n_grids, int32_t d, const double* hist, const double* grid_in,
+                            double alpha, double* grid_out) {
+  if (n_grids < 1 || d < 1 || d > MAXD || !hist || !grid_in || !grid_out || !(alpha > 0))
+    return fail(MEM_ERR_INVALID_ARG, "invalid argument");
+  const size_t gb = (size_t)n_grids * d * (NG + 1) * sizeof(double);
+  const size_t hb = (size_t)n_grids * d * NG * sizeof(double);
+  double *dg = nullptr, *dh = nullptr, *do_ = nullptr;
+  MEM_CK(cudaMalloc(&dg, gb));
+  cudaError_t e = cudaMalloc(&dh, hb);
+  if (e == cudaSuccess) e = cudaMalloc(&do_, gb);
+  if (e == cudaSuccess) e = cudaMemcpy(dg, grid_in, gb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dh, hist, hb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const size_t smem = (size_t)d * (3 * (NG + 1) + 2 * NG) * sizeof(double);
+    e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+      k_refine<<<n_grids, 32 * d, smem>>>(d, dh, dg, alpha, do_);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(grid_out, do_, gb, cudaMemcpyDeviceToHost);
+  cudaFree(dg);
+  cudaFree(dh);
+  cudaFree(do_);
+  if (e != cudaSuccess) return cuda_fail(e, "mem_vegas_refine");
+  return MEM_OK;
+}
+
+}  // extern "C"

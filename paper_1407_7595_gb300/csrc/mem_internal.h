@@ -1,0 +1,69 @@
+// Host-side interface between the C ABI (mem_api.cu) and the per-process
+// kernel launchers (mem_launch_*.cu). Internal to libmem.so.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mem_common.cuh"
+#include "mem_physics.cuh"
+
+namespace mem {
+
+struct IntegrateArgs {
+  const float* recs;        // device, n_events x REC
+  int64_t n_events, n_items;
+  ProcConst P;
+  TFConst T;
+  uint64_t seed, event_id_base;
+  int n_iters;              // adaptation iterations
+  uint32_t n_adapt;         // points per item per adaptation iteration
+  double alpha;
+  const double* grid_in;    // device d x (NG+1) or nullptr
+  uint32_t idx0;            // first point index of the frozen-grid phase
+  uint32_t n_main;          // frozen-grid points per item
+  uint32_t chunks_per_item;
+  GridBin* grid32;          // device n_items x D x NG
+  void* caches;             // device n_items x sizeof(Phys::Cache): per-item constants
+  Slot* slots;              // device n_items x chunks_per_item
+  cudaEvent_t* phase_events;  // optional: 4 events (before adapt, main, final; after final)
+};
+
+struct EvalArgs {
+  const float* rec;         // device, one record
+  int perm;
+  ProcConst P;
+  TFConst T;
+  uint64_t seed;
+  uint32_t event_id, point0;
+  int64_t n;
+  const GridBin* gb;        // device D x NG
+  double* w_out;            // device
+};
+
+// Points per CTA of the frozen-grid kernel for a process kind.
+uint32_t chunk_points(int kind);
+int dims_of(int kind);
+int nperm_of(int kind);
+
+cudaError_t launch_integrate(int kind, const IntegrateArgs& a, cudaStream_t st);
+cudaError_t launch_eval(int kind, const EvalArgs& a, cudaStream_t st);
+
+// per-process entry points (defined in the launch translation units)
+cudaError_t launch_integrate_dy(const IntegrateArgs&, cudaStream_t);
+cudaError_t launch_integrate_w(const IntegrateArgs&, cudaStream_t);
+cudaError_t launch_integrate_tt(const IntegrateArgs&, cudaStream_t);
+cudaError_t launch_eval_dy(const EvalArgs&, cudaStream_t);
+cudaError_t launch_eval_w(const EvalArgs&, cudaStream_t);
+cudaError_t launch_eval_tt(const EvalArgs&, cudaStream_t);
+
+size_t cache_size_dy();
+size_t cache_size_w();
+size_t cache_size_tt();
+size_t cache_size(int kind);
+
+cudaError_t launch_final(const Slot* slots, int64_t n_events, int nperm, uint32_t cpi,
+                         uint32_t n_main, uint64_t n_per_item, double prefactor, double* prob,
+                         double* err, uint64_t* n_used, int32_t* status, cudaStream_t st);
+
+}  // namespace mem

@@ -1,0 +1,287 @@
+// Integration kernels, templated on the process physics (PhysDY, PhysW, PhysTT).
+//
+// One item = (event, jet permutation). Per item:
+//   k_adapt : one CTA runs the VEGAS adaptation iterations (Sec. 2, Lepage's
+//             algorithm): Philox points -> grid map -> integrand -> squared
+//             weights histogrammed in shared memory -> FP64 grid refinement
+//             (one warp per dimension) -> next iteration. Leaves the frozen
+//             FP32 grid of the item in global memory.
+//   k_main  : CTAs of CHUNK points each sample the frozen grid; each thread
+//             keeps FP32 Kahan sums of w and w^2, merged by FP64 TwoSum warp
+//             shuffles and a fixed-order CTA reduction into one slot.
+//   k_final : one thread per event reduces its slots in fixed order (FP64
+//             Neumaier), forms the plain MC mean and error (Sec. 2, Eq. "sum"),
+//             averages over permutations (Sec. 4) and applies the FP64 prefactor.
+#pragma once
+#include "mem_physics.cuh"
+
+namespace mem {
+
+constexpr int THREADS = 256;
+constexpr int WARPS = THREADS / 32;
+
+// ---------------------------------------------------------------------------
+// VEGAS refinement of one dimension by one warp, FP64 (Lepage 1978):
+// three-point smoothing of the bin importances h, normalisation,
+// compression w_i = ((1 - r_i)/ln(1/r_i))^alpha, re-binning to equal w per bin.
+// g: NG+1 edges (updated in place); h: NG importances; wk, cum: scratch.
+// ---------------------------------------------------------------------------
+__device__ inline void refine_dim_warp(double* g, const double* h, double* wk, double* cum,
+                                       double* newg, double alpha) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < NG; i += 32) {
+    double s;
+    if (i == 0) s = 0.5 * (h[0] + h[1]);
+    else if (i == NG - 1) s = 0.5 * (h[NG - 2] + h[NG - 1]);
+    else s = (h[i - 1] + h[i] + h[i + 1]) / 3.0;
+    wk[i] = s;
+  }
+  __syncwarp();
+  double tot = 0.0;
+  if (lane == 0) {
+    for (int i = 0; i < NG; ++i) tot += wk[i];
+  }
+  tot = __shfl_sync(0xffffffffu, tot, 0);
+  if (!(tot > 0.0)) return;
+  for (int i = lane; i < NG; i += 32) {
+    const double r = wk[i] / tot;
+    double w;
+    if (r <= 0.0) w = 0.0;
+    else if (r >= 1.0) w = 1.0;
+    else w = pow((1.0 - r) / log(1.0 / r), alpha);
+    wk[i] = w;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    double acc = 0.0;
+    cum[0] = 0.0;
+    for (int i = 0; i < NG; ++i) {
+      acc += wk[i];
+      cum[i + 1] = acc;
+    }
+  }
+  __syncwarp();
+  const double per = cum[NG] / NG;
+  for (int k = lane; k <= NG; k += 32) {
+    double e;
+    if (k == 0 || k == NG) {
+      e = g[k];
+    } else {
+      const double target = k * per;
+      // smallest i with cum[i] + w[i] >= target (i <= NG - 1)
+      int lo = 0, hi = NG - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (cum[mid] + wk[mid] < target) lo = mid + 1;
+        else hi = mid;
+      }
+      const int i = lo;
+      double frac = wk[i] > 0.0 ? (target - cum[i]) / wk[i] : 0.0;
+      frac = frac < 0.0 ? 0.0 : (frac > 1.0 ? 1.0 : frac);
+      e = g[i] + frac * (g[i + 1] - g[i]);
+    }
+    newg[k] = e;
+  }
+  __syncwarp();
+  for (int k = lane; k <= NG; k += 32) g[k] = newg[k];
+  __syncwarp();
+}
+
+template <int D>
+__device__ inline void grid_to_bins(const double* g /* D x (NG+1) */, GridBin* gb) {
+  for (int t = threadIdx.x; t < D * NG; t += blockDim.x) {
+    const int j = t / NG, i = t % NG;
+    const double a = g[j * (NG + 1) + i], b = g[j * (NG + 1) + i + 1];
+    gb[t].x0 = (float)a;
+    gb[t].w = (float)(b - a);
+    gb[t].xc = (float)(1.0 - b);
+    gb[t].pad = 0.f;
+  }
+}
+
+template <class PH>
+struct AdaptSmem {
+  typename PH::Cache cache;
+  double g[PH::D * (NG + 1)];
+  double h[PH::D * NG];
+  double wk[PH::D * NG];
+  double cum[PH::D * (NG + 1)];
+  double newg[PH::D * (NG + 1)];
+  GridBin gb[PH::D * NG];
+  float hist[PH::D * NG];
+};
+
+template <class PH>
+__global__ void __launch_bounds__(THREADS)
+k_adapt(const float* __restrict__ recs, ProcConst P, TFConst T, int64_t n_items,
+        uint64_t seed, uint64_t event_id_base, int n_iters, uint32_t n_adapt, double alpha,
+        const double* __restrict__ grid_in, GridBin* __restrict__ grid32,
+        typename PH::Cache* __restrict__ caches) {
+  constexpr int D = PH::D;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  AdaptSmem<PH>& S = *reinterpret_cast<AdaptSmem<PH>*>(smem_raw);
+  const int64_t item = blockIdx.x;
+  if (item >= n_items) return;
+  const int64_t ev = item / PH::NPERM;
+  const int perm = (int)(item % PH::NPERM);
+  const float* rec = recs + ev * REC;
+  if (threadIdx.x == 0) {
+    // per-item constants, computed once in FP64 and kept for the sampling kernel
+    PH::setup(rec, perm, P, T, S.cache);
+    caches[item] = S.cache;
+  }
+  for (int t = threadIdx.x; t < D * (NG + 1); t += blockDim.x)
+    S.g[t] = grid_in ? grid_in[t] : (double)(t % (NG + 1)) / NG;
+  __syncthreads();
+  grid_to_bins<D>(S.g, S.gb);
+  const uint32_t eid = (uint32_t)(event_id_base + (uint64_t)ev);
+  for (int it = 0; it < n_iters; ++it) {
+    for (int t = threadIdx.x; t < D * NG; t += blockDim.x) S.hist[t] = 0.f;
+    __syncthreads();
+    if (S.cache.ok) {
+      for (uint32_t k = threadIdx.x; k < n_adapt; k += blockDim.x) {
+        float u[D], x[D], xc[D];
+        int bin[D];
+        point_uniforms<D>(seed, eid, (uint32_t)perm, (uint32_t)it * n_adapt + k, u);
+        const float J = vegas_map<D>(S.gb, u, x, xc, bin);
+        const float w = PH::eval(S.cache, P, x, xc) * J;
+        if (isfinite(w)) {
+          const float w2 = w * w;
+#pragma unroll
+          for (int j = 0; j < D; ++j) atomicAdd(&S.hist[j * NG + bin[j]], w2);
+        }
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < D * NG; t += blockDim.x) S.h[t] = (double)S.hist[t];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5;
+    for (int j = warp; j < D; j += WARPS)
+      refine_dim_warp(S.g + j * (NG + 1), S.h + j * NG, S.wk + j * NG, S.cum + j * (NG + 1),
+                      S.newg + j * (NG + 1), alpha);
+    __syncthreads();
+    grid_to_bins<D>(S.g, S.gb);
+    __syncthreads();
+  }
+  GridBin* out = grid32 + item * (D * NG);
+  for (int t = threadIdx.x; t < D * NG; t += blockDim.x) out[t] = S.gb[t];
+}
+
+template <class PH>
+struct MainSmem {
+  typename PH::Cache cache;
+  GridBin gb[PH::D * NG];
+  DD red[2][WARPS];
+  uint32_t bad[WARPS];
+};
+
+// Sample the frozen grid: CTA b handles points [chunk*CHUNK, (chunk+1)*CHUNK)
+// of item b / chunks_per_item, main-phase point index offset idx0.
+template <class PH, int PPT, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
+k_main(const float* __restrict__ recs, ProcConst P, TFConst T, int64_t n_items,
+       uint32_t chunks_per_item, uint64_t seed, uint64_t event_id_base, uint32_t idx0,
+       uint32_t n_main, const GridBin* __restrict__ grid32,
+       const typename PH::Cache* __restrict__ caches, Slot* __restrict__ slots) {
+  constexpr int D = PH::D;
+  constexpr uint32_t CHUNK = THREADS * PPT;
+  __shared__ MainSmem<PH> S;
+  const int64_t item = blockIdx.x / chunks_per_item;
+  const uint32_t chunk = blockIdx.x % chunks_per_item;
+  if (item >= n_items) return;
+  const int64_t ev = item / PH::NPERM;
+  const int perm = (int)(item % PH::NPERM);
+  {
+    static_assert(sizeof(typename PH::Cache) % 4 == 0, "cache must be word sized");
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(caches + item);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&S.cache);
+    for (int t = threadIdx.x; t < (int)(sizeof(typename PH::Cache) / 4); t += blockDim.x)
+      dst[t] = src[t];
+  }
+  const GridBin* gsrc = grid32 + item * (D * NG);
+  for (int t = threadIdx.x; t < D * NG; t += blockDim.x) S.gb[t] = gsrc[t];
+  __syncthreads();
+  const uint32_t eid = (uint32_t)(event_id_base + (uint64_t)ev);
+  Kahan32 a1, a2;
+  uint32_t nbad = 0;
+  if (S.cache.ok) {
+    const uint32_t base = chunk * CHUNK;
+#pragma unroll 1
+    for (int j = 0; j < PPT; ++j) {
+      const uint32_t p = base + (uint32_t)j * THREADS + threadIdx.x;
+      if (p < n_main) {
+        float u[D], x[D], xc[D];
+        int bin[D];
+        point_uniforms<D>(seed, eid, (uint32_t)perm, idx0 + p, u);
+        const float J = vegas_map<D>(S.gb, u, x, xc, bin);
+        const float w = PH::eval(S.cache, P, x, xc) * J;
+        if (isfinite(w)) {
+          a1.add(w);
+          a2.add(w * w);
+        } else {
+          ++nbad;
+        }
+      }
+    }
+  }
+  // Kahan state (s, c) represents s - c
+  DD v1 = {(double)a1.s, -(double)a1.c}, v2 = {(double)a2.s, -(double)a2.c};
+  v1 = warp_reduce_dd(v1);
+  v2 = warp_reduce_dd(v2);
+  for (int o = 16; o > 0; o >>= 1) nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    S.red[0][warp] = v1;
+    S.red[1][warp] = v2;
+    S.bad[warp] = nbad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    DD s1 = S.red[0][0], s2 = S.red[1][0];
+    uint32_t b = S.bad[0];
+    for (int w = 1; w < WARPS; ++w) {
+      s1 = two_sum_merge(s1, S.red[0][w]);
+      s2 = two_sum_merge(s2, S.red[1][w]);
+      b += S.bad[w];
+    }
+    Slot sl;
+    sl.s1 = s1.hi;
+    sl.c1 = s1.lo;
+    sl.s2 = s2.hi;
+    sl.c2 = s2.lo;
+    sl.n_bad = b | (S.cache.ok ? 0u : 0x80000000u);
+    sl.pad = 0;
+    slots[blockIdx.x] = sl;
+  }
+}
+
+// Per event: fixed-order FP64 reduction of the item slots, MC mean and error
+// per item, average over permutations, FP64 prefactor.
+__global__ void k_final(const Slot* __restrict__ slots, int64_t n_events, int nperm,
+                        uint32_t chunks_per_item, uint32_t n_main, uint64_t n_per_item,
+                        double prefactor, double* __restrict__ prob, double* __restrict__ err,
+                        uint64_t* __restrict__ n_used, int32_t* __restrict__ status);
+
+// Integrand at consecutive points of one item (parity tests): one thread per point.
+template <class PH>
+__global__ void __launch_bounds__(THREADS)
+k_eval(const float* __restrict__ rec, int perm, ProcConst P, TFConst T, uint64_t seed,
+       uint32_t event_id, uint32_t point0, int64_t n, const GridBin* __restrict__ gb,
+       double* __restrict__ w_out) {
+  constexpr int D = PH::D;
+  __shared__ typename PH::Cache cache;
+  __shared__ GridBin sg[D * NG];
+  if (threadIdx.x == 0) PH::setup(rec, perm, P, T, cache);
+  for (int t = threadIdx.x; t < D * NG; t += blockDim.x) sg[t] = gb[t];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float u[D], x[D], xc[D];
+  int bin[D];
+  point_uniforms<D>(seed, event_id, (uint32_t)perm, point0 + (uint32_t)i, u);
+  const float J = vegas_map<D>(sg, u, x, xc, bin);
+  const float w = cache.ok ? PH::eval(cache, P, x, xc) * J : 0.f;
+  w_out[i] = (double)w * P.prefactor;
+}
+
+}  // namespace mem

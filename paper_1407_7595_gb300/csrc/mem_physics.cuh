@@ -1,0 +1,303 @@
+// FP32 integrands of the matrix-element method (Sec. 1 Eq. "mem_def" with the
+// transfer-function convolution; Sec. 3 Eq. "integrand"), one per process,
+// written for throughput and FP32 accuracy:
+//  * every quantity that would be a difference of nearly equal numbers is
+//    formed from per-event constants computed once in FP64 (1 - tanh(eta),
+//    1 - n1.n2, ...) or from the map variables directly;
+//  * Breit-Wigner propagators are cancelled analytically against the
+//    Jacobians of their maps (dq^2/dv / |D|^2 = R / (m G));
+//  * constant factors ((2 pi)^k, 2/s) are kept out of the FP32 weight and
+//    applied in FP64 (ProcConst::prefactor).
+#pragma once
+#include "mem_common.cuh"
+
+namespace mem {
+
+enum { PROC_DY = 0, PROC_W = 1, PROC_TTBAR = 2 };
+
+// Constants of a process, built on the host in FP64 and rounded once.
+struct ProcConst {
+  int kind;
+  float sqrt_s, s;
+  float mz2, mzgz, mw2, mwgw, mt2, mtgt;
+  float mz2_lo;             // m_Z^2 - mz2 (the pole position to ~1e-14 relative)
+  // Drell-Yan: sum over u and d of the chirality-combination coefficients of
+  // sum |A_ab|^2 = a/s^2 + b Re(chi)/s + c |chi|^2, for a = b (same) and a != b (opp).
+  float dy_same[3], dy_opp[3];
+  float w_coup;             // W: g^4 / 12
+  float tt_gg, tt_qq;       // ttbar: couplings x colour x averaging factors
+  float pdfA[3], pdfa[3], pdfb[3];
+  int pdf_amode[3];         // 1: x^-1/2, 2: x^-1, 0: general power
+  int pdf_bint[3];          // integer exponent of (1-x) if >= 0, else general power
+  double prefactor;         // FP64 constant multiplying every FP32 weight
+};
+
+struct TFConst {
+  float lep_rel, window_k;
+  float jet_core, jet_tail, jet_tail_w, jet_lo_div, jet_hi_mul;
+  float met_sigma, met_box_k;
+};
+
+// Parametric PDF f(x) = A x^a (1-x)^b (Eq. "mem_def" f1, f2), zero outside (0,1).
+__device__ __forceinline__ float pdf(const ProcConst& P, int t, float x) {
+  if (!(x > 0.f && x < 1.f)) return 0.f;
+  const float y = 1.f - x;
+  float fa;
+  if (P.pdf_amode[t] == 1) fa = rsqrtf(x);
+  else if (P.pdf_amode[t] == 2) fa = 1.f / x;
+  else fa = exp2f(P.pdfa[t] * log2f(x));
+  float fb = 1.f;
+  const int bi = P.pdf_bint[t];
+  if (bi >= 0) {
+    for (int k = 0; k < bi; ++k) fb *= y;
+  } else {
+    fb = exp2f(P.pdfb[t] * log2f(y));
+  }
+  return P.pdfA[t] * fa * fb;
+}
+
+// Per-object constants, computed in FP64 from (E, eta, phi) once per item.
+struct ObjC {
+  float E;               // measured energy
+  float nx, ny, nz;      // direction
+  float sin_t;           // 1/cosh(eta)
+  float lc_m, lc_p;      // 1 - tanh(eta), 1 + tanh(eta): (E - pz)/E, (E + pz)/E
+  float om_sin;          // 1 - sin(theta)
+};
+
+__device__ inline ObjC make_obj(const float* rec, int o) {
+  const double E = rec[4 * o], eta = rec[4 * o + 1], phi = rec[4 * o + 2];
+  const double ch = cosh(eta), th = tanh(eta);
+  ObjC c;
+  c.E = (float)E;
+  c.nx = (float)(cos(phi) / ch);
+  c.ny = (float)(sin(phi) / ch);
+  c.nz = (float)th;
+  c.sin_t = (float)(1.0 / ch);
+  c.lc_m = (float)(exp(-eta) / ch);   // 1 - tanh(eta) without cancellation
+  c.lc_p = (float)(exp(eta) / ch);    // 1 + tanh(eta)
+  c.om_sin = (float)((ch - 1.0) / ch);
+  return c;
+}
+
+// Transverse boost of the final state to zero total pT (the recoil absorbed
+// by a flat transverse-momentum transfer function): given the total energy E,
+// total pT^2 and pz, and the invariant mass squared shat (known accurately
+// from the map), returns gamma - 1, gamma, beta and the parton fractions.
+struct Boost {
+  float gm1, gam, bx, by, x1, x2;
+};
+
+__device__ __forceinline__ Boost transverse_boost(float E, float px, float py, float pz,
+                                                  float shat, const ProcConst& P) {
+  Boost b;
+  const float pt2 = fmaf(px, px, py * py);
+  const float Ep = sqrtf(fmaf(pz, pz, shat));       // energy after the boost
+  b.gm1 = pt2 / (Ep * (E + Ep));                     // gamma - 1 = (E - E')/E'
+  b.gam = 1.f + b.gm1;
+  const float iE = 1.f / E;
+  b.bx = px * iE;
+  b.by = py * iE;
+  const float inv_rs = 1.f / P.sqrt_s;
+  // x1 x2 s = shat: take the larger one directly and the smaller from the product
+  if (pz >= 0.f) {
+    b.x1 = (Ep + pz) * inv_rs;
+    b.x2 = shat / (P.s * b.x1);
+  } else {
+    b.x2 = (Ep - pz) * inv_rs;
+    b.x1 = shat / (P.s * b.x2);
+  }
+  return b;
+}
+
+// Light-cone components E' -+ pz of a massless object of lab energy E along n
+// after the transverse boost: E [(1 -+ tanh eta) + (gamma - 1)] - gamma beta.pT.
+__device__ __forceinline__ void light_cone(const ObjC& o, float E, const Boost& b, float& lm,
+                                           float& lp) {
+  const float bn = b.gam * fmaf(b.bx, o.nx, b.by * o.ny);
+  lm = E * ((o.lc_m + b.gm1) - bn);
+  lp = E * ((o.lc_p + b.gm1) - bn);
+}
+
+// ---------------------------------------------------------------------------
+// Drell-Yan: q qbar -> photon/Z -> mu- mu+, muon energies integrated (d = 2)
+// ---------------------------------------------------------------------------
+struct DYCache {
+  ObjC o[2];               // mu-, mu+
+  float Elo[2];            // lower window edges Em/(1 + k r)
+  float L;                 // log((1 + k r)/(1 - k r))
+  float kr, r;
+  float omc;               // 1 - n_mu-.n_mu+
+  float K;                 // 2 Elo_1 Elo_2 (1 - n1.n2): shat = K (1 + em_1)(1 + em_2)
+  float K_mz2;             // K - m_Z^2, formed in FP64 (the Z pole is not shifted by rounding)
+  float cst;               // sin(theta_1) sin(theta_2) L^2 / (2 pi r^2)
+  int ok;
+};
+
+struct PhysDY {
+  static constexpr int D = 2;
+  static constexpr int NPERM = 1;
+  using Cache = DYCache;
+
+  __device__ static void setup(const float* rec, int, const ProcConst& P, const TFConst& T,
+                               Cache& c) {
+    const double r = T.lep_rel, kr = T.window_k * T.lep_rel;
+    c.ok = (rec[3] == 1.f && rec[7] == 2.f && kr < 1.0 && rec[0] > 0.f && rec[4] > 0.f);
+    for (int i = 0; i < 2; ++i) {
+      c.o[i] = make_obj(rec, i);
+      c.Elo[i] = (float)(rec[4 * i] / (1.0 + kr));
+    }
+    const double L = log((1.0 + kr) / (1.0 - kr));
+    c.L = (float)L;
+    c.kr = (float)kr;
+    c.r = (float)r;
+    // 1 - cos(angle) from the (eta, phi) of both muons in FP64
+    const double e0 = rec[1], p0 = rec[2], e1 = rec[5], p1 = rec[6];
+    const double ch0 = cosh(e0), ch1 = cosh(e1);
+    const double cosang = (cos(p0 - p1) + sinh(e0) * sinh(e1)) / (ch0 * ch1);
+    c.omc = (float)(1.0 - cosang);
+    const double K = 2.0 * ((double)rec[0] / (1.0 + kr)) * ((double)rec[4] / (1.0 + kr)) *
+                     (1.0 - cosang);
+    const double mz2 = (double)P.mz2 + (double)P.mz2_lo;
+    c.K = (float)K;
+    c.K_mz2 = (float)(K - mz2);
+    c.cst = (float)((1.0 / ch0) * (1.0 / ch1) * L * L / (2.0 * PI_D * r * r));
+  }
+
+  __device__ static float eval(const Cache& c, const ProcConst& P, const float (&x)[D],
+                               const float (&)[D]) {
+    float E[2], em[2], z2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      em[i] = expm1_small(x[i] * c.L);               // E = Elo e^{xL}
+      E[i] = c.Elo[i] * (1.f + em[i]);
+      const float z = (c.kr - em[i]) / (c.r * (1.f + em[i]));  // (Em - E)/(r E)
+      z2 = fmaf(z, z, z2);
+    }
+    // shat = K (1 + eps), eps = (1+em1)(1+em2) - 1 formed without cancellation
+    const float eps = fmaf(em[0], em[1], em[0] + em[1]);
+    const float shat = fmaf(c.K, eps, c.K);
+    const float px = E[0] * c.o[0].nx + E[1] * c.o[1].nx;
+    const float py = E[0] * c.o[0].ny + E[1] * c.o[1].ny;
+    const float pz = E[0] * c.o[0].nz + E[1] * c.o[1].nz;
+    const Boost b = transverse_boost(E[0] + E[1], px, py, pz, shat, P);
+    if (!(b.x1 < 1.f && b.x2 < 1.f)) return 0.f;
+    float lm0, lp0, lm1, lp1;
+    light_cone(c.o[0], E[0], b, lm0, lp0);
+    light_cone(c.o[1], E[1], b, lm1, lp1);
+    const float k1 = b.x1 * P.sqrt_s;
+    const float t = -k1 * lm0;  // (k1 - p_mu-)^2
+    const float u = -k1 * lm1;  // (k1 - p_mu+)^2
+    const float dre = fmaf(c.K, eps, c.K_mz2);  // shat - m_Z^2
+    const float inv_den = 1.f / fmaf(dre, dre, P.mzgz * P.mzgz);
+    const float is = 1.f / shat;
+    const float S = fmaf(P.dy_same[0] * is, is, fmaf(P.dy_same[1] * dre, inv_den * is,
+                                                     P.dy_same[2] * inv_den));
+    const float O = fmaf(P.dy_opp[0] * is, is, fmaf(P.dy_opp[1] * dre, inv_den * is,
+                                                    P.dy_opp[2] * inv_den));
+    const float mA = fmaf(u * u, S, t * t * O);  // quark from beam 1
+    const float mB = fmaf(t * t, S, u * u * O);  // quark from beam 2: t <-> u
+    const float fl = pdf(P, 0, b.x1) * pdf(P, 1, b.x2) * mA + pdf(P, 1, b.x1) * pdf(P, 0, b.x2) * mB;
+    return c.cst * E[0] * E[1] * __expf(-0.5f * z2) * (4.f * is) * fl * (1.f / 3.f);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// W -> e nu: electron energy, neutrino px, py (MET box) and q^2_W (d = 4);
+// neutrino pz from the W mass constraint, both roots summed.
+// ---------------------------------------------------------------------------
+struct WCache {
+  ObjC e;
+  float Elo, L, kr, r;
+  float metx, mety, B, kbox;
+  float hi_s;        // upper end of the q^2 range (s)
+  float psi_hi;      // atan2(m_W G_W, s - m_W^2)
+  float cst;
+  int charge;        // +1 e+, -1 e-
+  int ok;
+};
+
+struct PhysW {
+  static constexpr int D = 4;
+  static constexpr int NPERM = 1;
+  using Cache = WCache;
+
+  __device__ static void setup(const float* rec, int, const ProcConst& P, const TFConst& T,
+                               Cache& c) {
+    const double r = T.lep_rel, kr = T.window_k * T.lep_rel;
+    c.ok = ((rec[3] == 4.f || rec[3] == 3.f) && kr < 1.0 && rec[0] > 0.f && T.met_sigma > 0.f);
+    c.e = make_obj(rec, 0);
+    c.charge = rec[3] == 4.f ? 1 : -1;
+    c.Elo = (float)(rec[0] / (1.0 + kr));
+    const double L = log((1.0 + kr) / (1.0 - kr));
+    c.L = (float)L;
+    c.kr = (float)kr;
+    c.r = (float)r;
+    c.metx = rec[24];
+    c.mety = rec[25];
+    c.kbox = T.met_box_k;
+    c.B = (float)((double)T.met_box_k * T.met_sigma);
+    c.hi_s = P.s;
+    c.psi_hi = (float)atan2((double)P.mwgw, (double)P.s - (double)P.mw2);
+    const double k = T.met_box_k;
+    // sin(theta) L/(sqrt(2 pi) r)  x  (2k)^2/(2 pi)  x  g^4/12  x  2/(m G)
+    c.cst = (float)((1.0 / cosh((double)rec[1])) * L / (sqrt(2.0 * PI_D) * r) *
+                    (4.0 * k * k) / (2.0 * PI_D) * (double)P.w_coup * 2.0 / (double)P.mwgw);
+  }
+
+  __device__ static float eval(const Cache& c, const ProcConst& P, const float (&x)[D],
+                               const float (&xc)[D]) {
+    // electron energy (log map over the Gaussian window) and its TF argument
+    const float em = expm1_small(x[0] * c.L);
+    const float Ee = c.Elo * (1.f + em);
+    const float z = (c.kr - em) / (c.r * (1.f + em));
+    // neutrino transverse momentum in the MET box; TF argument (MET - pT_nu)/sigma
+    const float sx = fmaf(2.f, x[1], -1.f), sy = fmaf(2.f, x[2], -1.f);
+    const float nx = fmaf(c.B, sx, c.metx), ny = fmaf(c.B, sy, c.mety);
+    const float zm2 = c.kbox * c.kbox * fmaf(sx, sx, sy * sy);
+    // transverse mass: pTe pTnu - pTe.pTnu without cancellation
+    const float pex = Ee * c.e.nx, pey = Ee * c.e.ny, pez = Ee * c.e.nz;
+    const float pTe = Ee * c.e.sin_t;
+    const float pTn = sqrtf(fmaf(nx, nx, ny * ny));
+    const float prod = pTe * pTn;
+    const float dotT = fmaf(pex, nx, pey * ny);
+    const float cross = fmaf(pex, ny, -pey * nx);
+    const float h = dotT > 0.f ? cross * cross / (prod + dotT) : prod - dotT;
+    const float mt2 = 2.f * h;
+    // q^2_W: Breit-Wigner map over [mT^2, s] after v = t^2 (removes the
+    // 1/sqrt(q^2 - mT^2) endpoint singularity of the pz Jacobian)
+    const float t = x[3];
+    const BW bw = bw_map(mt2, c.hi_s - mt2, P.mw2, P.mwgw, t * t, xc[3] * (1.f + t), c.psi_hi);
+    const float half = 0.5f * bw.d_lo;
+    const float Dp = half * (half + 2.f * prod);       // discriminant, product form
+    const float sD = sqrtf(Dp);
+    const float a = half + prod;                       // q^2/2 + pTe.pTnu
+    const float pTe2 = pTe * pTe;
+    // stable roots: q = a pz_e + sign(pz_e) E_e sqrt(D'); pz1 = q/pTe^2, pz2 = c/q
+    const float qq = fmaf(a, pez, copysignf(Ee * sD, pez));
+    const float pz1 = qq / pTe2;
+    const float cterm = (pTn * Ee * c.e.om_sin - half) * (pTn * Ee + a);  // Ee^2 pTn^2 - a^2
+    const float pz2 = cterm / qq;
+    float acc = 0.f;
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+      const float pzn = rr == 0 ? pz1 : pz2;
+      const float En = sqrtf(fmaf(pzn, pzn, pTn * pTn));
+      const Boost b = transverse_boost(Ee + En, pex + nx, pey + ny, pez + pzn, bw.q2, P);
+      if (!(b.x1 < 1.f && b.x2 < 1.f)) continue;
+      float lm, lp;
+      light_cone(c.e, Ee, b, lm, lp);
+      const float uA = b.x1 * P.sqrt_s * lm;  // -(k1 - p_e)^2
+      const float uB = b.x2 * P.sqrt_s * lp;  // -(k2 - p_e)^2
+      const float fq1 = pdf(P, 0, b.x1), fqb1 = pdf(P, 1, b.x1);
+      const float fq2 = pdf(P, 0, b.x2), fqb2 = pdf(P, 1, b.x2);
+      // W+: (k_u . p_e+)^2 ; W-: (k_ubar . p_e-)^2
+      acc += c.charge > 0 ? fmaf(fq1 * fqb2, uA * uA, fqb1 * fq2 * uB * uB)
+                          : fmaf(fq1 * fqb2, uB * uB, fqb1 * fq2 * uA * uA);
+    }
+    // common factors: E_e, TFs, flux 4/shat, BW Jacobian / |D|^2 ~ t R, pz Jacobian 1/sqrt(D')
+    return c.cst * Ee * __expf(-0.5f * (z * z + zm2)) * (4.f / bw.q2) * (t * bw.R / sD) * acc;
+  }
+};
+
+}  // namespace mem

@@ -17,12 +17,13 @@ import pytest
 
 def test_u01_exact_and_open(ora):
     lib = ora.load()
-    for x, want in [(0, 0.5 / 2**24), (0xFFFFFFFF, (2**24 - 0.5) / 2**24), (256, 1.5 / 2**24)]:
+    for x, want in [(0, 0.5 / 2**23), (0xFFFFFFFF, (2**23 - 0.5) / 2**23), (512, 1.5 / 2**23)]:
         assert lib.ora_u01(x) == want
-    # the conversion keeps 24 bits: every uniform is an odd multiple of 2^-25
+    # 23 random bits: every uniform is an odd multiple of 2^-24, hence exact in FP32
     u = np.array([ora.point_u(7, 3, 0, i, 4) for i in range(512)]).ravel()
-    k = u * 2**25
+    k = u * 2**24
     assert np.all(k == np.round(k)) and np.all(np.round(k) % 2 == 1)
+    assert np.array_equal(u.astype(np.float32).astype(np.float64), u)
     assert u.min() > 0.0 and u.max() < 1.0
 
 
@@ -89,5 +90,5 @@ def test_counter_layout(ora):
     w0 = ora.philox([77, 0, 11, 5], key)
     w1 = ora.philox([77, 1 << 8, 11, 5], key)
     words = w0 + w1
-    want = [((x >> 8) + 0.5) / 2**24 for x in words[:7]]
+    want = [((x >> 9) + 0.5) / 2**23 for x in words[:7]]
     assert np.array_equal(u, np.array(want))
