@@ -124,6 +124,34 @@ mem_status mem_integrate(const mem_events* ev, const mem_process* proc, const me
                          uint64_t n_points, uint64_t seed, const mem_opts* opts, double* prob,
                          double* err, uint64_t* n_used, int32_t* ev_status, void* stream);
 
+/* Working memory of mem_integrate_noalloc, fixed at build time (32 MiB per GPU). */
+#define MEM_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* mem_integrate without any device allocation. The paper has no counterpart:
+ * this entry point exists for callers that may not allocate device memory
+ * once they are running -- e.g. an online event selection inside a
+ * data-acquisition process that reserves all GPU memory at start-up and
+ * forbids per-batch allocations for predictable latency, or an application
+ * that lends the library buffers from its own pool. It runs the same kernels
+ * as mem_integrate with the default plan (5 VEGAS adaptation iterations of
+ * min(2^14, n/8) points, alpha 1.5) and takes the process and transfer
+ * functions by descriptor (no handles). `records` (n_events x 32 float32),
+ * `prob`, `err` and `ev_status` (optional) must be DEVICE memory; the call is
+ * asynchronous on `stream` and copies nothing.
+ * Working memory (grids, per-item constants, partial sums) is one static
+ * device array of MEM_NOALLOC_SCRATCH_BYTES that every GPU loading the library
+ * keeps until exit; a call needing more is rejected with MEM_ERR_INVALID_ARG
+ * (about 2,400 Drell-Yan or W events at 2^20 points per event fit). The
+ * first call on a device, with that device current, looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture. All calls share the array: calls that overlap on
+ * the GPU (other streams, other host threads) race on it and must be
+ * serialised by the caller. Nothing in it needs clearing between calls. */
+mem_status mem_integrate_noalloc(const mem_process_desc* desc, const mem_tf_desc* tf,
+                                 const float* records, int64_t n_events, uint64_t n_points,
+                                 uint64_t seed, uint64_t event_id_base, double* prob,
+                                 double* err, int32_t* ev_status, void* stream);
+
 /* Release a mem_process or mem_events handle (NULL is a no-op). Releasing a
  * process does not release events uploaded with it. */
 void mem_destroy(void* handle);

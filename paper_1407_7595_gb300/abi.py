@@ -62,6 +62,9 @@ SIGNATURES = [
     ("mem_upload_events", C.c_int, [_vp, _vp, C.c_int64, C.c_int32, _vp, C.POINTER(_vp)]),
     ("mem_integrate", C.c_int, [_vp, _vp, C.POINTER(mem_tf_desc), C.c_uint64, C.c_uint64,
                                 C.POINTER(mem_opts), _vp, _vp, _vp, _vp, _vp]),
+    ("mem_integrate_noalloc", C.c_int, [C.POINTER(mem_process_desc), C.POINTER(mem_tf_desc),
+                                        _vp, C.c_int64, C.c_uint64, C.c_uint64, C.c_uint64,
+                                        _vp, _vp, _vp, _vp]),
     ("mem_destroy", None, [_vp]),
     ("mem_last_error", C.c_char_p, []),
     ("mem_eval_points", C.c_int, [_vp, _vp, C.POINTER(mem_tf_desc), C.c_int64, C.c_int32,
@@ -173,6 +176,14 @@ def mem_integrate(events, proc, tf, n_points, seed, opts, prob, err, n_used=None
     _check(lib().mem_integrate(events, proc, C.byref(tf), n_points, seed,
                                C.byref(opts) if opts is not None else None, _ptr(prob),
                                _ptr(err), _ptr(n_used), _ptr(ev_status), stream))
+
+
+def mem_integrate_noalloc(desc, tf, records, n_points, seed, event_id_base, prob, err,
+                          ev_status=None, stream=None):
+    """Allocation-free integration: records, prob, err, ev_status are device tensors."""
+    _check(lib().mem_integrate_noalloc(C.byref(desc), C.byref(tf), _ptr(records),
+                                       records.shape[0], n_points, seed, event_id_base,
+                                       _ptr(prob), _ptr(err), _ptr(ev_status), stream))
 
 
 def mem_destroy(handle):

@@ -245,6 +245,14 @@ TFConst make_tf_const(const mem_tf_desc& t) {
   return T;
 }
 
+ProcConst make_proc_const_from(const void* p) {
+  return make_proc_const(*reinterpret_cast<const mem_process_desc*>(p));
+}
+TFConst make_tf_const_from(const void* p) {
+  return make_tf_const(*reinterpret_cast<const mem_tf_desc*>(p));
+}
+void set_last_error(const char* msg) { g_err = msg; }
+
 }  // namespace mem
 
 using namespace mem;

@@ -57,6 +57,11 @@ cudaError_t launch_eval_dy(const EvalArgs&, cudaStream_t);
 cudaError_t launch_eval_w(const EvalArgs&, cudaStream_t);
 cudaError_t launch_eval_tt(const EvalArgs&, cudaStream_t);
 
+// constants and error reporting shared with entry points outside mem_api.cu
+ProcConst make_proc_const_from(const void* mem_process_desc_ptr);
+TFConst make_tf_const_from(const void* mem_tf_desc_ptr);
+void set_last_error(const char* msg);
+
 size_t cache_size_dy();
 size_t cache_size_w();
 size_t cache_size_tt();
