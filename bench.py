@@ -47,6 +47,8 @@ WORKLOAD_NAMES = {
     "w": "W->e nu LO, 4-dim integral (E_e, nu px, nu py, q^2_W), 1024 events x 2^20 "
          "evaluations/event, FP32 integrand + FP64 accumulation",
     "dy": "Drell-Yan Z/photon->mu mu, 2-dim integral, 64 events x 2^16 evaluations/event",
+    "ttbar": "semileptonic ttbar (gg + qqbar, spin-correlated helicity amplitudes), 7-dim "
+             "integral x 24 jet permutations, 4096 events x 2^22 evaluations/event",
 }
 
 
@@ -56,7 +58,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["w", "dy"], default="w")
+    ap.add_argument("--workload", choices=["w", "dy", "ttbar"], default="w")
     ap.add_argument("--events", type=int, default=None, help="override the event count")
     ap.add_argument("--points", type=int, default=None, help="override points per event")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
@@ -129,7 +131,10 @@ class ClockSampler:
 def cpu_baseline(kind, seed):
     """The FP64 oracle, as it stands, on a bounded sample of the workload, all host cores."""
     from oracle import oracle as O
-    n_ev, n_pts = {synth.PROC_W: (64, 1 << 16), synth.PROC_DY: (16, 1 << 15)}[kind]
+    # (events, evaluations per item): about 10 s of work on 16 Grace cores
+    n_ev, n_pts = {synth.PROC_W: (64, 1 << 16), synth.PROC_DY: (16, 1 << 15),
+                   synth.PROC_TTBAR: (2, 1 << 10)}[kind]
+    n_perm = synth.NPERM[kind]
     recs = synth.gen_events(kind, n_ev, seed)
     P = O.process(kind, synth.DEFAULT_PROCESS)
     T = O.tf(synth.DEFAULT_TF[kind])
@@ -137,9 +142,9 @@ def cpu_baseline(kind, seed):
     t = time.perf_counter()
     O.integrate(P, T, recs, seed=1, n_points=n_pts, n_threads=cores)
     dt = time.perf_counter() - t
-    return {"value": n_ev * n_pts / dt, "unit": "integrand evals/s", "cores": cores,
-            "kind": "oracle", "sample": f"{n_ev} events x {n_pts} evaluations/event "
-                                       f"(same generator and VEGAS plan), {dt:.1f} s"}
+    return {"value": n_ev * n_perm * n_pts / dt, "unit": "integrand evals/s", "cores": cores,
+            "kind": "oracle", "sample": f"{n_ev} events x {n_perm} permutations x {n_pts} "
+                                       f"evaluations (same generator and VEGAS plan), {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -203,12 +208,16 @@ def run_ours(args):
     for e in ph:
         e.record(stream)  # create the underlying CUDA events
     opts = abi.make_opts(event_id_base=rank * n_ev, phase_events=ph)
-    n_adapt = min(1 << 14, n_pts // 8)
-    n_main = n_pts - 5 * n_adapt
+    # the per-event budget is split equally over the jet permutations (items)
+    n_perm = synth.NPERM[kind]
+    n_item = -(-n_pts // n_perm)
+    n_adapt = min(1 << 14, n_item // 8)
+    n_main = n_item - 5 * n_adapt
+    evals_per_step = n_ev * n_perm * n_item
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
     def step(seed):
-        abi.mem_integrate(events, proc, tf, n_pts, seed, opts, prob, err, used, st, sp)
+        abi.mem_integrate(events, proc, tf, n_item, seed, opts, prob, err, used, st, sp)
 
     for i in range(args.warmup):
         step(10_000 + i)
@@ -241,7 +250,7 @@ def run_ours(args):
         total_ms = float(tt.item())
     clocks = sampler.stop() if rank == 0 else None
     ms_step = total_ms / args.steps
-    value = world * n_ev * n_pts / (ms_step * 1e-3)
+    value = world * evals_per_step / (ms_step * 1e-3)
     ok = bool(torch.all(st == 0).item())
 
     # end to end through the public API with host buffers: pinned records in,
@@ -258,7 +267,7 @@ def run_ours(args):
         t = time.perf_counter()
         for i in range(e2e_steps):
             ev2 = abi.mem_upload_events(proc, pinned, sp)
-            abi.mem_integrate(ev2, proc, tf, n_pts, 500 + i, abi.make_opts(event_id_base=rank * n_ev),
+            abi.mem_integrate(ev2, proc, tf, n_item, 500 + i, abi.make_opts(event_id_base=rank * n_ev),
                               hp.numpy(), he.numpy(), hu.numpy(), hs.numpy(), sp)
             abi.mem_destroy(ev2)
         torch.cuda.synchronize()
@@ -267,7 +276,7 @@ def run_ours(args):
             tt = torch.tensor([dt], dtype=torch.float64, device=dev)
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
             dt = float(tt.item())
-        e2e = {"value": world * n_ev * n_pts / dt, "unit": "integrand evals/s",
+        e2e = {"value": world * evals_per_step / dt, "unit": "integrand evals/s",
                "h2d_bytes_per_step": int(recs.nbytes),
                "d2h_bytes_per_step": int(n_ev * (8 + 8 + 8 + 4)),
                "ms_per_step": dt * 1e3}
@@ -279,7 +288,7 @@ def run_ours(args):
         peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
         fpe = FLOPS_PER_EVAL.get(kind)
         t_main = statistics.mean(main_ms) * 1e-3
-        achieved = fpe * n_ev * n_main / t_main / 1e12 if fpe else None
+        achieved = fpe * n_ev * n_perm * n_main / t_main / 1e12 if fpe else None
         roof = {"bound": "alu", "kernel": "k_main (frozen-grid sampling)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": None,

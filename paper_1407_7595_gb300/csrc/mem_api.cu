@@ -227,7 +227,7 @@ ProcConst make_proc_const(const mem_process_desc& d) {
   const double tp = 2.0 * PI_D;
   if (d.kind == PROC_DY) P.prefactor = (2.0 / s) / (4.0 * tp * tp);
   else if (d.kind == PROC_W) P.prefactor = (2.0 / s) / (8.0 * tp * tp);
-  else P.prefactor = (2.0 / s) * std::pow(tp, 4.0 - 18.0) / 64.0;
+  else P.prefactor = (2.0 / s) * std::pow(tp, 4.0 - 18.0) / 64.0 / TT_WEIGHT_SCALE;
   return P;
 }
 

@@ -111,8 +111,8 @@ struct AdaptSmem {
   float hist[PH::D * NG];
 };
 
-template <class PH>
-__global__ void __launch_bounds__(THREADS)
+template <class PH, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
 k_adapt(const float* __restrict__ recs, ProcConst P, TFConst T, int64_t n_items,
         uint64_t seed, uint64_t event_id_base, int n_iters, uint32_t n_adapt, double alpha,
         const double* __restrict__ grid_in, GridBin* __restrict__ grid32,

@@ -11,14 +11,14 @@ cudaError_t run_integrate(const IntegrateArgs& a, cudaStream_t st) {
   const size_t smem = sizeof(AdaptSmem<PH>);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_adapt<PH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_adapt<PH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   if (a.phase_events) cudaEventRecord(a.phase_events[0], st);
   // with n_iters == 0 the starting grid is frozen as given
-  k_adapt<PH><<<(unsigned)a.n_items, THREADS, smem, st>>>(
+  k_adapt<PH, MINB><<<(unsigned)a.n_items, THREADS, smem, st>>>(
       a.recs, a.P, a.T, a.n_items, a.seed, a.event_id_base, a.n_iters, a.n_adapt, a.alpha,
       a.grid_in, a.grid32, reinterpret_cast<typename PH::Cache*>(a.caches));
   cudaError_t e = cudaGetLastError();

@@ -1,13 +1,16 @@
 // Kernel instantiations for the semileptonic ttbar process.
 #include "mem_launch.cuh"
+#include "mem_ttbar.cuh"
 
 namespace mem {
 
-cudaError_t launch_integrate_tt(const IntegrateArgs&, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t launch_eval_tt(const EvalArgs&, cudaStream_t) { return cudaErrorNotSupported; }
+constexpr int PPT_TT = 8;
+constexpr int MINB_TT = 2;  // <= 128 registers, no spills
 
-}  // namespace mem
+cudaError_t launch_integrate_tt(const IntegrateArgs& a, cudaStream_t st) {
+  return run_integrate<PhysTT, PPT_TT, MINB_TT>(a, st);
+}
+cudaError_t launch_eval_tt(const EvalArgs& a, cudaStream_t st) { return run_eval<PhysTT>(a, st); }
+size_t cache_size_tt() { return cache_bytes<PhysTT>(); }
 
-namespace mem {
-size_t cache_size_tt() { return 16; }
 }  // namespace mem

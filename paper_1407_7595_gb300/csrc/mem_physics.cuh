@@ -15,6 +15,11 @@ namespace mem {
 
 enum { PROC_DY = 0, PROC_W = 1, PROC_TTBAR = 2 };
 
+// ttbar weights are carried in FP32 multiplied by 2^40 (an exact power of two,
+// divided out of the FP64 prefactor) so that products of small factors in
+// far-tail points stay in the FP32 normal range.
+constexpr double TT_WEIGHT_SCALE = 1099511627776.0;
+
 // Constants of a process, built on the host in FP64 and rounded once.
 struct ProcConst {
   int kind;
