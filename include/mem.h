@@ -79,8 +79,9 @@ typedef struct {
 /* Integration options (NULL = defaults: fixed n_points per event, 5 VEGAS
  * adaptation iterations of min(2^14, n/8) points, alpha = 1.5). */
 typedef struct {
-  double target_rel_err;  /* > 0: adaptive budget -- keep adding frozen-grid chunks
-                             until err/prob <= target or max_points (per event) */
+  double target_rel_err;  /* > 0: adaptive budget -- keep adding frozen-grid points
+                             until err/prob <= target or max_points (per event);
+                             mem_integrate then runs the mem_integrate_batch schedule */
   uint64_t max_points;    /* cap per event in adaptive mode (0 = 2^24) */
   uint64_t min_points;    /* minimum per event in adaptive mode (0 = n_points) */
   int32_t n_adapt_iters;  /* VEGAS adaptation iterations, excluded from the estimate */
@@ -123,6 +124,28 @@ mem_status mem_upload_events(mem_process* proc, const float* records, int64_t n_
 mem_status mem_integrate(const mem_events* ev, const mem_process* proc, const mem_tf_desc* tf,
                          uint64_t n_points, uint64_t seed, const mem_opts* opts, double* prob,
                          double* err, uint64_t* n_used, int32_t* ev_status, void* stream);
+
+/* Integrate several event sets (one mem_events per process; uneven dimensions,
+ * permutation counts and budgets) to a target relative error in one call: the
+ * per-event stop rule of the adaptive mode, err/prob <= opts->target_rel_err
+ * (Sec. 2's MC error estimate; p_hat averaged over jet permutations, Sec. 4),
+ * capped at opts->max_points per event (0 = 2^24) and starting from
+ * opts->min_points (0 = 2^14) frozen-grid points per event after
+ * opts->n_adapt_iters VEGAS iterations of opts->adapt_points points per item
+ * (0 = 8192). Points are added in rounds that double each unconverged event's
+ * budget; every round runs on the device and the whole schedule of all groups
+ * is one CUDA graph (one forked stream per group). Outputs are concatenated
+ * over the groups in order (sum of n_events entries each); ev_status is
+ * MEM_OK (converged), MEM_NOT_CONVERGED (cap reached), MEM_ERR_NONFINITE or
+ * MEM_ERR_INVALID_ARG (invalid record). Event ids in the Philox counter are
+ * opts->event_id_base + the event's position in the concatenation. The call
+ * returns when the work is complete. Errors: MEM_ERR_INVALID_ARG (NULL,
+ * n_groups outside [1, 16], target_rel_err <= 0, grid_in given, budgets that do
+ * not fit), MEM_ERR_OOM, MEM_ERR_CUDA. */
+mem_status mem_integrate_batch(int32_t n_groups, const mem_events* const* events,
+                               const mem_process* const* procs, const mem_tf_desc* const* tfs,
+                               uint64_t seed, const mem_opts* opts, double* prob, double* err,
+                               uint64_t* n_used, int32_t* ev_status, void* stream);
 
 /* Working memory of mem_integrate_noalloc, fixed at build time (32 MiB per GPU). */
 #define MEM_NOALLOC_SCRATCH_BYTES (32u << 20)

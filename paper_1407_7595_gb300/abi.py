@@ -62,6 +62,8 @@ SIGNATURES = [
     ("mem_upload_events", C.c_int, [_vp, _vp, C.c_int64, C.c_int32, _vp, C.POINTER(_vp)]),
     ("mem_integrate", C.c_int, [_vp, _vp, C.POINTER(mem_tf_desc), C.c_uint64, C.c_uint64,
                                 C.POINTER(mem_opts), _vp, _vp, _vp, _vp, _vp]),
+    ("mem_integrate_batch", C.c_int, [C.c_int32, _vp, _vp, _vp, C.c_uint64, C.POINTER(mem_opts),
+                                      _vp, _vp, _vp, _vp, _vp]),
     ("mem_integrate_noalloc", C.c_int, [C.POINTER(mem_process_desc), C.POINTER(mem_tf_desc),
                                         _vp, C.c_int64, C.c_uint64, C.c_uint64, C.c_uint64,
                                         _vp, _vp, _vp, _vp]),
@@ -176,6 +178,18 @@ def mem_integrate(events, proc, tf, n_points, seed, opts, prob, err, n_used=None
     _check(lib().mem_integrate(events, proc, C.byref(tf), n_points, seed,
                                C.byref(opts) if opts is not None else None, _ptr(prob),
                                _ptr(err), _ptr(n_used), _ptr(ev_status), stream))
+
+
+def mem_integrate_batch(groups, seed, opts, prob, err, n_used=None, ev_status=None,
+                        stream=None):
+    """groups: list of (events handle, process handle, mem_tf_desc); outputs concatenated."""
+    n = len(groups)
+    evs = (C.c_void_p * n)(*[g[0] for g in groups])
+    prs = (C.c_void_p * n)(*[g[1] for g in groups])
+    tfs = (C.c_void_p * n)(*[C.addressof(g[2]) for g in groups])
+    _check(lib().mem_integrate_batch(n, C.cast(evs, C.c_void_p), C.cast(prs, C.c_void_p),
+                                     C.cast(tfs, C.c_void_p), seed, C.byref(opts), _ptr(prob),
+                                     _ptr(err), _ptr(n_used), _ptr(ev_status), stream))
 
 
 def mem_integrate_noalloc(desc, tf, records, n_points, seed, event_id_base, prob, err,

@@ -14,9 +14,6 @@
 
 namespace {
 
-constexpr uint32_t MAGIC_PROC = 0x4D454D50u;  // "MEMP"
-constexpr uint32_t MAGIC_EVT = 0x4D454D45u;   // "MEME"
-
 thread_local std::string g_err;
 
 mem_status fail(mem_status s, const std::string& msg) {
@@ -46,20 +43,6 @@ bool is_device_ptr(const void* p) {
 }
 
 }  // namespace
-
-struct mem_process {
-  uint32_t magic;
-  mem_process_desc desc;
-  mem::ProcConst pc;
-};
-
-struct mem_events {
-  uint32_t magic;
-  int32_t kind;
-  int64_t n;
-  int device;
-  float* d_recs;
-};
 
 namespace mem {
 
@@ -387,7 +370,13 @@ mem_status mem_integrate(const mem_events* ev, const mem_process* proc, const me
   int iters = opts ? opts->n_adapt_iters : 5;
   if (iters < 0 || iters > 64) return fail(MEM_ERR_INVALID_ARG, "n_adapt_iters out of range [0, 64]");
   if (opts && opts->reserved0 != 0) return fail(MEM_ERR_INVALID_ARG, "reserved0 must be 0");
-  if (opts && opts->target_rel_err > 0.0) return fail(MEM_ERR_INVALID_ARG, "adaptive budgets are served by the batched integrator");
+  if (opts && opts->target_rel_err > 0.0) {
+    // adaptive budget: the batched schedule with this one event set
+    const mem_events* evs[1] = {ev};
+    const mem_process* prs[1] = {proc};
+    const mem_tf_desc* tfs[1] = {tf};
+    return mem_integrate_batch(1, evs, prs, tfs, seed, opts, prob, err, n_used, ev_status, stream);
+  }
   uint64_t na = opts && opts->adapt_points ? opts->adapt_points : (n_points / 8 < 16384 ? n_points / 8 : 16384);
   if (iters == 0) na = 0;
   if (n_points > ((uint64_t)1 << 32)) return fail(MEM_ERR_INVALID_ARG, "n_points above 2^32 per item");

@@ -5,8 +5,27 @@
 
 #include <cstdint>
 
+#include "../../include/mem.h"
 #include "mem_common.cuh"
 #include "mem_physics.cuh"
+
+constexpr uint32_t MAGIC_PROC = 0x4D454D50u;  // "MEMP"
+constexpr uint32_t MAGIC_EVT = 0x4D454D45u;   // "MEME"
+
+// Library-owned handles (opaque to callers).
+struct mem_process {
+  uint32_t magic;
+  mem_process_desc desc;
+  mem::ProcConst pc;
+};
+
+struct mem_events {
+  uint32_t magic;
+  int32_t kind;
+  int64_t n;
+  int device;
+  float* d_recs;
+};
 
 namespace mem {
 
@@ -66,6 +85,11 @@ size_t cache_size_dy();
 size_t cache_size_w();
 size_t cache_size_tt();
 size_t cache_size(int kind);
+
+struct BatchArgs;
+cudaError_t launch_batch_dy(const BatchArgs&, cudaStream_t);
+cudaError_t launch_batch_w(const BatchArgs&, cudaStream_t);
+cudaError_t launch_batch_tt(const BatchArgs&, cudaStream_t);
 
 cudaError_t launch_final(const Slot* slots, int64_t n_events, int nperm, uint32_t cpi,
                          uint32_t n_main, uint64_t n_per_item, double prefactor, double* prob,

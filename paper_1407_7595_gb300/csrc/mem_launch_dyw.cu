@@ -22,3 +22,10 @@ namespace mem {
 size_t cache_size_dy() { return cache_bytes<PhysDY>(); }
 size_t cache_size_w() { return cache_bytes<PhysW>(); }
 }  // namespace mem
+
+#include "mem_batch.cuh"
+
+namespace mem {
+cudaError_t launch_batch_dy(const BatchArgs& b, cudaStream_t st) { return run_batch<PhysDY, 1>(b, st); }
+cudaError_t launch_batch_w(const BatchArgs& b, cudaStream_t st) { return run_batch<PhysW, MINB_W>(b, st); }
+}  // namespace mem

@@ -14,3 +14,9 @@ cudaError_t launch_eval_tt(const EvalArgs& a, cudaStream_t st) { return run_eval
 size_t cache_size_tt() { return cache_bytes<PhysTT>(); }
 
 }  // namespace mem
+
+#include "mem_batch.cuh"
+
+namespace mem {
+cudaError_t launch_batch_tt(const BatchArgs& b, cudaStream_t st) { return run_batch<PhysTT, MINB_TT>(b, st); }
+}  // namespace mem
