@@ -175,6 +175,48 @@ mem_status mem_integrate_noalloc(const mem_process_desc* desc, const mem_tf_desc
                                  uint64_t seed, uint64_t event_id_base, double* prob,
                                  double* err, int32_t* ev_status, void* stream);
 
+/* ---- learned importance sampler ------------------------------------------
+ * An event-conditioned affine-coupling normalising flow on the unit cube that
+ * replaces the VEGAS map (Sec. 2, importance sampling) for the ttbar
+ * integrand: u ~ U(0,1)^7 -> logit -> 6 coupling layers (z_B <- z_B e^s + t,
+ * (s, t) from a 128-128 ReLU MLP of z_A and 16 event features, s = 2 tanh(s_raw/2))
+ * -> sigmoid. Its log-Jacobian is exact, so f(y)|dy/du| is an unbiased weight.
+ * Hidden layers run on BF16 tensor cores with FP32 accumulation; FP32 master
+ * parameters. Parameters use a flat FP32 layout: per layer k = 0..5 with
+ * |A| = 4 (k even) or 3 (k odd) and |B| = 7 - |A|: W1a [|A|][128], W1c [16][128],
+ * b1 [128], W2 [128][128], b2 [128], W3 [128][2|B|], b3 [2|B|]. */
+typedef struct mem_flow mem_flow;
+
+/* Number of FP32 parameters of the flow. */
+int64_t mem_flow_param_count(void);
+/* Create a flow on the current device: random hidden weights (seeded), zero
+ * output layers (the identity map). Release with mem_destroy. */
+mem_status mem_flow_create(uint64_t seed, mem_flow** out);
+/* Copy parameters in/out (host arrays of mem_flow_param_count() floats). */
+mem_status mem_flow_set_params(mem_flow* flow, const float* params, int64_t n);
+mem_status mem_flow_get_params(const mem_flow* flow, float* params, int64_t n);
+/* Forward map of n points sharing one conditioning vector: cond (16 floats),
+ * u (n x 7) -> y (n x 7) and log|dy/du| (n); all DEVICE arrays; synchronous. */
+mem_status mem_flow_map(const mem_flow* flow, const float* cond, const float* u, int64_t n,
+                        float* y, float* logj, void* stream);
+
+/* Training data layout (all DEVICE arrays): n_items items of 128 samples, ys
+ * [n_items][128][7] points in (0,1)^7, ws [n_items][128] weights normalised to
+ * sum 1 per item, cs [n_items][16] conditioning. Loss of an item:
+ * L = sum_i w_i log|dy/du|(y_i) = -sum_i w_i log q(y_i) (KL divergence from the
+ * normalised integrand to the flow density, up to a constant).
+ * mem_flow_grad: gradient of the summed loss over all items w.r.t. every
+ * parameter (flat layout, HOST output of mem_flow_param_count() floats) and
+ * the loss (host double); parameters unchanged.
+ * mem_flow_train: n_steps Adam steps (beta 0.9/0.999) on minibatches of
+ * batch_items items drawn by epochs of seeded permutations, gradient = mean
+ * over the minibatch's items; loss_trace (HOST, n_steps floats, optional). */
+mem_status mem_flow_grad(mem_flow* flow, const float* ys, const float* ws, const float* cs,
+                         int64_t n_items, float* grad, double* loss, void* stream);
+mem_status mem_flow_train(mem_flow* flow, const float* ys, const float* ws, const float* cs,
+                          int64_t n_items, int32_t n_steps, int32_t batch_items, float lr,
+                          uint64_t seed, float* loss_trace, void* stream);
+
 /* Release a mem_process or mem_events handle (NULL is a no-op). Releasing a
  * process does not release events uploaded with it. */
 void mem_destroy(void* handle);

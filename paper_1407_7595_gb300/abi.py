@@ -67,6 +67,15 @@ SIGNATURES = [
     ("mem_integrate_noalloc", C.c_int, [C.POINTER(mem_process_desc), C.POINTER(mem_tf_desc),
                                         _vp, C.c_int64, C.c_uint64, C.c_uint64, C.c_uint64,
                                         _vp, _vp, _vp, _vp]),
+    ("mem_flow_param_count", C.c_int64, []),
+    ("mem_flow_create", C.c_int, [C.c_uint64, C.POINTER(_vp)]),
+    ("mem_flow_set_params", C.c_int, [_vp, _vp, C.c_int64]),
+    ("mem_flow_get_params", C.c_int, [_vp, _vp, C.c_int64]),
+    ("mem_flow_map", C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _vp, _vp]),
+    ("mem_flow_grad", C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, _vp, C.POINTER(C.c_double),
+                                _vp]),
+    ("mem_flow_train", C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, C.c_int32, C.c_int32,
+                                 C.c_float, C.c_uint64, _vp, _vp]),
     ("mem_destroy", None, [_vp]),
     ("mem_last_error", C.c_char_p, []),
     ("mem_eval_points", C.c_int, [_vp, _vp, C.POINTER(mem_tf_desc), C.c_int64, C.c_int32,
@@ -202,6 +211,48 @@ def mem_integrate_noalloc(desc, tf, records, n_points, seed, event_id_base, prob
 
 def mem_destroy(handle):
     lib().mem_destroy(handle)
+
+
+def mem_flow_param_count():
+    return lib().mem_flow_param_count()
+
+
+def mem_flow_create(seed=0):
+    h = _vp()
+    _check(lib().mem_flow_create(seed, C.byref(h)))
+    return h
+
+
+def mem_flow_set_params(flow, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(lib().mem_flow_set_params(flow, _ptr(p), p.size))
+
+
+def mem_flow_get_params(flow):
+    p = np.zeros(mem_flow_param_count(), dtype=np.float32)
+    _check(lib().mem_flow_get_params(flow, _ptr(p), p.size))
+    return p
+
+
+def mem_flow_grad(flow, ys, ws, cs, stream=None):
+    """ys (n, 128, 7), ws (n, 128), cs (n, 16): device tensors -> (flat grad, loss)."""
+    g = np.zeros(mem_flow_param_count(), dtype=np.float32)
+    loss = C.c_double(0.0)
+    _check(lib().mem_flow_grad(flow, _ptr(ys), _ptr(ws), _ptr(cs), ys.shape[0], _ptr(g),
+                               C.byref(loss), stream))
+    return g, loss.value
+
+
+def mem_flow_train(flow, ys, ws, cs, n_steps, batch_items, lr=1e-3, seed=0, stream=None):
+    trace = np.zeros(n_steps, dtype=np.float32)
+    _check(lib().mem_flow_train(flow, _ptr(ys), _ptr(ws), _ptr(cs), ys.shape[0], n_steps,
+                                batch_items, lr, seed, _ptr(trace), stream))
+    return trace
+
+
+def mem_flow_map(flow, cond, u, y, logj, stream=None):
+    """cond (16,), u (n, 7), y (n, 7), logj (n,): device tensors."""
+    _check(lib().mem_flow_map(flow, _ptr(cond), _ptr(u), u.shape[0], _ptr(y), _ptr(logj), stream))
 
 
 def mem_eval_points(events, proc, tf, event_index, perm, seed, point0, n, grid, w_out,

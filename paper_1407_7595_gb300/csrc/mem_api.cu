@@ -354,6 +354,8 @@ void mem_destroy(void* handle) {
     cudaFree(e->d_recs);
     e->magic = 0;
     delete e;
+  } else if (m == MAGIC_FLOW) {  // learned-sampler parameters
+    mem_flow_release(reinterpret_cast<mem_flow*>(handle));
   }
 }
 

@@ -28,6 +28,27 @@ struct mem_events {
 };
 
 namespace mem {
+struct FlowW;
+struct FlowB;
+}  // namespace mem
+
+constexpr uint32_t MAGIC_FLOW = 0x4D454D46u;  // "MEMF"
+
+// Learned-sampler parameters (mem_flow.cu).
+struct mem_flow {
+  uint32_t magic;
+  int device;
+  mem::FlowW* W;      // FP32 master
+  mem::FlowB* B;      // BF16 operands
+  mem::FlowW* m;      // Adam first moment
+  mem::FlowW* v;      // Adam second moment
+  float* grad;        // FlowW-shaped gradient accumulator
+  int64_t step;
+};
+
+void mem_flow_release(mem_flow* f);
+
+namespace mem {
 
 struct IntegrateArgs {
   const float* recs;        // device, n_events x REC
