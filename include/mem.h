@@ -85,7 +85,9 @@ typedef struct {
   uint64_t max_points;    /* cap per event in adaptive mode (0 = 2^24) */
   uint64_t min_points;    /* minimum per event in adaptive mode (0 = n_points) */
   int32_t n_adapt_iters;  /* VEGAS adaptation iterations, excluded from the estimate */
-  int32_t reserved0;      /* must be 0 */
+  int32_t flow_guided;    /* mem_integrate_flow: 1 = the VEGAS judge's grid starts from one
+                             refinement with the flow pilot's per-bin sums of w^2 instead of
+                             the uniform grid; must be 0 for every other entry point */
   uint64_t adapt_points;  /* points per item per adaptation iteration (0 = min(2^14, n/8)) */
   double alpha;           /* grid compression exponent (0 = 1.5) */
   const double* grid_in;  /* optional HOST array d x 129: starting grid shared by all items */
@@ -93,6 +95,13 @@ typedef struct {
   void* phase_events;     /* optional array of 4 cudaEvent_t recorded on `stream` before the
                              adaptation kernel, before the frozen-grid kernel, before the
                              finalisation kernel and after it (phase timing); NULL = none */
+  double flow_screen;     /* mem_integrate_flow: after the flow pilot round an item goes to
+                             the VEGAS judge when its flow variance per point exceeds
+                             flow_screen * (event estimate)^2 / n_perm, or when the event
+                             estimate is not positive (0 = 1.0; < 0: every item is judged) */
+  double flow_cost;       /* mem_integrate_flow: time of a flow point relative to a VEGAS
+                             point; the judge keeps the flow when
+                             var_flow * flow_cost <= var_vegas (0 = 1.0) */
 } mem_opts;
 
 /* Number of integration dimensions / jet permutations of a process kind (-1 if invalid). */
@@ -216,6 +225,55 @@ mem_status mem_flow_grad(mem_flow* flow, const float* ys, const float* ws, const
 mem_status mem_flow_train(mem_flow* flow, const float* ys, const float* ws, const float* cs,
                           int64_t n_items, int32_t n_steps, int32_t batch_items, float lr,
                           uint64_t seed, float* loss_trace, void* stream);
+
+/* Training set for the ttbar flow (Sec. 2: samples of the integrand drawn by
+ * the VEGAS importance sampler). Every item (event, jet permutation) is
+ * adapted as in mem_integrate (opts: n_adapt_iters, 0 = the uniform grid,
+ * adapt_points, 0 = 8192, alpha; opts NULL = 5 x 8192, 1.5), then 128 points of the VEGAS stream that follow the
+ * adaptation are drawn from its grid: ys = the points (kept inside
+ * [2^-24, 1 - 2^-24]), ws = f J normalised to sum 1 over the item's 128 points
+ * (per_event = 0) or over the event's 24 x 128 points (per_event = 1: items
+ * weighted by their share of the event's estimate); 0 where the sum is 0.
+ * cs = the item's 16 conditioning features (units of 100 GeV, frame rotated
+ * to lepton phi = 0): lepton (px, pz); jets b, bbar, d, ubar of the
+ * permutation, each (px, py, pz); missing pT (x, y). log_jv (optional) = log J
+ * of the VEGAS map at each point, so that sum w log J is the training loss
+ * that the VEGAS density itself would score. Outputs are DEVICE arrays laid out
+ * as mem_flow_train reads them (n_items = n_events * 24).
+ * MEM_ERR_INVALID_ARG for a process other than MEM_PROC_TTBAR. */
+#define MEM_FLOW_SAMPLES_PER_ITEM 128
+mem_status mem_flow_samples(const mem_events* events, const mem_process* process,
+                            const mem_tf_desc* tf, uint64_t seed, const mem_opts* opts,
+                            int32_t per_event, float* ys, float* ws, float* cs, float* log_jv,
+                            void* stream);
+
+/* Adaptive-budget ttbar integral with the flow as the importance sampler and
+ * VEGAS as its fallback and judge. Round 0 (pilot): every item draws
+ * ceil(min_points / 24) flow points (Philox stream 2). Items that the pilot
+ * flags (opts->flow_screen) are adapted by VEGAS (n_adapt_iters x adapt_points,
+ * defaults 5 x 8192); the variance of its last adaptation iteration is compared
+ * with the flow's, and the lower (flow_cost-weighted) sampler integrates that item
+ * from then on. Later rounds double the points of every item of every
+ * unconverged event until err <= target_rel_err * prob or max_points (as
+ * mem_integrate_batch). Samples of both samplers are pooled per item (both are
+ * unbiased). n_used counts every evaluated point, adaptation included.
+ * item_sampler (optional, n_events * 24 bytes, host or device, same kind as
+ * prob): 0 flow, 1 flow kept by the judge, 2 VEGAS chosen by the judge.
+ * Synchronous; target_rel_err must be > 0. */
+mem_status mem_integrate_flow(const mem_events* events, const mem_process* process,
+                              const mem_tf_desc* tf, const mem_flow* flow, uint64_t seed,
+                              const mem_opts* opts, double* prob, double* err, uint64_t* n_used,
+                              int32_t* ev_status, uint8_t* item_sampler, void* stream);
+
+/* Flow-sampled points of one ttbar item (parity checks): points point0 ..
+ * point0 + n - 1 of stream 2 for (seed, event_id, perm), record = one event
+ * record (DEVICE); outputs the final logits z (n x 7 floats; the point is
+ * y = 1 / (1 + exp(-z))), log|dy/du| (n floats) and the weight
+ * prefactor * f(y) |dy/du| (n doubles), all DEVICE; synchronous. */
+mem_status mem_flow_eval_points(const mem_process* process, const mem_tf_desc* tf,
+                                const mem_flow* flow, const float* record, int32_t perm,
+                                uint64_t seed, uint32_t event_id, uint32_t point0, int64_t n,
+                                float* z, float* logj, double* w, void* stream);
 
 /* Release a mem_process or mem_events handle (NULL is a no-op). Releasing a
  * process does not release events uploaded with it. */

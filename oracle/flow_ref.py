@@ -185,3 +185,36 @@ def grad(layers, y, w, c):
         gz = g_zk1
         grads[k] = G
     return grads
+
+
+# ---------------------------------------------------------------------------
+# Conditioning of the ttbar sampler: 16 measured-momentum features per item
+# (event record, jet permutation), in units of 100 GeV, in the frame rotated
+# about the beam axis so that the lepton has phi = 0. Massless objects:
+# p = E (cos phi / cosh eta, sin phi / cosh eta, tanh eta).
+# Order: lepton (px, pz); the jets assigned to b, bbar, d, ubar, each
+# (px, py, pz); missing pT (x, y). Record layout: object o at [4o .. 4o+3] =
+# (E, eta, phi, kind), lepton o = 0, jets o = 1..4, missing pT at [24], [25];
+# permutation p (0..23) = the p-th lexicographic ordering of the 4 jets.
+# ---------------------------------------------------------------------------
+def _momentum(E, eta, phi):
+    return E * np.array([np.cos(phi) / np.cosh(eta), np.sin(phi) / np.cosh(eta), np.tanh(eta)])
+
+
+def features(rec, perm):
+    import itertools
+    rec = np.asarray(rec, dtype=np.float64)
+    order = list(itertools.permutations(range(4)))[perm]
+    phil = rec[2]
+    R = np.array([[np.cos(phil), np.sin(phil), 0.0],      # rotation by -phi_l about z
+                  [-np.sin(phil), np.cos(phil), 0.0],
+                  [0.0, 0.0, 1.0]])
+    pl = R @ _momentum(rec[0], rec[1], rec[2])
+    out = [pl[0], pl[2]]
+    for k in range(4):
+        o = 1 + order[k]
+        pj = R @ _momentum(rec[4 * o], rec[4 * o + 1], rec[4 * o + 2])
+        out += list(pj)
+    met = R @ np.array([rec[24], rec[25], 0.0])
+    out += [met[0], met[1]]
+    return np.array(out) / 100.0

@@ -38,14 +38,21 @@ void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 double ora_u01(uint32_t x) { return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 /* Counter layout: (point index, draw block << 8 | stream tag, event id, perm);
- * key = (seed low word, seed high word). Integration stream tag = 0. Draw block
- * b supplies dimensions 4b .. 4b+3. */
-void ora_point_u(uint64_t seed, uint64_t event_id, int perm, uint64_t idx, int d, double* u) {
+ * key = (seed low word, seed high word). Stream tags: 0 = integration on the
+ * VEGAS grid, 2 = base draws of the learned sampler. Draw block b supplies
+ * dimensions 4b .. 4b+3. */
+void ora_point_u_tag(uint64_t seed, uint64_t event_id, int perm, uint64_t idx, int d, int tag,
+                     double* u) {
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   for (int b = 0; 4 * b < d; ++b) {
-    uint32_t ctr[4] = {(uint32_t)idx, (uint32_t)(b << 8), (uint32_t)event_id, (uint32_t)perm};
+    uint32_t ctr[4] = {(uint32_t)idx, (uint32_t)(b << 8) | (uint32_t)(tag & 0xff),
+                       (uint32_t)event_id, (uint32_t)perm};
     uint32_t o[4];
     ora_philox4x32_10(ctr, key, o);
     for (int j = 0; j < 4 && 4 * b + j < d; ++j) u[4 * b + j] = ora_u01(o[j]);
   }
+}
+
+void ora_point_u(uint64_t seed, uint64_t event_id, int perm, uint64_t idx, int d, double* u) {
+  ora_point_u_tag(seed, event_id, perm, idx, d, 0, u);
 }

@@ -65,6 +65,9 @@ void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 double ora_u01(uint32_t x);
 /* Unit-cube point for (event_id, perm, point index) from the integration stream. */
 void ora_point_u(uint64_t seed, uint64_t event_id, int perm, uint64_t idx, int d, double* u);
+/* The same from stream `tag` (2 = base draws of the learned sampler). */
+void ora_point_u_tag(uint64_t seed, uint64_t event_id, int perm, uint64_t idx, int d, int tag,
+                     double* u);
 
 /* Integrand on the unit cube (physics map + Jacobians, no VEGAS map). */
 double ora_integrand(const ora_process* P, const ora_tf* T, const float* rec, int perm,

@@ -80,6 +80,8 @@ def load():
     lib.ora_u01.argtypes = [C.c_uint32]
     lib.ora_u01.restype = C.c_double
     lib.ora_point_u.argtypes = [C.c_uint64, C.c_uint64, C.c_int, C.c_uint64, C.c_int, _dp]
+    lib.ora_point_u_tag.argtypes = [C.c_uint64, C.c_uint64, C.c_int, C.c_uint64, C.c_int,
+                                    C.c_int, _dp]
     lib.ora_integrand.argtypes = [P, T, fp, C.c_int, _dp]
     lib.ora_integrand.restype = C.c_double
     lib.ora_kinematics.argtypes = [P, T, fp, C.c_int, _dp, C.c_int, _dp, _dp, _dp, _dp]
@@ -153,9 +155,9 @@ def philox(ctr, key):
     return list(o)
 
 
-def point_u(seed, event_id, perm, idx, d):
+def point_u(seed, event_id, perm, idx, d, tag=0):
     u = np.zeros(d)
-    load().ora_point_u(seed, event_id, perm, idx, d, u.ctypes.data_as(_dp))
+    load().ora_point_u_tag(seed, event_id, perm, idx, d, tag, u.ctypes.data_as(_dp))
     return u
 
 

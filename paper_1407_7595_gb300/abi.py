@@ -46,9 +46,10 @@ class mem_tf_desc(C.Structure):
 class mem_opts(C.Structure):
     _fields_ = [("target_rel_err", C.c_double), ("max_points", C.c_uint64),
                 ("min_points", C.c_uint64), ("n_adapt_iters", C.c_int32),
-                ("reserved0", C.c_int32), ("adapt_points", C.c_uint64), ("alpha", C.c_double),
+                ("flow_guided", C.c_int32), ("adapt_points", C.c_uint64), ("alpha", C.c_double),
                 ("grid_in", C.POINTER(C.c_double)), ("event_id_base", C.c_uint64),
-                ("phase_events", C.c_void_p)]
+                ("phase_events", C.c_void_p), ("flow_screen", C.c_double),
+                ("flow_cost", C.c_double)]
 
 
 _lib = None
@@ -76,6 +77,13 @@ SIGNATURES = [
                                 _vp]),
     ("mem_flow_train", C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, C.c_int32, C.c_int32,
                                  C.c_float, C.c_uint64, _vp, _vp]),
+    ("mem_flow_samples", C.c_int, [_vp, _vp, C.POINTER(mem_tf_desc), C.c_uint64,
+                                   C.POINTER(mem_opts), C.c_int32, _vp, _vp, _vp, _vp, _vp]),
+    ("mem_integrate_flow", C.c_int, [_vp, _vp, C.POINTER(mem_tf_desc), _vp, C.c_uint64,
+                                     C.POINTER(mem_opts), _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("mem_flow_eval_points", C.c_int, [_vp, C.POINTER(mem_tf_desc), _vp, _vp, C.c_int32,
+                                       C.c_uint64, C.c_uint32, C.c_uint32, C.c_int64, _vp, _vp,
+                                       _vp, _vp]),
     ("mem_destroy", None, [_vp]),
     ("mem_last_error", C.c_char_p, []),
     ("mem_eval_points", C.c_int, [_vp, _vp, C.POINTER(mem_tf_desc), C.c_int64, C.c_int32,
@@ -134,7 +142,8 @@ def tf_desc(params):
 
 
 def make_opts(n_adapt_iters=5, adapt_points=0, alpha=1.5, grid_in=None, event_id_base=0,
-              target_rel_err=0.0, max_points=0, min_points=0, phase_events=None):
+              target_rel_err=0.0, max_points=0, min_points=0, phase_events=None,
+              flow_screen=0.0, flow_cost=0.0, flow_guided=0):
     """phase_events: optional list of 4 torch.cuda.Event (created with
     enable_timing=True) recorded at the phase boundaries on the call's stream."""
     o = mem_opts()
@@ -142,7 +151,7 @@ def make_opts(n_adapt_iters=5, adapt_points=0, alpha=1.5, grid_in=None, event_id
     o.max_points = max_points
     o.min_points = min_points
     o.n_adapt_iters = n_adapt_iters
-    o.reserved0 = 0
+    o.flow_guided = flow_guided
     o.adapt_points = adapt_points
     o.alpha = alpha
     keep = None
@@ -150,6 +159,8 @@ def make_opts(n_adapt_iters=5, adapt_points=0, alpha=1.5, grid_in=None, event_id
         keep = np.ascontiguousarray(grid_in, dtype=np.float64)
         o.grid_in = keep.ctypes.data_as(C.POINTER(C.c_double))
     o.event_id_base = event_id_base
+    o.flow_screen = flow_screen
+    o.flow_cost = flow_cost
     ev_arr = None
     if phase_events is not None:
         assert len(phase_events) == 4
@@ -248,6 +259,42 @@ def mem_flow_train(flow, ys, ws, cs, n_steps, batch_items, lr=1e-3, seed=0, stre
     _check(lib().mem_flow_train(flow, _ptr(ys), _ptr(ws), _ptr(cs), ys.shape[0], n_steps,
                                 batch_items, lr, seed, _ptr(trace), stream))
     return trace
+
+
+FLOW_SAMPLES_PER_ITEM = 128
+
+
+def mem_flow_samples(events, proc, tf, n_events, seed, opts=None, per_event=False,
+                     want_logj=False, stream=None):
+    """Training set of the ttbar flow: (ys, ws, cs[, log_jv]) device tensors of
+    shapes (n_items, 128, 7), (n_items, 128), (n_items, 16), (n_items, 128),
+    n_items = 24 n_events."""
+    import torch
+    n_items = n_events * 24
+    ys = torch.empty(n_items, FLOW_SAMPLES_PER_ITEM, 7, dtype=torch.float32, device="cuda")
+    ws = torch.empty(n_items, FLOW_SAMPLES_PER_ITEM, dtype=torch.float32, device="cuda")
+    cs = torch.empty(n_items, 16, dtype=torch.float32, device="cuda")
+    lj = torch.empty(n_items, FLOW_SAMPLES_PER_ITEM, dtype=torch.float32,
+                     device="cuda") if want_logj else None
+    _check(lib().mem_flow_samples(events, proc, C.byref(tf), seed,
+                                  None if opts is None else C.byref(opts), int(per_event),
+                                  _ptr(ys), _ptr(ws), _ptr(cs), _ptr(lj), stream))
+    return (ys, ws, cs, lj) if want_logj else (ys, ws, cs)
+
+
+def mem_integrate_flow(events, proc, tf, flow, seed, opts, prob, err, n_used=None,
+                       ev_status=None, item_sampler=None, stream=None):
+    _check(lib().mem_integrate_flow(events, proc, C.byref(tf), flow, seed, C.byref(opts),
+                                    _ptr(prob), _ptr(err), _ptr(n_used), _ptr(ev_status),
+                                    _ptr(item_sampler), stream))
+
+
+def mem_flow_eval_points(proc, tf, flow, record, perm, seed, event_id, point0, n, z, logj, w,
+                         stream=None):
+    """record: device tensor of one event record; z (n, 7) final logits, logj (n,),
+    w (n,) float64: device tensors."""
+    _check(lib().mem_flow_eval_points(proc, C.byref(tf), flow, _ptr(record), perm, seed,
+                                      event_id, point0, n, _ptr(z), _ptr(logj), _ptr(w), stream))
 
 
 def mem_flow_map(flow, cond, u, y, logj, stream=None):

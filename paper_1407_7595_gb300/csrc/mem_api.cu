@@ -371,7 +371,7 @@ mem_status mem_integrate(const mem_events* ev, const mem_process* proc, const me
   const int d = dims_of(kind), np = nperm_of(kind);
   int iters = opts ? opts->n_adapt_iters : 5;
   if (iters < 0 || iters > 64) return fail(MEM_ERR_INVALID_ARG, "n_adapt_iters out of range [0, 64]");
-  if (opts && opts->reserved0 != 0) return fail(MEM_ERR_INVALID_ARG, "reserved0 must be 0");
+  if (opts && opts->flow_guided != 0) return fail(MEM_ERR_INVALID_ARG, "flow_guided must be 0");
   if (opts && opts->target_rel_err > 0.0) {
     // adaptive budget: the batched schedule with this one event set
     const mem_events* evs[1] = {ev};

@@ -32,13 +32,13 @@ __global__ void k_round_reduce(const int32_t* __restrict__ active, const RoundCt
 }
 
 __global__ void k_round_check(int64_t n_events, int nperm, double target, double prefactor,
-                              int last_round, const ItemAcc* __restrict__ acc,
+                              int last_round, uint64_t keep_n, const ItemAcc* __restrict__ acc,
                               int32_t* __restrict__ ev_state, uint8_t* __restrict__ flags) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_events) return;
   int32_t state = ev_state[e];
+  double ms = 0, mc = 0, vs = 0, vc = 0;
   if (state == 0) {
-    double ms = 0, mc = 0, vs = 0, vc = 0;
     bool invalid = false;
     for (int p = 0; p < nperm; ++p) {
       const ItemAcc A = acc[e * nperm + p];
@@ -57,13 +57,28 @@ __global__ void k_round_check(int64_t n_events, int nperm, double target, double
     else if (last_round) state = 2;
     ev_state[e] = state;
   }
-  const uint8_t f = state == 0 ? 1 : 0;
-  for (int p = 0; p < nperm; ++p) flags[e * nperm + p] = f;
+  // Items of an unconverged event keep sampling while their variance of the
+  // mean exceeds a quarter of their equal share of the event's error budget
+  // (target |sum of means|)^2 / nperm, or while they have no variance estimate
+  // yet and fewer than keep_n points (support not found yet).
+  const double tot = fabs(ms + mc);
+  const double share = (target * tot) * (target * tot) / nperm;
+  for (int p = 0; p < nperm; ++p) {
+    uint8_t f = 0;
+    if (state == 0) {
+      const ItemAcc A = acc[e * nperm + p];
+      const double N = (double)A.n;
+      const double mean = (A.s1 + A.c1) / N;
+      const double var = ((A.s2 + A.c2) / N - mean * mean) / (N - 1.0);
+      f = (var > 0.25 * share || (!(var > 0.0) && A.n < keep_n) || !(tot > 0.0)) ? 1 : 0;
+    }
+    flags[e * nperm + p] = f;
+  }
 }
 
 __global__ void k_round_compact(int64_t n_items, const uint8_t* __restrict__ flags,
                                 int32_t* __restrict__ active, RoundCtl* __restrict__ ctl,
-                                int target_tiles) {
+                                int target_tiles, const uint8_t* __restrict__ sel, int want) {
   // block-wide exclusive scan over chunks of blockDim items, in item order
   __shared__ int32_t wsum[32];
   __shared__ int32_t base;
@@ -72,7 +87,7 @@ __global__ void k_round_compact(int64_t n_items, const uint8_t* __restrict__ fla
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int64_t off = 0; off < n_items; off += blockDim.x) {
     const int64_t i = off + threadIdx.x;
-    const int f = (i < n_items) ? flags[i] : 0;
+    const int f = (i < n_items) ? (flags[i] && (!sel || sel[i] == want)) : 0;
     int x = f;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -108,8 +123,9 @@ __global__ void k_round_compact(int64_t n_items, const uint8_t* __restrict__ fla
 
 __global__ void k_batch_final(int64_t n_events, int nperm, double prefactor, uint64_t adapt_pts_item,
                               const ItemAcc* __restrict__ acc, const int32_t* __restrict__ ev_state,
-                              double* __restrict__ prob, double* __restrict__ err,
-                              uint64_t* __restrict__ n_used, int32_t* __restrict__ status) {
+                              const uint8_t* __restrict__ adapted, double* __restrict__ prob,
+                              double* __restrict__ err, uint64_t* __restrict__ n_used,
+                              int32_t* __restrict__ status) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_events) return;
   double ms = 0, mc = 0, vs = 0, vc = 0;
@@ -123,7 +139,7 @@ __global__ void k_batch_final(int64_t n_events, int nperm, double prefactor, uin
     var = var > 0.0 ? var : 0.0;
     neu2(ms, mc, mean);
     neu2(vs, vc, var);
-    n += A.n + adapt_pts_item;
+    n += A.n + ((!adapted || adapted[e * nperm + p]) ? adapt_pts_item : 0);
     bad += A.n_bad;
   }
   prob[e] = prefactor * (ms + mc) / nperm;
@@ -169,7 +185,7 @@ extern "C" mem_status mem_integrate_batch(int32_t n_groups, const mem_events* co
   if (n_groups < 1 || n_groups > 16 || !events || !procs || !tfs || !opts || !prob || !err)
     return bfail(MEM_ERR_INVALID_ARG, "invalid argument");
   if (!(opts->target_rel_err > 0.0)) return bfail(MEM_ERR_INVALID_ARG, "target_rel_err must be > 0");
-  if (opts->reserved0 != 0) return bfail(MEM_ERR_INVALID_ARG, "reserved0 must be 0");
+  if (opts->flow_guided != 0) return bfail(MEM_ERR_INVALID_ARG, "flow_guided must be 0");
   const int iters = opts->n_adapt_iters;
   if (iters < 1 || iters > 64) return bfail(MEM_ERR_INVALID_ARG, "n_adapt_iters must be in [1, 64] for adaptive budgets");
   const uint64_t cap_ev = opts->max_points ? opts->max_points : (uint64_t)1 << 24;

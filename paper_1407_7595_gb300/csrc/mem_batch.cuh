@@ -10,7 +10,9 @@
 //   k_round_reduce : per active item, its slots in order -> running FP64 sums.
 //   k_round_check  : per event, the estimate over permutations (Sec. 4: average)
 //                    and its MC error (Sec. 2); done when err <= target |p| or the
-//                    next round would pass the point cap.
+//                    next round would pass the point cap. Within an unconverged
+//                    event only the items whose variance still matters go on
+//                    (a cheap form of allocating points in proportion to sigma).
 //   k_round_compact: one CTA, prefix scan of the active flags -> next active list.
 // Every round's launch sequence is fixed, so all rounds of all processes are
 // captured into one CUDA graph; no host synchronisation between rounds.
@@ -124,21 +126,26 @@ __global__ void k_round_reduce(const int32_t* __restrict__ active, const RoundCt
                                uint32_t pts_item, const Slot* __restrict__ slots,
                                ItemAcc* __restrict__ acc);
 
-// Per event: estimate, error, stop rule; writes item active flags.
+// Per event: estimate, error, stop rule; writes item active flags (only the
+// items of an unconverged event whose variance still matters stay active).
 __global__ void k_round_check(int64_t n_events, int nperm, double target, double prefactor,
-                              int last_round, const ItemAcc* __restrict__ acc,
+                              int last_round, uint64_t keep_n, const ItemAcc* __restrict__ acc,
                               int32_t* __restrict__ ev_state, uint8_t* __restrict__ flags);
 
-// One CTA: active flags -> compacted list, counts and tiles per item.
+// One CTA: active flags -> compacted list, counts and tiles per item. With
+// sel != nullptr only items with sel[i] == want are listed.
 __global__ void k_round_compact(int64_t n_items, const uint8_t* __restrict__ flags,
                                 int32_t* __restrict__ active, RoundCtl* __restrict__ ctl,
-                                int target_tiles);
+                                int target_tiles, const uint8_t* __restrict__ sel, int want);
 
-// Final per-event outputs from the running sums.
+// Final per-event outputs from the running sums. Every item's adaptation
+// points count as used, or with adapted != nullptr only those of items with
+// adapted[i] != 0.
 __global__ void k_batch_final(int64_t n_events, int nperm, double prefactor, uint64_t adapt_pts_item,
                               const ItemAcc* __restrict__ acc, const int32_t* __restrict__ ev_state,
-                              double* __restrict__ prob, double* __restrict__ err,
-                              uint64_t* __restrict__ n_used, int32_t* __restrict__ status);
+                              const uint8_t* __restrict__ adapted, double* __restrict__ prob,
+                              double* __restrict__ err, uint64_t* __restrict__ n_used,
+                              int32_t* __restrict__ status);
 
 // Buffers and schedule of one process group.
 struct BatchArgs {
@@ -182,9 +189,10 @@ cudaError_t run_batch_rounds(const BatchArgs& b, cudaStream_t st) {
     k_round_reduce<<<(unsigned)((b.base.n_items + 255) / 256), 256, 0, st>>>(b.active, b.ctl, pts,
                                                                             b.slots, b.acc);
     k_round_check<<<(unsigned)((b.base.n_events + 127) / 128), 128, 0, st>>>(
-        b.base.n_events, b.nperm, b.target, b.base.P.prefactor, r == b.n_rounds - 1, b.acc,
-        b.ev_state, b.flags);
-    k_round_compact<<<1, 1024, 0, st>>>(b.base.n_items, b.flags, b.active, b.ctl, b.target_tiles);
+        b.base.n_events, b.nperm, b.target, b.base.P.prefactor, r == b.n_rounds - 1,
+        (uint64_t)b.pts0 * 4, b.acc, b.ev_state, b.flags);
+    k_round_compact<<<1, 1024, 0, st>>>(b.base.n_items, b.flags, b.active, b.ctl, b.target_tiles,
+                                        nullptr, 0);
     idx += pts;
     pts *= 2;
   }
@@ -207,12 +215,13 @@ cudaError_t run_batch(BatchArgs b, cudaStream_t st) {
   cudaMemsetAsync(b.flags, 1, (size_t)a.n_items, st);
   cudaMemsetAsync(b.acc, 0, (size_t)a.n_items * sizeof(ItemAcc), st);
   cudaMemsetAsync(b.ev_state, 0, (size_t)a.n_events * sizeof(int32_t), st);
-  k_round_compact<<<1, 1024, 0, st>>>(a.n_items, b.flags, b.active, b.ctl, b.target_tiles);
+  k_round_compact<<<1, 1024, 0, st>>>(a.n_items, b.flags, b.active, b.ctl, b.target_tiles, nullptr,
+                                      0);
   e = run_batch_rounds<PH, MINB>(b, st);
   if (e != cudaSuccess) return e;
   k_batch_final<<<(unsigned)((a.n_events + 127) / 128), 128, 0, st>>>(
       a.n_events, b.nperm, a.P.prefactor, (uint64_t)a.n_iters * a.n_adapt, b.acc, b.ev_state,
-      b.prob, b.err, b.n_used, b.status);
+      nullptr, b.prob, b.err, b.n_used, b.status);
   return cudaGetLastError();
 }
 

@@ -42,13 +42,18 @@ __device__ __forceinline__ float u01(uint32_t x) {
   return __uint2float_rn((x >> 9) * 2u + 1u) * 5.9604644775390625e-08f;
 }
 
+// Stream tags (low byte of counter word 1): 0 = points on the VEGAS grid,
+// 2 = base draws of the learned sampler.
+constexpr uint32_t TAG_VEGAS = 0, TAG_FLOW = 2;
+
 template <int D>
 __device__ __forceinline__ void point_uniforms(uint64_t seed, uint32_t event_id, uint32_t perm,
-                                               uint32_t idx, float (&u)[D]) {
+                                               uint32_t idx, float (&u)[D],
+                                               uint32_t tag = TAG_VEGAS) {
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
 #pragma unroll
   for (int b = 0; b < (D + 3) / 4; ++b) {
-    u32x4 o = philox4x32_10(idx, (uint32_t)b << 8, event_id, perm, k0, k1);
+    u32x4 o = philox4x32_10(idx, ((uint32_t)b << 8) | tag, event_id, perm, k0, k1);
     if (4 * b + 0 < D) u[4 * b + 0] = u01(o.a);
     if (4 * b + 1 < D) u[4 * b + 1] = u01(o.b);
     if (4 * b + 2 < D) u[4 * b + 2] = u01(o.c);

@@ -1,0 +1,328 @@
+// The learned sampler inside the Monte Carlo integral (Sec. 2, importance
+// sampling) of the ttbar process: per-item conditioning features, the training
+// set drawn from adapted VEGAS grids, and the fused sampling kernel
+//
+//   Philox u (stream 2) -> z = logit u -> 6 coupling layers (BF16 mma) ->
+//   y = sigmoid z -> w = F(y) |dy/du|
+//
+// whose per-point weight is unbiased for the integral whatever the flow's
+// parameters, because |dy/du| is the exact Jacobian of the map that was applied.
+#pragma once
+#include "mem_batch.cuh"
+#include "mem_flow.cuh"
+#include "mem_ttbar.cuh"
+
+namespace mem {
+
+constexpr int FCH = 2048;        // points per pass of a sampling CTA (z state in shared memory)
+constexpr int FROWS = WARPS * 16;  // rows per MLP sweep of the CTA (each warp takes 16)
+constexpr int FTS = 128;         // training samples per item
+
+// The 16 conditioning features of an item (event record, jet permutation), in
+// units of 100 GeV, in the frame rotated about the beam so that the lepton has
+// phi = 0: lepton (px, pz); jets b, bbar, d, ubar of the permutation, each
+// (px, py, pz); missing pT (x, y). Massless objects: pT = E / cosh(eta),
+// pz = E tanh(eta).
+__device__ inline void flow_features(const float* rec, int perm, float* c) {
+  int p[4];
+  tt_perm_decode(perm, p);
+  const double El = rec[0], etal = rec[1], phil = rec[2];
+  const double cl = cos(phil), sl = sin(phil);
+  c[0] = (float)(El / cosh(etal) * 0.01);
+  c[1] = (float)(El * tanh(etal) * 0.01);
+  for (int k = 0; k < 4; ++k) {
+    const int o = 1 + p[k];
+    const double E = rec[4 * o], eta = rec[4 * o + 1], dphi = (double)rec[4 * o + 2] - phil;
+    const double pt = E / cosh(eta);
+    c[2 + 3 * k] = (float)(pt * cos(dphi) * 0.01);
+    c[3 + 3 * k] = (float)(pt * sin(dphi) * 0.01);
+    c[4 + 3 * k] = (float)(E * tanh(eta) * 0.01);
+  }
+  const double mx = rec[24], my = rec[25];
+  c[14] = (float)((mx * cl + my * sl) * 0.01);
+  c[15] = (float)((my * cl - mx * sl) * 0.01);
+}
+
+// One thread per item: integrand constants and conditioning features.
+template <class PH>
+__global__ void k_flow_setup(const float* __restrict__ recs, ProcConst P, TFConst T,
+                             int64_t n_items, typename PH::Cache* __restrict__ caches,
+                             float* __restrict__ feats) {
+  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (item >= n_items) return;
+  const int64_t ev = item / PH::NPERM;
+  const int perm = (int)(item % PH::NPERM);
+  const float* rec = recs + ev * REC;
+  typename PH::Cache c;
+  PH::setup(rec, perm, P, T, c);
+  caches[item] = c;
+  flow_features(rec, perm, feats + item * FC);
+}
+
+// Training set: per item FTS points of the VEGAS stream after the adaptation
+// (indices idx0 ..), drawn from the item's adapted grid: y = x, raw weights
+// w = F(x) J (samples of F / I, importance-weighted against the VEGAS density),
+// their per-item sums in tot[item], and log J (optional); y is kept inside
+// [2^-24, 1 - 2^-24] for the logit.
+template <class PH>
+__global__ void __launch_bounds__(FTS)
+k_flow_samples(const float* __restrict__ recs, ProcConst P, int64_t n_items, uint64_t seed,
+               uint64_t event_id_base, uint32_t idx0, const GridBin* __restrict__ grid32,
+               const typename PH::Cache* __restrict__ caches, float* __restrict__ ys,
+               float* __restrict__ ws, float* __restrict__ cs, double* __restrict__ tot_out,
+               float* __restrict__ logj) {
+  constexpr int D = PH::D;
+  __shared__ typename PH::Cache cache;
+  __shared__ GridBin gb[D * NG];
+  __shared__ double red[FTS / 32];
+  const int64_t item = blockIdx.x;
+  if (item >= n_items) return;
+  const int64_t ev = item / PH::NPERM;
+  const int perm = (int)(item % PH::NPERM);
+  if (threadIdx.x == 0) cache = caches[item];
+  for (int t = threadIdx.x; t < D * NG; t += blockDim.x) gb[t] = grid32[item * (D * NG) + t];
+  __syncthreads();
+  float u[D], x[D], xc[D];
+  int bin[D];
+  point_uniforms<D>(seed, (uint32_t)(event_id_base + (uint64_t)ev), (uint32_t)perm,
+                    idx0 + threadIdx.x, u);
+  const float J = vegas_map<D>(gb, u, x, xc, bin);
+  float w = cache.ok ? PH::eval(cache, P, x, xc) * J : 0.f;
+  if (!isfinite(w) || w < 0.f) w = 0.f;
+  double s = w;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  const int64_t row = item * FTS + threadIdx.x;
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int k = 0; k < FTS / 32; ++k) tot += red[k];
+    tot_out[item] = tot;
+  }
+  ws[row] = w;
+  if (logj) logj[row] = __logf(J);
+  const float lo = 5.9604645e-8f, hi = 1.f - 5.9604645e-8f;  // 2^-24, 1 - 2^-24
+#pragma unroll
+  for (int j = 0; j < D; ++j) ys[row * D + j] = xc[j] < lo ? hi : fmaxf(x[j], lo);
+  if (threadIdx.x == 0) flow_features(recs + ev * REC, perm, cs + item * FC);
+}
+
+// Weights of the training set normalised to sum 1 per item (per_event = 0) or
+// per event (per_event = 1: an item then carries its share of the event's
+// estimate, so the loss favours the permutations that dominate the integral).
+__global__ void k_flow_normalise(int64_t n_items, int nperm, int per_event,
+                                 const double* __restrict__ tot, float* __restrict__ ws) {
+  const int64_t item = blockIdx.x;
+  if (item >= n_items) return;
+  double T = tot[item];
+  if (per_event) {
+    const int64_t e0 = item / nperm * nperm;
+    T = 0.0;
+    for (int p = 0; p < nperm; ++p) T += tot[e0 + p];
+  }
+  const float scale = T > 0.0 ? (float)(1.0 / T) : 0.f;
+  for (int t = threadIdx.x; t < FTS; t += blockDim.x) ws[item * FTS + t] *= scale;
+}
+
+// Shared memory of a sampling CTA (about 114 KB: two CTAs per SM).
+template <class PH>
+struct FlowSampSmem {
+  FlowLayerSmem L;
+  float zs[FCH * 8];      // per point: z[0..6], running log-Jacobian
+  float st[WARPS][16][8];
+  typename PH::Cache cache;
+  float c[FC];
+  DD red[2][WARPS];
+  uint32_t bad[WARPS];
+  float hist[PH::D * NG];  // w^2 over NG uniform bins per dimension (pilot round)
+};
+
+__device__ __forceinline__ void sigmoid_pair(float z, float& y, float& yc, float& lsp) {
+  // y = 1/(1+e^-z), 1 - y = 1/(1+e^z), both to full relative precision, and
+  // log(y (1 - y)) = -|z| - 2 log(1 + e^-|z|)
+  const float t = __expf(-fabsf(z));
+  const float r = 1.f / (1.f + t);
+  y = z >= 0.f ? r : t * r;
+  yc = z >= 0.f ? t * r : r;
+  lsp = -fabsf(z) - 2.f * log1pf(t);
+}
+
+// One pass of a CTA over points q0 .. q0 + nrow of an item (nrow a multiple of
+// FROWS, at most FCH; rows at or past p1 are computed but not used): base draw,
+// the coupling layers, then out(r, y, yc, log|dy/du|) per used row, threads
+// striding over rows.
+template <class PH, class Out>
+__device__ inline void flow_pass(FlowSampSmem<PH>& S, const FlowW* __restrict__ W,
+                                 const FlowB* __restrict__ Bw, uint64_t seed, uint32_t eid,
+                                 int perm, uint32_t idx_base, uint32_t q0, uint32_t nrow,
+                                 uint32_t p1, Out& out) {
+  constexpr int D = PH::D;
+  static_assert(D == FD, "the flow is built for the 7-dimensional ttbar integral");
+  for (uint32_t r = threadIdx.x; r < nrow; r += THREADS) {
+    const uint32_t p = q0 + r;
+    float u[D];
+    if (p < p1) {
+      point_uniforms<D>(seed, eid, (uint32_t)perm, idx_base + p, u, TAG_FLOW);
+    } else {
+#pragma unroll
+      for (int j = 0; j < D; ++j) u[j] = 0.5f;
+    }
+    float lj = 0.f;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const float z = __logf(u[j]) - log1pf(-u[j]);
+      S.zs[r * 8 + j] = z;
+      lj -= log_sig_prime(z);
+    }
+    S.zs[r * 8 + 7] = lj;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  for (int k = 0; k < FK; ++k) {
+    flow_load_layer(S.L, W, Bw, k, S.c);
+    __syncthreads();
+    for (uint32_t rb = warp * 16; rb < nrow; rb += FROWS) flow_mlp_rows(S.L, k, S.zs, rb, S.st[warp]);
+    __syncthreads();
+  }
+  for (uint32_t r = threadIdx.x; r < nrow; r += THREADS) {
+    if (q0 + r >= p1) continue;
+    float y[D], yc[D];
+    float lj = S.zs[r * 8 + 7];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      float lsp;
+      sigmoid_pair(S.zs[r * 8 + j], y[j], yc[j], lsp);
+      lj += lsp;
+    }
+    out(r, y, yc, lj);
+  }
+  __syncthreads();
+}
+
+// Flow-sampled round of the adaptive integrator: persistent CTAs walk the
+// compacted active list in tiles (as the VEGAS round kernel does) and write
+// one compensated (sum w, sum w^2) slot per tile. With HIST, every point also
+// adds w^2 to its item's histogram over NG uniform bins per dimension (hist,
+// n_items x D x NG), the importance a VEGAS grid refinement starts from.
+template <class PH, int MINB, bool HIST>
+__global__ void __launch_bounds__(THREADS, MINB)
+k_flow_round_sample(const float* __restrict__ recs, ProcConst P, uint64_t seed,
+                    uint64_t event_id_base, const int32_t* __restrict__ active,
+                    const RoundCtl* __restrict__ ctl, uint32_t idx_base, uint32_t pts_item,
+                    const FlowW* __restrict__ W, const FlowB* __restrict__ Bw,
+                    const typename PH::Cache* __restrict__ caches,
+                    const float* __restrict__ feats, Slot* __restrict__ slots,
+                    float* __restrict__ hist) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FlowSampSmem<PH>& S = *reinterpret_cast<FlowSampSmem<PH>*>(smem_raw);
+  const int n_act = ctl->n_active, tpi = ctl->tiles_per_item;
+  const int64_t n_tiles = (int64_t)n_act * tpi;
+  const uint32_t per_tile = ((pts_item + tpi - 1) / tpi + FROWS - 1) / FROWS * FROWS;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int32_t item = active[tile / tpi];
+    const uint32_t k = (uint32_t)(tile % tpi);
+    const int64_t ev = item / PH::NPERM;
+    const int perm = (int)(item % PH::NPERM);
+    {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(caches + item);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&S.cache);
+      for (int t = threadIdx.x; t < (int)(sizeof(typename PH::Cache) / 4); t += blockDim.x)
+        dst[t] = src[t];
+      if (threadIdx.x < FC) S.c[threadIdx.x] = feats[(int64_t)item * FC + threadIdx.x];
+      if (HIST)
+        for (int t = threadIdx.x; t < PH::D * NG; t += blockDim.x) S.hist[t] = 0.f;
+    }
+    __syncthreads();
+    const uint32_t eid = (uint32_t)(event_id_base + (uint64_t)ev);
+    const uint32_t p0 = min(k * per_tile, pts_item);
+    const uint32_t p1 = min(p0 + per_tile, pts_item);
+    Kahan32 a1, a2;
+    uint32_t nbad = 0;
+    if (S.cache.ok) {
+      auto acc = [&](uint32_t, const float (&y)[PH::D], const float (&yc)[PH::D], float lj) {
+        const float w = PH::eval(S.cache, P, y, yc) * __expf(lj);
+        if (isfinite(w)) {
+          a1.add(w);
+          a2.add(w * w);
+          if (HIST) {
+#pragma unroll
+            for (int j = 0; j < PH::D; ++j) {
+              const int b = min((int)(y[j] * (float)NG), NG - 1);
+              atomicAdd(&S.hist[j * NG + b], w * w);
+            }
+          }
+        } else {
+          ++nbad;
+        }
+      };
+#pragma unroll 1
+      for (uint32_t q0 = p0; q0 < p1; q0 += FCH) {
+        const uint32_t nrow = min((uint32_t)FCH, (p1 - q0 + FROWS - 1) / FROWS * FROWS);
+        flow_pass<PH>(S, W, Bw, seed, eid, perm, idx_base, q0, nrow, p1, acc);
+      }
+    }
+    DD v1 = {(double)a1.s, -(double)a1.c}, v2 = {(double)a2.s, -(double)a2.c};
+    v1 = warp_reduce_dd(v1);
+    v2 = warp_reduce_dd(v2);
+    for (int o = 16; o > 0; o >>= 1) nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+      S.red[0][warp] = v1;
+      S.red[1][warp] = v2;
+      S.bad[warp] = nbad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      DD s1 = S.red[0][0], s2 = S.red[1][0];
+      uint32_t b = S.bad[0];
+      for (int w = 1; w < WARPS; ++w) {
+        s1 = two_sum_merge(s1, S.red[0][w]);
+        s2 = two_sum_merge(s2, S.red[1][w]);
+        b += S.bad[w];
+      }
+      Slot sl;
+      sl.s1 = s1.hi;
+      sl.c1 = s1.lo;
+      sl.s2 = s2.hi;
+      sl.c2 = s2.lo;
+      sl.n_bad = b | (S.cache.ok ? 0u : 0x80000000u);
+      sl.pad = 0;
+      slots[tile] = sl;
+    }
+    if (HIST) {
+      float* hg = hist + (int64_t)item * (PH::D * NG);
+      for (int t = threadIdx.x; t < PH::D * NG; t += blockDim.x)
+        if (S.hist[t] != 0.f) atomicAdd(&hg[t], S.hist[t]);
+    }
+    __syncthreads();
+  }
+}
+
+// Flow-sampled points of one item, one output row per point (parity tests):
+// final logits z (y = sigmoid z), log|dy/du| and the weight with its
+// prefactor. CTA b handles points b FCH .. of the n requested.
+template <class PH, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
+k_flow_points(const float* __restrict__ rec, int perm, ProcConst P, TFConst T, uint64_t seed,
+              uint32_t event_id, uint32_t point0, uint32_t n, const FlowW* __restrict__ W,
+              const FlowB* __restrict__ Bw, float* __restrict__ z_out, float* __restrict__ lj_out,
+              double* __restrict__ w_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FlowSampSmem<PH>& S = *reinterpret_cast<FlowSampSmem<PH>*>(smem_raw);
+  if (threadIdx.x == 0) PH::setup(rec, perm, P, T, S.cache);
+  if (threadIdx.x == 32) flow_features(rec, perm, S.c);
+  __syncthreads();
+  const uint32_t q0 = blockIdx.x * FCH;
+  const uint32_t nrow = min((uint32_t)FCH, (n - q0 + FROWS - 1) / FROWS * FROWS);
+  auto put = [&](uint32_t r, const float (&y)[PH::D], const float (&yc)[PH::D], float lj) {
+    const uint32_t i = q0 + r;
+    const float w = S.cache.ok ? PH::eval(S.cache, P, y, yc) * __expf(lj) : 0.f;
+#pragma unroll
+    for (int j = 0; j < PH::D; ++j) z_out[(size_t)i * PH::D + j] = S.zs[r * 8 + j];
+    lj_out[i] = lj;
+    w_out[i] = (double)w * P.prefactor;
+  };
+  flow_pass<PH>(S, W, Bw, seed, event_id, perm, point0 + q0, 0, nrow, n - q0, put);
+}
+
+}  // namespace mem

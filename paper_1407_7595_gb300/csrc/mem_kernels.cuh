@@ -109,19 +109,25 @@ struct AdaptSmem {
   double newg[PH::D * (NG + 1)];
   GridBin gb[PH::D * NG];
   float hist[PH::D * NG];
+  DD red[2][WARPS];
 };
 
-template <class PH, int MINB>
-__global__ void __launch_bounds__(THREADS, MINB)
-k_adapt(const float* __restrict__ recs, ProcConst P, TFConst T, int64_t n_items,
-        uint64_t seed, uint64_t event_id_base, int n_iters, uint32_t n_adapt, double alpha,
-        const double* __restrict__ grid_in, GridBin* __restrict__ grid32,
-        typename PH::Cache* __restrict__ caches) {
+// One CTA adapts the VEGAS grid of one item: n_iters iterations of n_adapt
+// points, each filling the per-bin histograms of w^2 and refining every
+// dimension (one warp per dimension, FP64). With MOM, the moments of the last
+// iteration (sum w, sum w^2, compensated) are written to *mom: the variance of
+// the sampler the adapted grid replaces, for comparing samplers. With hist0,
+// the starting grid is first refined once with the item's histogram
+// hist0[item] (D x NG sums of w^2 over bins of the starting grid, gathered by
+// another sampler).
+template <class PH, bool MOM>
+__device__ void adapt_item(AdaptSmem<PH>& S, const float* __restrict__ recs, const ProcConst& P,
+                           const TFConst& T, int64_t item, uint64_t seed, uint64_t event_id_base,
+                           int n_iters, uint32_t n_adapt, double alpha,
+                           const double* __restrict__ grid_in, GridBin* __restrict__ grid32,
+                           typename PH::Cache* __restrict__ caches, Slot* __restrict__ mom,
+                           const float* __restrict__ hist0 = nullptr) {
   constexpr int D = PH::D;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  AdaptSmem<PH>& S = *reinterpret_cast<AdaptSmem<PH>*>(smem_raw);
-  const int64_t item = blockIdx.x;
-  if (item >= n_items) return;
   const int64_t ev = item / PH::NPERM;
   const int perm = (int)(item % PH::NPERM);
   const float* rec = recs + ev * REC;
@@ -133,8 +139,17 @@ k_adapt(const float* __restrict__ recs, ProcConst P, TFConst T, int64_t n_items,
   for (int t = threadIdx.x; t < D * (NG + 1); t += blockDim.x)
     S.g[t] = grid_in ? grid_in[t] : (double)(t % (NG + 1)) / NG;
   __syncthreads();
+  if (hist0) {
+    for (int t = threadIdx.x; t < D * NG; t += blockDim.x) S.h[t] = (double)hist0[item * (D * NG) + t];
+    __syncthreads();
+    for (int j = threadIdx.x >> 5; j < D; j += WARPS)
+      refine_dim_warp(S.g + j * (NG + 1), S.h + j * NG, S.wk + j * NG, S.cum + j * (NG + 1),
+                      S.newg + j * (NG + 1), alpha);
+    __syncthreads();
+  }
   grid_to_bins<D>(S.g, S.gb);
   const uint32_t eid = (uint32_t)(event_id_base + (uint64_t)ev);
+  Kahan32 a1, a2;
   for (int it = 0; it < n_iters; ++it) {
     for (int t = threadIdx.x; t < D * NG; t += blockDim.x) S.hist[t] = 0.f;
     __syncthreads();
@@ -149,6 +164,10 @@ k_adapt(const float* __restrict__ recs, ProcConst P, TFConst T, int64_t n_items,
           const float w2 = w * w;
 #pragma unroll
           for (int j = 0; j < D; ++j) atomicAdd(&S.hist[j * NG + bin[j]], w2);
+          if (MOM && it == n_iters - 1) {
+            a1.add(w);
+            a2.add(w2);
+          }
         }
       }
     }
@@ -165,6 +184,67 @@ k_adapt(const float* __restrict__ recs, ProcConst P, TFConst T, int64_t n_items,
   }
   GridBin* out = grid32 + item * (D * NG);
   for (int t = threadIdx.x; t < D * NG; t += blockDim.x) out[t] = S.gb[t];
+  if (MOM) {
+    DD v1 = {(double)a1.s, -(double)a1.c}, v2 = {(double)a2.s, -(double)a2.c};
+    v1 = warp_reduce_dd(v1);
+    v2 = warp_reduce_dd(v2);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+      S.red[0][warp] = v1;
+      S.red[1][warp] = v2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      DD s1 = S.red[0][0], s2 = S.red[1][0];
+      for (int w = 1; w < WARPS; ++w) {
+        s1 = two_sum_merge(s1, S.red[0][w]);
+        s2 = two_sum_merge(s2, S.red[1][w]);
+      }
+      Slot sl;
+      sl.s1 = s1.hi;
+      sl.c1 = s1.lo;
+      sl.s2 = s2.hi;
+      sl.c2 = s2.lo;
+      sl.n_bad = S.cache.ok ? 0u : 0x80000000u;
+      sl.pad = 0;
+      *mom = sl;
+    }
+  }
+  __syncthreads();
+}
+
+template <class PH, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
+k_adapt(const float* __restrict__ recs, ProcConst P, TFConst T, int64_t n_items,
+        uint64_t seed, uint64_t event_id_base, int n_iters, uint32_t n_adapt, double alpha,
+        const double* __restrict__ grid_in, GridBin* __restrict__ grid32,
+        typename PH::Cache* __restrict__ caches) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  AdaptSmem<PH>& S = *reinterpret_cast<AdaptSmem<PH>*>(smem_raw);
+  const int64_t item = blockIdx.x;
+  if (item >= n_items) return;
+  adapt_item<PH, false>(S, recs, P, T, item, seed, event_id_base, n_iters, n_adapt, alpha,
+                        grid_in, grid32, caches, nullptr);
+}
+
+// Adaptation of the items in list[0 .. *n_list) (persistent CTAs), with the
+// last iteration's moments per item in mom[item] and an optional starting
+// histogram per item (hist0, see adapt_item).
+template <class PH, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
+k_adapt_list(const float* __restrict__ recs, ProcConst P, TFConst T,
+             const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, uint64_t seed,
+             uint64_t event_id_base, int n_iters, uint32_t n_adapt, double alpha,
+             GridBin* __restrict__ grid32, typename PH::Cache* __restrict__ caches,
+             Slot* __restrict__ mom, const float* __restrict__ hist0) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  AdaptSmem<PH>& S = *reinterpret_cast<AdaptSmem<PH>*>(smem_raw);
+  const int n = *n_list;
+  for (int b = blockIdx.x; b < n; b += gridDim.x) {
+    const int64_t item = list[b];
+    adapt_item<PH, true>(S, recs, P, T, item, seed, event_id_base, n_iters, n_adapt, alpha,
+                         nullptr, grid32, caches, mom + item, hist0);
+  }
 }
 
 template <class PH>

@@ -139,6 +139,20 @@ __device__ __forceinline__ float dgauss_g(const TTCache& c, float Em, float E) {
   return fmaf(c.core_w, __expf(-0.5f * z1 * z1), c.tail_w * __expf(-0.5f * z2 * z2));
 }
 
+// Lexicographic permutation `perm` (0..23) of (0,1,2,3): parton slot k
+// (b, bbar, d, ubar) takes jet p[k].
+__host__ __device__ inline void tt_perm_decode(int perm, int (&p)[4]) {
+  int rem = perm, avail[4] = {0, 1, 2, 3}, n = 4;
+  const int fact[4] = {6, 2, 1, 1};
+  for (int k = 0; k < 4; ++k) {
+    const int q = rem / fact[k];
+    rem %= fact[k];
+    p[k] = avail[q];
+    for (int t = q; t < n - 1; ++t) avail[t] = avail[t + 1];
+    --n;
+  }
+}
+
 struct PhysTT {
   static constexpr int D = 7;
   static constexpr int NPERM = 24;
@@ -146,19 +160,8 @@ struct PhysTT {
 
   __device__ static void setup(const float* rec, int perm, const ProcConst& P, const TFConst& T,
                                Cache& c) {
-    // lexicographic permutations of (0,1,2,3): parton slot k takes jet p[k]
-    int p[4] = {0, 1, 2, 3};
-    {
-      int rem = perm, avail[4] = {0, 1, 2, 3}, n = 4;
-      const int fact[4] = {6, 2, 1, 1};
-      for (int k = 0; k < 4; ++k) {
-        const int q = rem / fact[k];
-        rem %= fact[k];
-        p[k] = avail[q];
-        for (int t = q; t < n - 1; ++t) avail[t] = avail[t + 1];
-        --n;
-      }
-    }
+    int p[4];
+    tt_perm_decode(perm, p);
     c.ok = (rec[3] == 4.f || rec[3] == 2.f) && rec[0] > 0.f && perm >= 0 && perm < 24 &&
            T.jet_core > 0.f && T.jet_tail > 0.f && T.met_sigma > 0.f;
     double nj[4][3];
