@@ -26,6 +26,14 @@ __global__ void k_flow_bf16(const FlowW* __restrict__ W, FlowB* __restrict__ B) 
     const int o = t / FLD, i = t % FLD;
     B->W3t[k][o][i] = __float2bfloat16_rn(i < FH ? W->W3[k][i][o] : 0.f);
   }
+  // first layer, K = 16: [W1a_hi | W1a_hi | W1a_lo | 0] (W1a rows past |A| are zero)
+  for (int t = threadIdx.x; t < FH * FW1; t += blockDim.x) {
+    const int o = t / FW1, i = t % FW1, q = i >> 2;
+    const float v = i < 12 ? W->W1a[k][i & 3][o] : 0.f;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    B->W1t[k][o][i] = q <= 1 ? hi : (q == 2 ? lo : __float2bfloat16_rn(0.f));
+  }
 }
 
 // Forward map of n points sharing one conditioning vector: 128 points per CTA.
@@ -33,9 +41,8 @@ __global__ void __launch_bounds__(128) k_flow_map(const FlowW* __restrict__ W,
                                                    const FlowB* __restrict__ Bw, const float* cond,
                                                    const float* __restrict__ u, int64_t n,
                                                    float* __restrict__ y, float* __restrict__ logj) {
-  __shared__ FlowLayerSmem L;
+  __shared__ FlowInferLayer L;
   __shared__ float zs[64 * 8];
-  __shared__ float st[4][16][8];
   __shared__ float c[FC];
   const int64_t base = (int64_t)blockIdx.x * 64;
   if (threadIdx.x < FC) c[threadIdx.x] = cond[threadIdx.x];
@@ -53,9 +60,9 @@ __global__ void __launch_bounds__(128) k_flow_map(const FlowW* __restrict__ W,
   __syncthreads();
   const int warp = threadIdx.x >> 5;
   for (int k = 0; k < FK; ++k) {
-    flow_load_layer(L, W, Bw, k, c);
+    flow_load_infer(L, W, Bw, k, c);
     __syncthreads();
-    flow_mlp_rows(L, k, zs, warp * 16, st[warp]);
+    flow_layer_rows<1>(L, k, zs, warp * 16);
     __syncthreads();
   }
   for (int t = threadIdx.x; t < 64; t += blockDim.x) {

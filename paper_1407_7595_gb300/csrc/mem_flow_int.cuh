@@ -15,7 +15,8 @@
 namespace mem {
 
 constexpr int FCH = 2048;        // points per pass of a sampling CTA (z state in shared memory)
-constexpr int FROWS = WARPS * 16;  // rows per MLP sweep of the CTA (each warp takes 16)
+constexpr int FRB = 1;           // 16-row blocks per warp sharing each weight fragment
+constexpr int FROWS = WARPS * 16 * FRB;  // rows per MLP sweep of the CTA
 constexpr int FTS = 128;         // training samples per item
 
 // The 16 conditioning features of an item (event record, jet permutation), in
@@ -127,9 +128,8 @@ __global__ void k_flow_normalise(int64_t n_items, int nperm, int per_event,
 // Shared memory of a sampling CTA (about 114 KB: two CTAs per SM).
 template <class PH>
 struct FlowSampSmem {
-  FlowLayerSmem L;
+  FlowInferLayer L;
   float zs[FCH * 8];      // per point: z[0..6], running log-Jacobian
-  float st[WARPS][16][8];
   typename PH::Cache cache;
   float c[FC];
   DD red[2][WARPS];
@@ -179,9 +179,9 @@ __device__ inline void flow_pass(FlowSampSmem<PH>& S, const FlowW* __restrict__ 
   __syncthreads();
   const int warp = threadIdx.x >> 5;
   for (int k = 0; k < FK; ++k) {
-    flow_load_layer(S.L, W, Bw, k, S.c);
+    flow_load_infer(S.L, W, Bw, k, S.c);
     __syncthreads();
-    for (uint32_t rb = warp * 16; rb < nrow; rb += FROWS) flow_mlp_rows(S.L, k, S.zs, rb, S.st[warp]);
+    for (uint32_t r0 = warp * 16 * FRB; r0 < nrow; r0 += FROWS) flow_layer_rows<FRB>(S.L, k, S.zs, r0);
     __syncthreads();
   }
   for (uint32_t r = threadIdx.x; r < nrow; r += THREADS) {

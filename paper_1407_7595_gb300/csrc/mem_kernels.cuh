@@ -21,47 +21,73 @@ constexpr int THREADS = 256;
 constexpr int WARPS = THREADS / 32;
 
 // ---------------------------------------------------------------------------
-// VEGAS refinement of one dimension by one warp, FP64 (Lepage 1978):
-// three-point smoothing of the bin importances h, normalisation,
-// compression w_i = ((1 - r_i)/ln(1/r_i))^alpha, re-binning to equal w per bin.
+// VEGAS refinement of one dimension by one warp (Lepage 1978): three-point
+// smoothing of the bin importances h, normalisation, compression
+// w_i = ((1 - r_i)/ln(1/r_i))^alpha, re-binning to equal w per bin.
 // g: NG+1 edges (updated in place); h: NG importances; wk, cum: scratch.
+// Precision: importances, their sums and the new edges in FP64; the
+// compression exponent (a damping heuristic whose rounding moves edges by
+// ~1e-7 of a bin and cannot bias the estimate) in FP32, because FP64
+// transcendentals run at a small fraction of the FP32 rate on this part.
+// Each lane owns NG/32 consecutive bins; sums are warp scans.
 // ---------------------------------------------------------------------------
 __device__ inline void refine_dim_warp(double* g, const double* h, double* wk, double* cum,
                                        double* newg, double alpha) {
+  static_assert(NG % 32 == 0, "bins per lane");
+  constexpr int BPL = NG / 32;
   const int lane = threadIdx.x & 31;
-  for (int i = lane; i < NG; i += 32) {
+  const int i0 = lane * BPL;
+  double sm[BPL];
+  double part = 0.0;
+#pragma unroll
+  for (int q = 0; q < BPL; ++q) {
+    const int i = i0 + q;
     double s;
     if (i == 0) s = 0.5 * (h[0] + h[1]);
     else if (i == NG - 1) s = 0.5 * (h[NG - 2] + h[NG - 1]);
-    else s = (h[i - 1] + h[i] + h[i + 1]) / 3.0;
-    wk[i] = s;
+    else s = (h[i - 1] + h[i] + h[i + 1]) * (1.0 / 3.0);
+    sm[q] = s;
+    part += s;
   }
-  __syncwarp();
-  double tot = 0.0;
-  if (lane == 0) {
-    for (int i = 0; i < NG; ++i) tot += wk[i];
-  }
-  tot = __shfl_sync(0xffffffffu, tot, 0);
+  double tot = part;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
   if (!(tot > 0.0)) return;
-  for (int i = lane; i < NG; i += 32) {
-    const double r = wk[i] / tot;
+  const double inv = 1.0 / tot;
+  const float af = (float)alpha;
+  double wsum = 0.0;
+#pragma unroll
+  for (int q = 0; q < BPL; ++q) {
+    const double r = sm[q] * inv;
     double w;
-    if (r <= 0.0) w = 0.0;
-    else if (r >= 1.0) w = 1.0;
-    else w = pow((1.0 - r) / log(1.0 / r), alpha);
-    wk[i] = w;
-  }
-  __syncwarp();
-  if (lane == 0) {
-    double acc = 0.0;
-    cum[0] = 0.0;
-    for (int i = 0; i < NG; ++i) {
-      acc += wk[i];
-      cum[i + 1] = acc;
+    if (!(r > 0.0)) {
+      w = 0.0;
+    } else if (r >= 1.0) {
+      w = 1.0;
+    } else {
+      const float rf = fmaxf((float)r, 1e-30f);
+      w = (double)powf((1.f - rf) / -logf(rf), af);
     }
+    sm[q] = w;
+    wsum += w;
   }
+  // exclusive prefix of the lane sums
+  double incl = wsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  double acc = incl - wsum;
+#pragma unroll
+  for (int q = 0; q < BPL; ++q) {
+    wk[i0 + q] = sm[q];
+    cum[i0 + q] = acc;
+    acc += sm[q];
+  }
+  if (lane == 31) cum[NG] = incl;
   __syncwarp();
-  const double per = cum[NG] / NG;
+  const double per = cum[NG] * (1.0 / NG);
   for (int k = lane; k <= NG; k += 32) {
     double e;
     if (k == 0 || k == NG) {

@@ -1,7 +1,9 @@
 """GPU <-> oracle parity through the C ABI (libmem.so), DY and W processes.
 
 * Philox uniforms: bitwise equal to the oracle's.
-* VEGAS refinement: device FP64 refinement equals the oracle's to 1e-12.
+* VEGAS refinement: the device refinement equals the oracle's to 2e-6 in the
+  edges (FP64 sums and edges; the compression exponent ((1-r)/ln(1/r))^alpha,
+  a damping heuristic, is evaluated in FP32 on the device).
 * Integrand at identical Philox points (uniform and adapted grids): FP32 kernel
   vs FP64 oracle, |w_gpu - w_ora| <= 1e-5 |w_ora| + 1e-9 mean|w_ora| on at least
   99.9 % of the points, and the sum over points within 1e-6.
@@ -79,7 +81,8 @@ def test_vegas_refine_matches_oracle(env):
     out = abi.mem_vegas_refine(hist, grids, 1.5)
     for i in range(n):
         ref = O.vegas_refine(hist[i], grids[i], 1.5)
-        assert np.allclose(out[i], ref, rtol=0, atol=1e-12)
+        assert np.allclose(out[i], ref, rtol=0, atol=2e-6)
+        assert np.all(np.diff(out[i], axis=1) >= 0)
 
 
 @pytest.mark.parametrize("kind", KINDS)
