@@ -40,7 +40,7 @@ from paper_1407_7595_gb300 import synth  # noqa: E402
 # FP32 flops (FADD, FMUL = 1; FFMA = 2) executed per integrand evaluation by the
 # frozen-grid kernel, counted with ncu instruction counters (see profiles/);
 # MUFU, integer (Philox) and memory instructions are not counted as flops.
-FLOPS_PER_EVAL = {synth.PROC_DY: None, synth.PROC_W: 406.0, synth.PROC_TTBAR: None}
+FLOPS_PER_EVAL = {synth.PROC_DY: 161.6, synth.PROC_W: 406.0, synth.PROC_TTBAR: 3098.7}
 FP32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 FP32 lanes
 
 WORKLOAD_NAMES = {
@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--points", type=int, default=None, help="override points per event")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-flow", action="store_true", help="skip the learned-proposal A/B leg")
     return ap.parse_args()
 
 
@@ -314,6 +315,8 @@ def run_ours(args):
                "gpu_launches": 3 * args.steps}
         if not args.no_adaptive:
             out["to_1pct"] = adaptive_leg(abi, torch, events, proc, tf, n_ev, rank * n_ev, sp)
+        if not args.no_flow:
+            out["flow_ab"] = flow_ab_leg(abi, torch, sp)
         if not args.no_baseline and world >= 1:
             out["cpu_baseline"] = cpu_baseline(kind, w["seed"])
         print(json.dumps(out), flush=True)
@@ -348,6 +351,120 @@ def adaptive_leg(abi, torch, events, proc, tf, n_ev, eid_base, sp, target=0.01, 
             "converged_fraction": conv,
             "mean_points_per_event": float(used.double().mean().item()),
             "evals_per_s": float(used.double().sum().item()) / m}
+
+
+def flow_ab_leg(abi, torch, sp, n_train=4096, n_eval=4096, batch=304,
+                schedule=((10000, 1e-3), (6000, 3e-4), (4000, 1e-4)), reps=2):
+    """Learned proposal against plain VEGAS on semileptonic ttbar (7 dims x 24
+    permutations). The flow is trained on VEGAS-weighted samples of n_train
+    events (128 per item: 4096 x 24 x 128 = 1.26e7 samples), then n_eval fresh
+    events are integrated to 1 % relative error (cap 2^24 points per event) by
+    each arm; each arm's best setting (by time) from a small sweep is reported.
+    Flow arm: flow pilot -> VEGAS judge seeded by the pilot -> cheaper sampler per
+    item, with the judge's cost ratio measured here (flow point vs VEGAS point)."""
+    K = synth.PROC_TTBAR
+    wl = synth.WORKLOADS["flow"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    proc = abi.mem_create_process(abi.process_desc(K, synth.DEFAULT_PROCESS))
+    tf = abi.tf_desc(synth.DEFAULT_TF[K])
+    ev_tr = abi.mem_upload_events(proc, synth.gen_events(K, n_train, wl["seed"] + 100), sp)
+    ev_ev = abi.mem_upload_events(proc, synth.gen_events(K, n_eval, wl["seed"] + 200), sp)
+    sample_opts = abi.make_opts(n_adapt_iters=5, adapt_points=8192)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    ys, ws, cs = abi.mem_flow_samples(ev_tr, proc, tf, n_train, 1, sample_opts)
+    torch.cuda.synchronize()
+    t_samples = time.perf_counter() - t
+    f = abi.mem_flow_create(1)
+    t = time.perf_counter()
+    trace = []
+    for i, (n, lr) in enumerate(schedule):
+        trace.append(abi.mem_flow_train(f, ys, ws, cs, n, batch, lr, seed=i))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t
+    n_samples = int(ws.numel())
+    del ys, ws, cs
+    ye, we, ce, lje = abi.mem_flow_samples(ev_ev, proc, tf, n_eval, 2, sample_opts, want_logj=True)
+    _, loss_flow = abi.mem_flow_grad(f, ye, we, ce)
+    loss_vegas = float((we.double() * lje.double()).sum().item())
+    n_items = ye.shape[0]
+    del ye, we, ce, lje
+
+    def outputs(n):
+        return (torch.zeros(n, dtype=torch.float64, device=dev), torch.zeros(n, dtype=torch.float64, device=dev),
+                torch.zeros(n, dtype=torch.int64, device=dev), torch.zeros(n, dtype=torch.int32, device=dev))
+
+    def timed(fn, seed0):
+        fn(seed0)          # warm-up (graph build, allocator)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for i in range(reps):
+            t0.record()
+            res = fn(seed0 + 1 + i)
+            t1.record()
+            t1.synchronize()
+            ms.append(t0.elapsed_time(t1))
+        return statistics.mean(ms), res
+
+    def vegas(events, n, seed, **kw):
+        p, e, u, s = outputs(n)
+        abi.mem_integrate_batch([(events, proc, tf)], seed, abi.make_opts(**kw), p, e, u, s, sp)
+        return p, e, u, s
+
+    def flow(events, n, seed, **kw):
+        p, e, u, s = outputs(n)
+        smp = torch.zeros(n * 24, dtype=torch.uint8, device=dev)
+        abi.mem_integrate_flow(events, proc, tf, f, seed, abi.make_opts(**kw), p, e, u, s, smp, sp)
+        return p, e, u, s, smp
+
+    # cost of a flow point relative to a VEGAS point (fixed budgets, every item active)
+    sub = abi.mem_upload_events(proc, synth.gen_events(K, 256, wl["seed"] + 300), sp)
+    fixed = dict(target_rel_err=1e-9, max_points=1 << 20, min_points=1 << 14)
+    ms_f, rf = timed(lambda sd: flow(sub, 256, sd, flow_screen=1e30, **fixed), 100)
+    ms_v, rv = timed(lambda sd: vegas(sub, 256, sd, n_adapt_iters=1, adapt_points=256, **fixed), 200)
+    cost = (ms_f / float(rf[2].sum().item())) / (ms_v / float(rv[2].sum().item()))
+    abi.mem_destroy(sub)
+
+    def summary(ms, res, cfg):
+        p, e, u, s = res[:4]
+        return {"setting": cfg, "events_per_s": n_eval / (ms * 1e-3), "ms": ms,
+                "mean_points_per_event": float(u.double().mean().item()),
+                "median_points_per_event": float(u.double().median().item()),
+                "converged_fraction": float((s == 0).double().mean().item())}
+
+    target = dict(target_rel_err=0.01, max_points=1 << 24)
+    v_runs = []
+    for it, ap in ((3, 4096), (5, 8192), (2, 8192)):
+        ms, res = timed(lambda sd: vegas(ev_ev, n_eval, sd, n_adapt_iters=it, adapt_points=ap, **target), 1000 + 10 * it)
+        v_runs.append((ms, res, f"VEGAS {it} x {ap} adaptation"))
+    f_runs = []
+    for it, ap in ((1, 2048), (2, 4096)):
+        ms, res = timed(lambda sd: flow(ev_ev, n_eval, sd, n_adapt_iters=it, adapt_points=ap, flow_screen=-1.0,
+                                        flow_guided=1, flow_cost=cost, **target), 2000 + 10 * it)
+        f_runs.append((ms, res, f"flow pilot + guided VEGAS judge {it} x {ap}, cost {cost:.2f}"))
+    bv = min(v_runs, key=lambda r: r[0])
+    bf = min(f_runs, key=lambda r: r[0])
+    ok = (bv[1][3] == 0) & (bf[1][3] == 0)
+    pull = ((bf[1][0] - bv[1][0]) / torch.sqrt(bf[1][1] ** 2 + bv[1][1] ** 2))[ok]
+    smp = bf[1][4]
+    out = {"workload": f"semileptonic ttbar, train {n_train} events (seed +100), evaluate {n_eval} "
+                       f"fresh events (seed +200), 1% target, cap 2^24 points/event",
+           "training": {"samples": n_samples, "sample_s": t_samples, "train_s": t_train,
+                        "steps": sum(n for n, _ in schedule), "batch_items": batch,
+                        "loss_first": float(trace[0][:50].mean() / batch),
+                        "loss_last": float(trace[-1][-200:].mean() / batch)},
+           "heldout_loss_per_item": {"flow": loss_flow / n_items, "vegas_density": loss_vegas / n_items},
+           "flow_point_cost_vs_vegas": cost,
+           "vegas": summary(*bv), "flow": summary(*bf),
+           "vegas_sweep": [summary(*r) for r in v_runs], "flow_sweep": [summary(*r) for r in f_runs],
+           "flow_items_kept": float((smp == 1).double().mean().item()),
+           "pull_flow_vs_vegas": {"mean": float(pull.mean().item()), "sd": float(pull.std().item()),
+                                  "n": int(pull.numel())}}
+    out["points_ratio_flow_over_vegas"] = out["flow"]["mean_points_per_event"] / out["vegas"]["mean_points_per_event"]
+    out["time_ratio_flow_over_vegas"] = out["flow"]["ms"] / out["vegas"]["ms"]
+    for h in (f, ev_tr, ev_ev, proc):
+        abi.mem_destroy(h)
+    return out
 
 
 def batch_kernels(kind, cap=1 << 24, min_pts=1 << 14, adapt=8192, iters=5):

@@ -89,9 +89,7 @@ k_round_sample(const float* __restrict__ recs, ProcConst P, uint64_t seed,
         }
       }
     }
-    DD v1 = {(double)a1.s, -(double)a1.c}, v2 = {(double)a2.s, -(double)a2.c};
-    v1 = warp_reduce_dd(v1);
-    v2 = warp_reduce_dd(v2);
+    const DD v1 = warp_reduce_kahan(a1), v2 = warp_reduce_kahan(a2);
     for (int o = 16; o > 0; o >>= 1) nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {

@@ -89,8 +89,11 @@ __device__ __forceinline__ float vegas_map(const GridBin* __restrict__ g, const 
 }
 
 // ---------------------------------------------------------------------------
-// Compensated accumulation: Kahan (1965) per thread in FP32; partial sums are
-// merged with Knuth's TwoSum in FP64.
+// Compensated accumulation: Kahan (1965) per thread in FP32; the 32 lanes of a
+// warp are merged as double-float pairs (Knuth's TwoSum in FP32, error-free in
+// the high parts; ~2^-44 relative), the warps of a CTA with TwoSum in FP64.
+// (FP64 runs at a small fraction of the FP32 rate on this part: a warp-level
+// FP64 butterfly cost ~60 FP64 operations per thread per CTA.)
 // ---------------------------------------------------------------------------
 struct Kahan32 {
   float s = 0.f, c = 0.f;
@@ -112,15 +115,29 @@ __device__ __forceinline__ DD two_sum_merge(DD a, DD b) {
   return {s, err + a.lo + b.lo};
 }
 
-__device__ __forceinline__ DD warp_reduce_dd(DD v) {
+struct FF { float hi, lo; };  // unevaluated sum hi + lo
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb);  // s + e = a.hi + b.hi exactly
+  const float t = e + (a.lo + b.lo);
+  const float h = s + t;
+  return {h, t - (h - s)};
+}
+
+// Warp sum of the lanes' Kahan states (s - c), valid in every lane, as an FP64
+// double-word for the CTA merge.
+__device__ __forceinline__ DD warp_reduce_kahan(const Kahan32& k) {
+  FF v = {k.s, -k.c};
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    DD w;
+    FF w;
     w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
     w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
-    v = two_sum_merge(v, w);
+    v = ff_add(v, w);
   }
-  return v;
+  return {(double)v.hi, (double)v.lo};
 }
 
 // ---------------------------------------------------------------------------

@@ -211,9 +211,7 @@ __device__ void adapt_item(AdaptSmem<PH>& S, const float* __restrict__ recs, con
   GridBin* out = grid32 + item * (D * NG);
   for (int t = threadIdx.x; t < D * NG; t += blockDim.x) out[t] = S.gb[t];
   if (MOM) {
-    DD v1 = {(double)a1.s, -(double)a1.c}, v2 = {(double)a2.s, -(double)a2.c};
-    v1 = warp_reduce_dd(v1);
-    v2 = warp_reduce_dd(v2);
+    const DD v1 = warp_reduce_kahan(a1), v2 = warp_reduce_kahan(a2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
       S.red[0][warp] = v1;
@@ -331,9 +329,7 @@ k_main(const float* __restrict__ recs, ProcConst P, TFConst T, int64_t n_items,
     }
   }
   // Kahan state (s, c) represents s - c
-  DD v1 = {(double)a1.s, -(double)a1.c}, v2 = {(double)a2.s, -(double)a2.c};
-  v1 = warp_reduce_dd(v1);
-  v2 = warp_reduce_dd(v2);
+  const DD v1 = warp_reduce_kahan(a1), v2 = warp_reduce_kahan(a2);
   for (int o = 16; o > 0; o >>= 1) nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
