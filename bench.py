@@ -434,14 +434,17 @@ def flow_ab_leg(abi, torch, sp, n_train=4096, n_eval=4096, batch=304,
 
     target = dict(target_rel_err=0.01, max_points=1 << 24)
     v_runs = []
-    for it, ap in ((3, 4096), (5, 8192), (2, 8192)):
-        ms, res = timed(lambda sd: vegas(ev_ev, n_eval, sd, n_adapt_iters=it, adapt_points=ap, **target), 1000 + 10 * it)
-        v_runs.append((ms, res, f"VEGAS {it} x {ap} adaptation"))
+    for it, ap, mp in ((3, 4096, 1 << 14), (5, 8192, 1 << 14), (2, 8192, 1 << 14), (3, 2048, 1 << 13)):
+        ms, res = timed(lambda sd: vegas(ev_ev, n_eval, sd, n_adapt_iters=it, adapt_points=ap, min_points=mp,
+                                         **target), 1000 + 10 * it + mp)
+        v_runs.append((ms, res, f"VEGAS {it} x {ap} adaptation, first round {mp // 24}/item"))
     f_runs = []
-    for it, ap in ((1, 2048), (2, 4096)):
+    for it, ap, mp in ((1, 2048, 1 << 14), (2, 4096, 1 << 14), (1, 2048, 1 << 13), (1, 4096, 1 << 13)):
         ms, res = timed(lambda sd: flow(ev_ev, n_eval, sd, n_adapt_iters=it, adapt_points=ap, flow_screen=-1.0,
-                                        flow_guided=1, flow_cost=cost, **target), 2000 + 10 * it)
-        f_runs.append((ms, res, f"flow pilot + guided VEGAS judge {it} x {ap}, cost {cost:.2f}"))
+                                        flow_guided=1, flow_cost=cost, min_points=mp, **target),
+                        2000 + 10 * it + mp)
+        f_runs.append((ms, res, f"flow pilot {mp // 24 // 128 * 128 + 128 * (mp // 24 % 128 > 0)}/item + "
+                                f"guided VEGAS judge {it} x {ap}, cost {cost:.2f}"))
     bv = min(v_runs, key=lambda r: r[0])
     bf = min(f_runs, key=lambda r: r[0])
     ok = (bv[1][3] == 0) & (bf[1][3] == 0)

@@ -49,11 +49,24 @@ struct FlowW {
 // K = 16 operand for z_A split into two BF16 parts (z = z_hi + z_lo):
 // k 0-3 = W1a_hi (times z_hi), 4-7 = W1a_hi (times z_lo), 8-11 = W1a_lo
 // (times z_hi), 12-15 = 0, so the product keeps ~16 significant bits.
+// W1u, W2u, W3u are the same three layers as tcgen05 B operands (N x K,
+// K-major, no swizzle; see umma_kmajor): first layer N 128 x K 16 (the split
+// form above), hidden N 128 x K 128, output N 16 x K 128 (rows 8-15 zero).
 struct FlowB {
   __nv_bfloat16 W2t[FK][FH][FLD];
   __nv_bfloat16 W3t[FK][8][FLD];
   __nv_bfloat16 W1t[FK][FH][FW1];
+  __nv_bfloat16 W1u[FK][FH * 16];
+  __nv_bfloat16 W2u[FK][FH * FH];
+  __nv_bfloat16 W3u[FK][16 * FH];
 };
+
+// Element index of (row m, column k) of a K-column tile in the tcgen05
+// canonical K-major layout without swizzle: core matrices of 8 rows x 8
+// elements (128 bytes); LBO = 128 bytes along K, SBO = 16 K bytes along rows.
+__host__ __device__ constexpr int umma_kmajor(int m, int k, int K) {
+  return (m >> 3) * (8 * K) + (k >> 3) * 64 + (m & 7) * 8 + (k & 7);
+}
 // Natural (unpadded) FP32 parameter count, the order of the flat host layout.
 __host__ __device__ constexpr int flow_layer_params(int k) {
   return flow_na(k) * FH + FC * FH + FH + FH * FH + FH + FH * 2 * flow_nb(k) + 2 * flow_nb(k);

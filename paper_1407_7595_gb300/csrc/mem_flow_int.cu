@@ -12,7 +12,7 @@
 
 namespace mem {
 
-constexpr int MINB_FLOW = 2;  // two 110 KB sampling CTAs per SM, <= 128 registers
+constexpr int MINB_FLOW = 2;  // two 112 KB sampling CTAs per SM, <= 128 registers
 
 // Per event, after the flow pilot: an item is judged by VEGAS when its variance
 // per point exceeds tau I^2 / nperm (I = sum of the item means of the event),
@@ -66,9 +66,16 @@ __global__ void k_flow_route(int64_t n_items, const uint8_t* __restrict__ sample
 
 size_t flow_samp_smem() { return sizeof(FlowSampSmem<PhysTT>); }
 
+// Dynamic shared memory of a kernel, with the largest carveout preferred so that
+// two 112 KB sampling CTAs fit on one SM (the occupancy query and the launch
+// otherwise assume the default carveout and place one).
 template <class K>
 cudaError_t set_smem(K kernel, size_t bytes) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  return e;
 }
 
 }  // namespace mem
@@ -176,16 +183,23 @@ mem_status mem_flow_eval_points(const mem_process* process, const mem_tf_desc* t
     return ffail(MEM_ERR_INVALID_ARG, "invalid argument");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t smem = flow_samp_smem();
+  int* d_err = nullptr;
+  int h_err = 0;
   cudaError_t e = set_smem(k_flow_points<PhysTT, MINB_FLOW>, smem);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_err, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
   if (e == cudaSuccess) {
     const unsigned blocks = (unsigned)((n + FCH - 1) / FCH);
     k_flow_points<PhysTT, MINB_FLOW><<<blocks, THREADS, smem, st>>>(
         record, perm, process->pc, make_tf_const_from(tf), seed, event_id, point0, (uint32_t)n,
-        flow->W, flow->B, z, logj, w);
+        flow->W, flow->B, z, logj, w, d_err);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (d_err) cudaFreeAsync(d_err, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail("mem_flow_eval_points", e);
+  if (h_err) return ffail(MEM_ERR_TIMEOUT, "mem_flow_eval_points: a tensor-core wait gave up");
   return MEM_OK;
 }
 
@@ -241,7 +255,11 @@ mem_status mem_integrate_flow(const mem_events* events, const mem_process* proce
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, k_adapt_list<PhysTT, MINB_FLOW>,
                                                       THREADS, smem_a);
   if (e != cudaSuccess) return cuda_fail("mem_integrate_flow", e);
-  const int ctas_f = (occ_f > 0 ? occ_f : 1) * sms, ctas_v = (occ_v > 0 ? occ_v : 1) * sms;
+  // the sampling kernel is built for MINB_FLOW CTAs per SM (launch bounds and
+  // shared memory); the occupancy query can under-report it for kernels that
+  // use tensor memory, and surplus CTAs of the persistent loop only queue
+  occ_f = occ_f > MINB_FLOW ? occ_f : MINB_FLOW;
+  const int ctas_f = occ_f * sms, ctas_v = (occ_v > 0 ? occ_v : 1) * sms;
   const int ctas_a = (occ_a > 0 ? occ_a : 1) * sms;
   const int tt_f = 2 * ctas_f, tt_v = 4 * ctas_v;
   const size_t slots_f = (size_t)n_items + tt_f + 1024, slots_v = (size_t)n_items + tt_v + 1024;
@@ -261,6 +279,7 @@ mem_status mem_integrate_flow(const mem_events* events, const mem_process* proce
   const size_t o_slf = total; total += up(slots_f * sizeof(Slot));
   const size_t o_slv = total; total += up(slots_v * sizeof(Slot));
   const size_t o_state = total; total += up((size_t)n_ev * sizeof(int32_t));
+  const size_t o_eflag = total; total += up(sizeof(int));
   const size_t o_hist = total;
   if (guided) total += up((size_t)n_items * PhysTT::D * NG * sizeof(float));
   const bool dev_out = dev_ptr(prob);
@@ -287,6 +306,8 @@ mem_status mem_integrate_flow(const mem_events* events, const mem_process* proce
   Slot* sl_v = reinterpret_cast<Slot*>(w + o_slv);
   int32_t* ev_state = reinterpret_cast<int32_t*>(w + o_state);
   float* hist = guided ? reinterpret_cast<float*>(w + o_hist) : nullptr;
+  int* d_err = reinterpret_cast<int*>(w + o_eflag);
+  int h_err = 0;
   double* o_prob = dev_out ? prob : reinterpret_cast<double*>(w + o_out);
   double* o_err = dev_out ? err : reinterpret_cast<double*>(w + o_out + up((size_t)n_ev * 8));
   uint64_t* o_used = dev_out ? n_used : reinterpret_cast<uint64_t*>(w + o_out + 2 * up((size_t)n_ev * 8));
@@ -310,6 +331,7 @@ mem_status mem_integrate_flow(const mem_events* events, const mem_process* proce
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     k_flow_setup<PhysTT><<<gi, 256, 0, cs>>>(recs, P, T, n_items, caches, feats);
+    cudaMemsetAsync(d_err, 0, sizeof(int), cs);
     cudaMemsetAsync(acc, 0, (size_t)n_items * sizeof(ItemAcc), cs);
     cudaMemsetAsync(ev_state, 0, (size_t)n_ev * sizeof(int32_t), cs);
     cudaMemsetAsync(flags, 1, (size_t)n_items, cs);
@@ -319,11 +341,11 @@ mem_status mem_integrate_flow(const mem_events* events, const mem_process* proce
       cudaMemsetAsync(hist, 0, (size_t)n_items * PhysTT::D * NG * sizeof(float), cs);
       k_flow_round_sample<PhysTT, MINB_FLOW, true><<<ctas_f, THREADS, smem_f, cs>>>(
           recs, P, seed, eid0, act_f, ctl_f, 0u, (uint32_t)pts0, flow->W, flow->B, caches, feats,
-          sl_f, hist);
+          sl_f, hist, d_err);
     } else {
       k_flow_round_sample<PhysTT, MINB_FLOW, false><<<ctas_f, THREADS, smem_f, cs>>>(
           recs, P, seed, eid0, act_f, ctl_f, 0u, (uint32_t)pts0, flow->W, flow->B, caches, feats,
-          sl_f, nullptr);
+          sl_f, nullptr, d_err);
     }
     k_round_reduce<<<gi, 256, 0, cs>>>(act_f, ctl_f, (uint32_t)pts0, sl_f, acc);
     // screen, VEGAS judge on the flagged items, sampler per item
@@ -343,7 +365,7 @@ mem_status mem_integrate_flow(const mem_events* events, const mem_process* proce
       k_round_compact<<<1, 1024, 0, cs>>>(n_items, flags, act_v, ctl_v, tt_v, route, 1);
       k_flow_round_sample<PhysTT, MINB_FLOW, false><<<ctas_f, THREADS, smem_f, cs>>>(
           recs, P, seed, eid0, act_f, ctl_f, (uint32_t)idx_f, (uint32_t)pts, flow->W, flow->B,
-          caches, feats, sl_f, nullptr);
+          caches, feats, sl_f, nullptr, d_err);
       k_round_sample<PhysTT, MINB_FLOW><<<ctas_v, THREADS, 0, cs>>>(
           recs, P, seed, eid0, act_v, ctl_v, (uint32_t)(adapt + idx_f), (uint32_t)pts, grid32,
           caches, sl_v);
@@ -371,6 +393,8 @@ mem_status mem_integrate_flow(const mem_events* events, const mem_process* proce
     if (e == cudaSuccess && ev_status)
       e = cudaMemcpyAsync(ev_status, o_st, n_ev * 4, cudaMemcpyDeviceToHost, st);
   }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && item_sampler)
     e = cudaMemcpyAsync(item_sampler, sampler, (size_t)n_items, dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
   cudaError_t e2 = cudaFreeAsync(w, st);
@@ -381,6 +405,7 @@ mem_status mem_integrate_flow(const mem_events* events, const mem_process* proce
   if (join) cudaEventDestroy(join);
   if (cs) cudaStreamDestroy(cs);
   if (e != cudaSuccess) return cuda_fail("mem_integrate_flow", e);
+  if (h_err) return ffail(MEM_ERR_TIMEOUT, "mem_integrate_flow: a tensor-core wait gave up");
   return MEM_OK;
 }
 

@@ -7,16 +7,24 @@
 //
 // whose per-point weight is unbiased for the integral whatever the flow's
 // parameters, because |dy/du| is the exact Jacobian of the map that was applied.
+//
+// The coupling MLPs run on the fifth-generation tensor cores: per 128-point tile
+// and layer, one thread issues tcgen05.mma (BF16 operands in shared memory,
+// FP32 accumulators in tensor memory) for the first (K 16), hidden (K 128) and
+// output (N 16) layers; the warps read the accumulators back (tcgen05.ld),
+// add the bias, apply ReLU and repack BF16 operands for the next product.
 #pragma once
 #include "mem_batch.cuh"
 #include "mem_flow.cuh"
 #include "mem_ttbar.cuh"
+#include "mem_umma.cuh"
 
 namespace mem {
 
-constexpr int FCH = 2048;        // points per pass of a sampling CTA (z state in shared memory)
-constexpr int FRB = 1;           // 16-row blocks per warp sharing each weight fragment
-constexpr int FROWS = WARPS * 16 * FRB;  // rows per MLP sweep of the CTA
+constexpr int FCH = 1024;        // points per pass of a sampling CTA (z state in shared memory)
+constexpr int FROWS = 128;       // rows per tensor-core tile (M of the MMA)
+constexpr uint32_t F_TMEM_COLS = 256;  // hidden accumulator 0..127, output 128..143
+constexpr uint32_t F_WAIT_LIMIT = 1u << 20;  // polls of one MMA-completion wait
 constexpr int FTS = 128;         // training samples per item
 
 // The 16 conditioning features of an item (event record, jet permutation), in
@@ -125,16 +133,26 @@ __global__ void k_flow_normalise(int64_t n_items, int nperm, int per_event,
   for (int t = threadIdx.x; t < FTS; t += blockDim.x) ws[item * FTS + t] *= scale;
 }
 
-// Shared memory of a sampling CTA (about 114 KB: two CTAs per SM).
+// Shared memory of a sampling CTA (about 112 KB: two CTAs per SM; tensor
+// memory 256 columns each, the SM's 512 between them).
 template <class PH>
-struct FlowSampSmem {
-  FlowInferLayer L;
-  float zs[FCH * 8];      // per point: z[0..6], running log-Jacobian
+struct __align__(1024) FlowSampSmem {
+  __nv_bfloat16 W2u[FH * FH];     // hidden layer, B operand
+  __nv_bfloat16 Act[FROWS * FH];  // A operand: first-layer input (K 16) or activations (K 128)
+  __nv_bfloat16 W1u[FH * 16];     // first layer, B operand
+  __nv_bfloat16 W3u[16 * FH];     // output layer, B operand
+  float cb1[FH];                  // c W1c + b1 for the CTA's item
+  float b2[FH];
+  float b3[16];
+  float zs[FCH * 8];              // per point: z[0..6], running log-Jacobian
   typename PH::Cache cache;
   float c[FC];
   DD red[2][WARPS];
   uint32_t bad[WARPS];
-  float hist[PH::D * NG];  // w^2 over NG uniform bins per dimension (pilot round)
+  float hist[PH::D * NG];         // w^2 over NG uniform bins per dimension (pilot round)
+  unsigned long long mbar;        // MMA completion
+  uint32_t tmem;                  // tensor-memory base address
+  int abort;
 };
 
 __device__ __forceinline__ void sigmoid_pair(float z, float& y, float& yc, float& lsp) {
@@ -147,17 +165,95 @@ __device__ __forceinline__ void sigmoid_pair(float z, float& y, float& yc, float
   lsp = -fabsf(z) - 2.f * log1pf(t);
 }
 
+// CTA prologue / epilogue of the sampling kernels: the MMA-completion barrier
+// and the tensor-memory allocation (warp 0), released on every exit path.
+template <class PH>
+__device__ inline uint32_t flow_tc_begin(FlowSampSmem<PH>& S) {
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&S.mbar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    S.abort = 0;
+  }
+  if (threadIdx.x < 32) {
+    tmem_alloc(smem_u32(&S.tmem), F_TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  return S.tmem;
+}
+
+template <class PH>
+__device__ inline void flow_tc_end(FlowSampSmem<PH>& S, uint32_t tmem) {
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc_fence_after();
+    tmem_dealloc(tmem, F_TMEM_COLS);
+  }
+}
+
+// Layer k's operands into shared memory (B operands copied as laid out in
+// global memory) and the per-item bias c W1c + b1.
+template <class PH>
+__device__ inline void flow_tc_load_layer(FlowSampSmem<PH>& S, const FlowW* __restrict__ W,
+                                          const FlowB* __restrict__ Bw, int k) {
+  const uint4* s2 = reinterpret_cast<const uint4*>(&Bw->W2u[k][0]);
+  uint4* d2 = reinterpret_cast<uint4*>(S.W2u);
+  for (int t = threadIdx.x; t < FH * FH / 8; t += blockDim.x) d2[t] = s2[t];
+  const uint4* s1 = reinterpret_cast<const uint4*>(&Bw->W1u[k][0]);
+  uint4* d1 = reinterpret_cast<uint4*>(S.W1u);
+  for (int t = threadIdx.x; t < FH * 16 / 8; t += blockDim.x) d1[t] = s1[t];
+  const uint4* s3 = reinterpret_cast<const uint4*>(&Bw->W3u[k][0]);
+  uint4* d3 = reinterpret_cast<uint4*>(S.W3u);
+  for (int t = threadIdx.x; t < 16 * FH / 8; t += blockDim.x) d3[t] = s3[t];
+  for (int n = threadIdx.x; n < FH; n += blockDim.x) {
+    float v = W->b1[k][n];
+#pragma unroll
+    for (int q = 0; q < FC; ++q) v = fmaf(S.c[q], W->W1c[k][q][n], v);
+    S.cb1[n] = v;
+    S.b2[n] = W->b2[k][n];
+  }
+  if (threadIdx.x < 16) S.b3[threadIdx.x] = threadIdx.x < 8 ? W->b3[k][threadIdx.x] : 0.f;
+}
+
+// Accumulator columns col0 .. col0 + 63 of this warp's 32 rows -> bias, ReLU,
+// BF16 -> activation operand (K 128).
+template <class PH>
+__device__ inline void flow_tc_hidden_epilogue(FlowSampSmem<PH>& S, uint32_t tmem,
+                                               const float* bias) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = warp & 3, row = 32 * q + lane;
+  const int cbase = 64 * (warp >> 2);
+  float v[64];
+  tmem_ld64(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)cbase, v);
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) {
+    const int col0 = cbase + 8 * cc;
+    uint32_t pk[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      pk[i] = pack_bf16(fmaxf(v[8 * cc + 2 * i] + bias[col0 + 2 * i], 0.f),
+                        fmaxf(v[8 * cc + 2 * i + 1] + bias[col0 + 2 * i + 1], 0.f));
+    *reinterpret_cast<uint4*>(&S.Act[umma_kmajor(row, col0, FH)]) =
+        make_uint4(pk[0], pk[1], pk[2], pk[3]);
+  }
+}
+
 // One pass of a CTA over points q0 .. q0 + nrow of an item (nrow a multiple of
 // FROWS, at most FCH; rows at or past p1 are computed but not used): base draw,
-// the coupling layers, then out(r, y, yc, log|dy/du|) per used row, threads
-// striding over rows.
+// the coupling layers on the tensor cores, then out(r, y, yc, log|dy/du|) per
+// used row, threads striding over rows. False if an MMA-completion wait gave up
+// (the CTA then stops issuing work).
 template <class PH, class Out>
-__device__ inline void flow_pass(FlowSampSmem<PH>& S, const FlowW* __restrict__ W,
-                                 const FlowB* __restrict__ Bw, uint64_t seed, uint32_t eid,
-                                 int perm, uint32_t idx_base, uint32_t q0, uint32_t nrow,
-                                 uint32_t p1, Out& out) {
+__device__ inline bool flow_pass(FlowSampSmem<PH>& S, uint32_t tmem, uint32_t& phase,
+                                 const FlowW* __restrict__ W, const FlowB* __restrict__ Bw,
+                                 uint64_t seed, uint32_t eid, int perm, uint32_t idx_base,
+                                 uint32_t q0, uint32_t nrow, uint32_t p1, Out& out) {
   constexpr int D = PH::D;
   static_assert(D == FD, "the flow is built for the 7-dimensional ttbar integral");
+  constexpr uint32_t ID_H = umma_idesc_bf16(FROWS, FH), ID_O = umma_idesc_bf16(FROWS, 16);
   for (uint32_t r = threadIdx.x; r < nrow; r += THREADS) {
     const uint32_t p = q0 + r;
     float u[D];
@@ -176,14 +272,98 @@ __device__ inline void flow_pass(FlowSampSmem<PH>& S, const FlowW* __restrict__ 
     }
     S.zs[r * 8 + 7] = lj;
   }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t a_addr = smem_u32(S.Act), w1 = smem_u32(S.W1u), w2 = smem_u32(S.W2u),
+                 w3 = smem_u32(S.W3u), mbar = smem_u32(&S.mbar);
   for (int k = 0; k < FK; ++k) {
-    flow_load_infer(S.L, W, Bw, k, S.c);
+    const int na = flow_na(k);
+    // the previous layer's products are complete and its z updates visible
+    tc_fence_before();
     __syncthreads();
-    for (uint32_t r0 = warp * 16 * FRB; r0 < nrow; r0 += FROWS) flow_layer_rows<FRB>(S.L, k, S.zs, r0);
-    __syncthreads();
+    if (S.abort) return false;
+    flow_tc_load_layer(S, W, Bw, k);
+    for (uint32_t t0 = 0; t0 < nrow; t0 += FROWS) {
+      // first-layer operand (K 16): [z_A hi | z_A lo] and [z_A hi | 0] per row
+      {
+        const int r = threadIdx.x >> 1, half = threadIdx.x & 1;
+        const float* zr = &S.zs[(t0 + r) * 8];
+        float zv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) zv[j] = j < na ? zr[flow_a(k, j)] : 0.f;
+        uint4 v;
+        v.x = pack_bf16(zv[0], zv[1]);
+        v.y = pack_bf16(zv[2], zv[3]);
+        if (half == 0) {
+          v.z = pack_bf16(zv[0] - bf16_hi(zv[0]), zv[1] - bf16_hi(zv[1]));
+          v.w = pack_bf16(zv[2] - bf16_hi(zv[2]), zv[3] - bf16_hi(zv[3]));
+        } else {
+          v.z = 0u;
+          v.w = 0u;
+        }
+        *reinterpret_cast<uint4*>(&S.Act[umma_kmajor(r, 8 * half, 16)]) = v;
+      }
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+        umma_bf16(tmem, umma_desc(a_addr, 128, 256), umma_desc(w1, 128, 256), ID_H, 0u);
+        umma_commit(mbar);
+        if (!mbar_wait(mbar, phase, F_WAIT_LIMIT)) S.abort = 1;
+      }
+      phase ^= 1u;
+      __syncthreads();   // the issuing thread saw the products complete
+      tc_fence_after();
+      flow_tc_hidden_epilogue(S, tmem, S.cb1);
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (S.abort) return false;
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+#pragma unroll
+        for (uint32_t s = 0; s < FH / 16; ++s)
+          umma_bf16(tmem, umma_desc(a_addr + 256 * s, 128, 2048), umma_desc(w2 + 256 * s, 128, 2048),
+                    ID_H, s > 0 ? 1u : 0u);
+        umma_commit(mbar);
+        if (!mbar_wait(mbar, phase, F_WAIT_LIMIT)) S.abort = 1;
+      }
+      phase ^= 1u;
+      __syncthreads();
+      tc_fence_after();
+      flow_tc_hidden_epilogue(S, tmem, S.b2);
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (S.abort) return false;
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+#pragma unroll
+        for (uint32_t s = 0; s < FH / 16; ++s)
+          umma_bf16(tmem + 128, umma_desc(a_addr + 256 * s, 128, 2048),
+                    umma_desc(w3 + 256 * s, 128, 2048), ID_O, s > 0 ? 1u : 0u);
+        umma_commit(mbar);
+        if (!mbar_wait(mbar, phase, F_WAIT_LIMIT)) S.abort = 1;
+      }
+      phase ^= 1u;
+      __syncthreads();
+      tc_fence_after();
+      if (warp < 4) {
+        float v[8];
+        tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + 128u, v);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] += S.b3[i];
+        float* zr = &S.zs[(t0 + 32 * warp + lane) * 8];
+        if (k & 1) flow_update_row<FD / 2 + 1>(zr, v, k);
+        else flow_update_row<FD / 2>(zr, v, k);
+      }
+      // no barrier here: the next tile's operand build touches other rows of zs
+      // and the first 4 KB of Act (read by products that have completed), and
+      // its barrier orders this tile's tensor-memory loads before the next MMA
+    }
   }
+  __syncthreads();
+  if (S.abort) return false;
   for (uint32_t r = threadIdx.x; r < nrow; r += THREADS) {
     if (q0 + r >= p1) continue;
     float y[D], yc[D];
@@ -197,6 +377,7 @@ __device__ inline void flow_pass(FlowSampSmem<PH>& S, const FlowW* __restrict__ 
     out(r, y, yc, lj);
   }
   __syncthreads();
+  return true;
 }
 
 // Flow-sampled round of the adaptive integrator: persistent CTAs walk the
@@ -212,13 +393,16 @@ k_flow_round_sample(const float* __restrict__ recs, ProcConst P, uint64_t seed,
                     const FlowW* __restrict__ W, const FlowB* __restrict__ Bw,
                     const typename PH::Cache* __restrict__ caches,
                     const float* __restrict__ feats, Slot* __restrict__ slots,
-                    float* __restrict__ hist) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  FlowSampSmem<PH>& S = *reinterpret_cast<FlowSampSmem<PH>*>(smem_raw);
+                    float* __restrict__ hist, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char flow_smem[];
+  FlowSampSmem<PH>& S = *reinterpret_cast<FlowSampSmem<PH>*>(flow_smem);
+  const uint32_t tmem = flow_tc_begin(S);
+  uint32_t phase = 0;
+  bool alive = true;
   const int n_act = ctl->n_active, tpi = ctl->tiles_per_item;
   const int64_t n_tiles = (int64_t)n_act * tpi;
   const uint32_t per_tile = ((pts_item + tpi - 1) / tpi + FROWS - 1) / FROWS * FROWS;
-  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  for (int64_t tile = blockIdx.x; tile < n_tiles && alive; tile += gridDim.x) {
     const int32_t item = active[tile / tpi];
     const uint32_t k = (uint32_t)(tile % tpi);
     const int64_t ev = item / PH::NPERM;
@@ -258,7 +442,10 @@ k_flow_round_sample(const float* __restrict__ recs, ProcConst P, uint64_t seed,
 #pragma unroll 1
       for (uint32_t q0 = p0; q0 < p1; q0 += FCH) {
         const uint32_t nrow = min((uint32_t)FCH, (p1 - q0 + FROWS - 1) / FROWS * FROWS);
-        flow_pass<PH>(S, W, Bw, seed, eid, perm, idx_base, q0, nrow, p1, acc);
+        if (!flow_pass<PH>(S, tmem, phase, W, Bw, seed, eid, perm, idx_base, q0, nrow, p1, acc)) {
+          alive = false;
+          break;
+        }
       }
     }
     const DD v1 = warp_reduce_kahan(a1), v2 = warp_reduce_kahan(a2);
@@ -294,6 +481,8 @@ k_flow_round_sample(const float* __restrict__ recs, ProcConst P, uint64_t seed,
     }
     __syncthreads();
   }
+  if (!alive && threadIdx.x == 0) atomicExch(err, 1);
+  flow_tc_end(S, tmem);
 }
 
 // Flow-sampled points of one item, one output row per point (parity tests):
@@ -304,9 +493,11 @@ __global__ void __launch_bounds__(THREADS, MINB)
 k_flow_points(const float* __restrict__ rec, int perm, ProcConst P, TFConst T, uint64_t seed,
               uint32_t event_id, uint32_t point0, uint32_t n, const FlowW* __restrict__ W,
               const FlowB* __restrict__ Bw, float* __restrict__ z_out, float* __restrict__ lj_out,
-              double* __restrict__ w_out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  FlowSampSmem<PH>& S = *reinterpret_cast<FlowSampSmem<PH>*>(smem_raw);
+              double* __restrict__ w_out, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char flow_smem[];
+  FlowSampSmem<PH>& S = *reinterpret_cast<FlowSampSmem<PH>*>(flow_smem);
+  const uint32_t tmem = flow_tc_begin(S);
+  uint32_t phase = 0;
   if (threadIdx.x == 0) PH::setup(rec, perm, P, T, S.cache);
   if (threadIdx.x == 32) flow_features(rec, perm, S.c);
   __syncthreads();
@@ -320,7 +511,11 @@ k_flow_points(const float* __restrict__ rec, int perm, ProcConst P, TFConst T, u
     lj_out[i] = lj;
     w_out[i] = (double)w * P.prefactor;
   };
-  flow_pass<PH>(S, W, Bw, seed, event_id, perm, point0 + q0, 0, nrow, n - q0, put);
+  if (!flow_pass<PH>(S, tmem, phase, W, Bw, seed, event_id, perm, point0 + q0, 0, nrow, n - q0,
+                     put) &&
+      threadIdx.x == 0)
+    atomicExch(err, 1);
+  flow_tc_end(S, tmem);
 }
 
 }  // namespace mem
