@@ -58,13 +58,20 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["w", "dy", "ttbar", "mix"], default="w")
+    ap.add_argument("--workload", choices=["w", "dy", "ttbar", "mix", "flow"], default="w")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the events-to-1%% leg")
     ap.add_argument("--events", type=int, default=None, help="override the event count")
     ap.add_argument("--points", type=int, default=None, help="override points per event")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-flow", action="store_true", help="skip the learned-proposal A/B leg")
+    ap.add_argument("--flow-train", type=int, default=4096, help="training events of the flow A/B")
+    ap.add_argument("--flow-eval", type=int, default=4096, help="fresh events of the flow A/B")
+    ap.add_argument("--flow-steps", type=int, default=20000, help="Adam steps of the flow A/B")
+    ap.add_argument("--flow-arm", choices=["both", "vegas", "flow"], default="both",
+                    help="flow A/B: run one arm at its default setting only (profiling)")
+    ap.add_argument("--flow-cost", type=float, default=None,
+                    help="flow A/B: cost of a flow point in VEGAS points (default: measured)")
     return ap.parse_args()
 
 
@@ -75,6 +82,22 @@ def workload(args):
     if args.points:
         w["n_points"] = args.points
     return w
+
+
+def max_over_ranks(x, world, device):
+    """The largest x over the ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard(rank, n_per_rank):
+    """Rank r integrates its own n_per_rank events with Philox event ids
+    r n_per_rank .. (r + 1) n_per_rank - 1 (disjoint random streams)."""
+    return {"event_id_base": rank * n_per_rank, "seed_offset": 1000003 * rank}
 
 
 def dist_env():
@@ -194,7 +217,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = workload(args)
     kind, n_ev, n_pts = w["proc"], w["n_events"], w["n_points"]
-    seed_r = w["seed"] + 1000003 * rank
+    seed_r = w["seed"] + shard(rank, n_ev)["seed_offset"]
     recs = synth.gen_events(kind, n_ev, seed_r)
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
@@ -209,7 +232,7 @@ def run_ours(args):
     ph = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     for e in ph:
         e.record(stream)  # create the underlying CUDA events
-    opts = abi.make_opts(event_id_base=rank * n_ev, phase_events=ph)
+    opts = abi.make_opts(event_id_base=shard(rank, n_ev)["event_id_base"], phase_events=ph)
     # the per-event budget is split equally over the jet permutations (items)
     n_perm = synth.NPERM[kind]
     n_item = -(-n_pts // n_perm)
@@ -246,10 +269,7 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     total_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     clocks = sampler.stop() if rank == 0 else None
     ms_step = total_ms / args.steps
     value = world * evals_per_step / (ms_step * 1e-3)
@@ -269,15 +289,12 @@ def run_ours(args):
         t = time.perf_counter()
         for i in range(e2e_steps):
             ev2 = abi.mem_upload_events(proc, pinned, sp)
-            abi.mem_integrate(ev2, proc, tf, n_item, 500 + i, abi.make_opts(event_id_base=rank * n_ev),
+            abi.mem_integrate(ev2, proc, tf, n_item, 500 + i, abi.make_opts(event_id_base=shard(rank, n_ev)["event_id_base"]),
                               hp.numpy(), he.numpy(), hu.numpy(), hs.numpy(), sp)
             abi.mem_destroy(ev2)
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t) / e2e_steps
-        if world > 1:
-            tt = torch.tensor([dt], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            dt = float(tt.item())
+        dt = max_over_ranks(dt, world, dev)
         e2e = {"value": world * evals_per_step / dt, "unit": "integrand evals/s",
                "h2d_bytes_per_step": int(recs.nbytes),
                "d2h_bytes_per_step": int(n_ev * (8 + 8 + 8 + 4)),
@@ -314,9 +331,11 @@ def run_ours(args):
                "roofline": roof, "clocks": clocks, "e2e": e2e,
                "gpu_launches": 3 * args.steps}
         if not args.no_adaptive:
-            out["to_1pct"] = adaptive_leg(abi, torch, events, proc, tf, n_ev, rank * n_ev, sp)
+            out["to_1pct"] = adaptive_leg(abi, torch, events, proc, tf, n_ev,
+                                          shard(rank, n_ev)["event_id_base"], sp)
         if not args.no_flow:
-            out["flow_ab"] = flow_ab_leg(abi, torch, sp)
+            out["flow_ab"] = flow_ab_leg(abi, torch, sp, args.flow_train, args.flow_eval,
+                                         steps=args.flow_steps)
         if not args.no_baseline and world >= 1:
             out["cpu_baseline"] = cpu_baseline(kind, w["seed"])
         print(json.dumps(out), flush=True)
@@ -353,8 +372,8 @@ def adaptive_leg(abi, torch, events, proc, tf, n_ev, eid_base, sp, target=0.01, 
             "evals_per_s": float(used.double().sum().item()) / m}
 
 
-def flow_ab_leg(abi, torch, sp, n_train=4096, n_eval=4096, batch=304,
-                schedule=((10000, 1e-3), (6000, 3e-4), (4000, 1e-4)), reps=2):
+def flow_ab_leg(abi, torch, sp, n_train=4096, n_eval=4096, batch=304, steps=20000, reps=2,
+                arm="both", cost=None):
     """Learned proposal against plain VEGAS on semileptonic ttbar (7 dims x 24
     permutations). The flow is trained on VEGAS-weighted samples of n_train
     events (128 per item: 4096 x 24 x 128 = 1.26e7 samples), then n_eval fresh
@@ -364,31 +383,36 @@ def flow_ab_leg(abi, torch, sp, n_train=4096, n_eval=4096, batch=304,
     item, with the judge's cost ratio measured here (flow point vs VEGAS point)."""
     K = synth.PROC_TTBAR
     wl = synth.WORKLOADS["flow"]
+    # learning-rate schedule: 1e-3, then 3e-4, then 1e-4 (50 / 30 / 20 % of the steps)
+    schedule = ((steps // 2, 1e-3), (steps * 3 // 10, 3e-4), (steps - steps // 2 - steps * 3 // 10, 1e-4))
     dev = torch.device("cuda", torch.cuda.current_device())
     proc = abi.mem_create_process(abi.process_desc(K, synth.DEFAULT_PROCESS))
     tf = abi.tf_desc(synth.DEFAULT_TF[K])
     ev_tr = abi.mem_upload_events(proc, synth.gen_events(K, n_train, wl["seed"] + 100), sp)
     ev_ev = abi.mem_upload_events(proc, synth.gen_events(K, n_eval, wl["seed"] + 200), sp)
     sample_opts = abi.make_opts(n_adapt_iters=5, adapt_points=8192)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    ys, ws, cs = abi.mem_flow_samples(ev_tr, proc, tf, n_train, 1, sample_opts)
-    torch.cuda.synchronize()
-    t_samples = time.perf_counter() - t
     f = abi.mem_flow_create(1)
-    t = time.perf_counter()
-    trace = []
-    for i, (n, lr) in enumerate(schedule):
-        trace.append(abi.mem_flow_train(f, ys, ws, cs, n, batch, lr, seed=i))
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t
-    n_samples = int(ws.numel())
-    del ys, ws, cs
-    ye, we, ce, lje = abi.mem_flow_samples(ev_ev, proc, tf, n_eval, 2, sample_opts, want_logj=True)
-    _, loss_flow = abi.mem_flow_grad(f, ye, we, ce)
-    loss_vegas = float((we.double() * lje.double()).sum().item())
-    n_items = ye.shape[0]
-    del ye, we, ce, lje
+    t_samples = t_train = 0.0
+    n_samples, trace, loss_flow, loss_vegas, n_items = 0, [np.zeros(1)], 0.0, 0.0, 1
+    if arm != "vegas":
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ys, ws, cs = abi.mem_flow_samples(ev_tr, proc, tf, n_train, 1, sample_opts)
+        torch.cuda.synchronize()
+        t_samples = time.perf_counter() - t
+        t = time.perf_counter()
+        trace = []
+        for i, (n, lr) in enumerate(schedule):
+            trace.append(abi.mem_flow_train(f, ys, ws, cs, n, batch, lr, seed=i))
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t
+        n_samples = int(ws.numel())
+        del ys, ws, cs
+        ye, we, ce, lje = abi.mem_flow_samples(ev_ev, proc, tf, n_eval, 2, sample_opts, want_logj=True)
+        _, loss_flow = abi.mem_flow_grad(f, ye, we, ce)
+        loss_vegas = float((we.double() * lje.double()).sum().item())
+        n_items = ye.shape[0]
+        del ye, we, ce, lje
 
     def outputs(n):
         return (torch.zeros(n, dtype=torch.float64, device=dev), torch.zeros(n, dtype=torch.float64, device=dev),
@@ -418,12 +442,13 @@ def flow_ab_leg(abi, torch, sp, n_train=4096, n_eval=4096, batch=304,
         return p, e, u, s, smp
 
     # cost of a flow point relative to a VEGAS point (fixed budgets, every item active)
-    sub = abi.mem_upload_events(proc, synth.gen_events(K, 256, wl["seed"] + 300), sp)
-    fixed = dict(target_rel_err=1e-9, max_points=1 << 20, min_points=1 << 14)
-    ms_f, rf = timed(lambda sd: flow(sub, 256, sd, flow_screen=1e30, **fixed), 100)
-    ms_v, rv = timed(lambda sd: vegas(sub, 256, sd, n_adapt_iters=1, adapt_points=256, **fixed), 200)
-    cost = (ms_f / float(rf[2].sum().item())) / (ms_v / float(rv[2].sum().item()))
-    abi.mem_destroy(sub)
+    if cost is None:
+        sub = abi.mem_upload_events(proc, synth.gen_events(K, 256, wl["seed"] + 300), sp)
+        fixed = dict(target_rel_err=1e-9, max_points=1 << 20, min_points=1 << 14)
+        ms_f, rf = timed(lambda sd: flow(sub, 256, sd, flow_screen=1e30, **fixed), 100)
+        ms_v, rv = timed(lambda sd: vegas(sub, 256, sd, n_adapt_iters=1, adapt_points=256, **fixed), 200)
+        cost = (ms_f / float(rf[2].sum().item())) / (ms_v / float(rv[2].sum().item()))
+        abi.mem_destroy(sub)
 
     def summary(ms, res, cfg):
         p, e, u, s = res[:4]
@@ -433,18 +458,29 @@ def flow_ab_leg(abi, torch, sp, n_train=4096, n_eval=4096, batch=304,
                 "converged_fraction": float((s == 0).double().mean().item())}
 
     target = dict(target_rel_err=0.01, max_points=1 << 24)
+    v_set = ((3, 4096, 1 << 14), (5, 8192, 1 << 14), (2, 8192, 1 << 14), (3, 2048, 1 << 13))
+    f_set = ((1, 2048, 1 << 14), (2, 4096, 1 << 14), (1, 2048, 1 << 13), (1, 4096, 1 << 13))
+    if arm == "vegas":
+        v_set, f_set = v_set[:1], ()
+    elif arm == "flow":
+        v_set, f_set = (), f_set[:1]
     v_runs = []
-    for it, ap, mp in ((3, 4096, 1 << 14), (5, 8192, 1 << 14), (2, 8192, 1 << 14), (3, 2048, 1 << 13)):
+    for it, ap, mp in v_set:
         ms, res = timed(lambda sd: vegas(ev_ev, n_eval, sd, n_adapt_iters=it, adapt_points=ap, min_points=mp,
                                          **target), 1000 + 10 * it + mp)
         v_runs.append((ms, res, f"VEGAS {it} x {ap} adaptation, first round {mp // 24}/item"))
     f_runs = []
-    for it, ap, mp in ((1, 2048, 1 << 14), (2, 4096, 1 << 14), (1, 2048, 1 << 13), (1, 4096, 1 << 13)):
+    for it, ap, mp in f_set:
         ms, res = timed(lambda sd: flow(ev_ev, n_eval, sd, n_adapt_iters=it, adapt_points=ap, flow_screen=-1.0,
                                         flow_guided=1, flow_cost=cost, min_points=mp, **target),
                         2000 + 10 * it + mp)
         f_runs.append((ms, res, f"flow pilot {mp // 24 // 128 * 128 + 128 * (mp // 24 % 128 > 0)}/item + "
                                 f"guided VEGAS judge {it} x {ap}, cost {cost:.2f}"))
+    if not v_runs or not f_runs:   # one arm only (profiling)
+        for h in (f, ev_tr, ev_ev, proc):
+            abi.mem_destroy(h)
+        r = (v_runs or f_runs)[0]
+        return {"arm": arm, "run": summary(*r), "flow_point_cost_vs_vegas": cost}
     bv = min(v_runs, key=lambda r: r[0])
     bf = min(f_runs, key=lambda r: r[0])
     ok = (bv[1][3] == 0) & (bf[1][3] == 0)
@@ -495,7 +531,7 @@ def run_mix(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = workload(args)
     n_ev = w["n_events"]
-    recs = synth.gen_mix(n_ev, w["seed"] + 1000003 * rank)
+    recs = synth.gen_mix(n_ev, w["seed"] + shard(rank, n_ev)["seed_offset"])
     sp = torch.cuda.current_stream().cuda_stream
     groups, handles = [], []
     for kind in (synth.PROC_DY, synth.PROC_W, synth.PROC_TTBAR):
@@ -513,7 +549,31 @@ def run_mix(args):
     used = torch.zeros(n_ev, dtype=torch.int64, device=dev)
     st = torch.zeros(n_ev, dtype=torch.int32, device=dev)
     target = 0.01
-    opts = abi.make_opts(target_rel_err=target, max_points=1 << 24, event_id_base=rank * n_ev)
+    base = dict(target_rel_err=target, max_points=1 << 24,
+                event_id_base=shard(rank, n_ev)["event_id_base"])
+    # autotune each process's schedule on a calibration sample (its first 256 events)
+    t_tune = time.perf_counter()
+    plans, tuned = [], []
+    kinds_present = [k for k in (synth.PROC_DY, synth.PROC_W, synth.PROC_TTBAR) if (recs[:, 27] == k).any()]
+    for (ev, proc, tf), kind in zip(groups, kinds_present):
+        sub = np.ascontiguousarray(recs[recs[:, 27] == kind][:256])
+        cal = abi.mem_upload_events(proc, sub, sp)
+        plan, rate, tried = abi.mem_autotune(cal, proc, tf, 77, abi.make_opts(**base), sp)
+        abi.mem_destroy(cal)
+        plans.append(plan)
+        tuned.append({"process": int(kind), "plan": plan.as_dict(), "calibration_events_per_s": rate,
+                      "plans_timed": tried})
+    t_tune = time.perf_counter() - t_tune
+    opts = abi.make_opts(plans=plans, **base)
+    # the library's default schedule, for reference
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d_opts = abi.make_opts(**base)
+    abi.mem_integrate_batch(groups, 8000, d_opts, prob, err, used, st, sp)
+    t0.record()
+    abi.mem_integrate_batch(groups, 8001, d_opts, prob, err, used, st, sp)
+    t1.record()
+    t1.synchronize()
+    default_ms = t0.elapsed_time(t1)
     for i in range(args.warmup):
         abi.mem_integrate_batch(groups, 9000 + i, opts, prob, err, used, st, sp)
     torch.cuda.synchronize()
@@ -532,10 +592,7 @@ def run_mix(args):
         ms.append(t0.elapsed_time(t1))
     torch.cuda.synchronize()
     total_ms = sum(ms)
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     clocks = sampler.stop() if rank == 0 else None
     ms_step = total_ms / args.steps
     if rank == 0:
@@ -553,12 +610,41 @@ def run_mix(args):
                           "launch": "one mem_integrate_batch call = one CUDA graph per step"},
                "converged_fraction": conv, "integrand_evals_per_s": evals / (ms_step * 1e-3),
                "mean_points_per_event": evals / n_ev, "clocks": clocks,
-               "gpu_launches": args.steps * sum(batch_kernels(k) for k in set(kinds.tolist()))}
+               "autotune": {"seconds": t_tune, "groups": tuned,
+                            "default_schedule_events_per_s": world * n_ev / (default_ms * 1e-3)},
+               "gpu_launches": args.steps * sum(
+                   batch_kernels(k, min_pts=pl.min_points, adapt=pl.adapt_points, iters=pl.n_adapt_iters)
+                   for k, pl in zip(kinds_present, plans))}
         print(json.dumps(out), flush=True)
     for h in handles:
         abi.mem_destroy(h)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_flow(args):
+    """The learned-proposal A/B alone (ttbar): one JSON line whose value is the flow
+    arm's events brought to 1 % per second; the VEGAS arm and the sweeps inside."""
+    import torch
+    from paper_1407_7595_gb300 import abi
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    sp = torch.cuda.current_stream().cuda_stream
+    sampler = ClockSampler(local)
+    sampler.start()
+    ab = flow_ab_leg(abi, torch, sp, args.flow_train, args.flow_eval, steps=args.flow_steps,
+                     reps=max(1, args.steps), arm=args.flow_arm, cost=args.flow_cost)
+    clocks = sampler.stop()
+    main_arm = ab["flow"] if "flow" in ab else ab["run"]
+    out = {"metric": "events integrated to 1% relative error per second (learned proposal)",
+           "value": main_arm["events_per_s"], "unit": "events/s", "n_gpus": 1,
+           "steps": max(1, args.steps), "warmup": 1, "ms_per_step": main_arm["ms"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+           "data": "synthetic", "impl": "ours",
+           "config": {"workload": f"semileptonic ttbar learned proposal vs VEGAS, {args.flow_eval} "
+                                  f"fresh events to 1% (arm: {args.flow_arm})"},
+           "flow_ab": ab, "clocks": clocks}
+    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -567,6 +653,8 @@ def main():
         run_reference(args)
     elif args.workload == "mix":
         run_mix(args)
+    elif args.workload == "flow":
+        run_flow(args)
     else:
         run_ours(args)
 

@@ -76,6 +76,16 @@ typedef struct {
   double met_sigma, met_box_k;
 } mem_tf_desc;
 
+/* Schedule of one process group in mem_integrate_batch, as chosen by
+ * mem_autotune or by hand; a field left 0 takes the mem_opts value (or its
+ * default). */
+typedef struct {
+  int32_t n_adapt_iters;  /* VEGAS adaptation iterations */
+  int32_t tiles_per_cta;  /* sampling tiles per persistent CTA and round (0 = 4) */
+  uint64_t adapt_points;  /* points per item per adaptation iteration */
+  uint64_t min_points;    /* points per event of the first frozen-grid round */
+} mem_plan;
+
 /* Integration options (NULL = defaults: fixed n_points per event, 5 VEGAS
  * adaptation iterations of min(2^14, n/8) points, alpha = 1.5). */
 typedef struct {
@@ -102,6 +112,8 @@ typedef struct {
   double flow_cost;       /* mem_integrate_flow: time of a flow point relative to a VEGAS
                              point; the judge keeps the flow when
                              var_flow * flow_cost <= var_vegas (0 = 1.0) */
+  const mem_plan* plans;  /* mem_integrate_batch: optional HOST array, one schedule per
+                             group (NULL = the fields above for every group) */
 } mem_opts;
 
 /* Number of integration dimensions / jet permutations of a process kind (-1 if invalid). */
@@ -155,6 +167,20 @@ mem_status mem_integrate_batch(int32_t n_groups, const mem_events* const* events
                                const mem_process* const* procs, const mem_tf_desc* const* tfs,
                                uint64_t seed, const mem_opts* opts, double* prob, double* err,
                                uint64_t* n_used, int32_t* ev_status, void* stream);
+
+/* Autotuner of the batched schedule for one process: every candidate plan
+ * (VEGAS adaptation of 2-5 iterations of 2048-8192 points per item; first
+ * round 2^13-2^15 points per event; 2-8 sampling tiles per CTA) integrates
+ * the given calibration events to opts->target_rel_err (cap opts->max_points)
+ * with mem_integrate_batch, timed with CUDA events on `stream` (one warm-up,
+ * best of two runs); the plan with the most converged events per second is
+ * written to *best and its rate to *events_per_s (optional). The search is
+ * two-staged (adaptation plan first, then first-round size and tiles) over a
+ * fixed list; n_tried (optional) receives the number of plans timed.
+ * Synchronous. Errors as mem_integrate_batch. */
+mem_status mem_autotune(const mem_events* events, const mem_process* process,
+                        const mem_tf_desc* tf, uint64_t seed, const mem_opts* opts,
+                        mem_plan* best, double* events_per_s, int32_t* n_tried, void* stream);
 
 /* Working memory of mem_integrate_noalloc, fixed at build time (32 MiB per GPU). */
 #define MEM_NOALLOC_SCRATCH_BYTES (32u << 20)

@@ -43,13 +43,21 @@ class mem_tf_desc(C.Structure):
                                           "met_sigma", "met_box_k")]
 
 
+class mem_plan(C.Structure):
+    _fields_ = [("n_adapt_iters", C.c_int32), ("tiles_per_cta", C.c_int32),
+                ("adapt_points", C.c_uint64), ("min_points", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class mem_opts(C.Structure):
     _fields_ = [("target_rel_err", C.c_double), ("max_points", C.c_uint64),
                 ("min_points", C.c_uint64), ("n_adapt_iters", C.c_int32),
                 ("flow_guided", C.c_int32), ("adapt_points", C.c_uint64), ("alpha", C.c_double),
                 ("grid_in", C.POINTER(C.c_double)), ("event_id_base", C.c_uint64),
                 ("phase_events", C.c_void_p), ("flow_screen", C.c_double),
-                ("flow_cost", C.c_double)]
+                ("flow_cost", C.c_double), ("plans", C.POINTER(mem_plan))]
 
 
 _lib = None
@@ -84,6 +92,8 @@ SIGNATURES = [
     ("mem_flow_eval_points", C.c_int, [_vp, C.POINTER(mem_tf_desc), _vp, _vp, C.c_int32,
                                        C.c_uint64, C.c_uint32, C.c_uint32, C.c_int64, _vp, _vp,
                                        _vp, _vp]),
+    ("mem_autotune", C.c_int, [_vp, _vp, C.POINTER(mem_tf_desc), C.c_uint64, C.POINTER(mem_opts),
+                               C.POINTER(mem_plan), C.POINTER(C.c_double), C.POINTER(C.c_int32), _vp]),
     ("mem_destroy", None, [_vp]),
     ("mem_last_error", C.c_char_p, []),
     ("mem_eval_points", C.c_int, [_vp, _vp, C.POINTER(mem_tf_desc), C.c_int64, C.c_int32,
@@ -143,7 +153,7 @@ def tf_desc(params):
 
 def make_opts(n_adapt_iters=5, adapt_points=0, alpha=1.5, grid_in=None, event_id_base=0,
               target_rel_err=0.0, max_points=0, min_points=0, phase_events=None,
-              flow_screen=0.0, flow_cost=0.0, flow_guided=0):
+              flow_screen=0.0, flow_cost=0.0, flow_guided=0, plans=None):
     """phase_events: optional list of 4 torch.cuda.Event (created with
     enable_timing=True) recorded at the phase boundaries on the call's stream."""
     o = mem_opts()
@@ -161,12 +171,16 @@ def make_opts(n_adapt_iters=5, adapt_points=0, alpha=1.5, grid_in=None, event_id
     o.event_id_base = event_id_base
     o.flow_screen = flow_screen
     o.flow_cost = flow_cost
+    plan_arr = None
+    if plans is not None:
+        plan_arr = (mem_plan * len(plans))(*plans)
+        o.plans = C.cast(plan_arr, C.POINTER(mem_plan))
     ev_arr = None
     if phase_events is not None:
         assert len(phase_events) == 4
         ev_arr = (C.c_void_p * 4)(*[e.cuda_event for e in phase_events])
         o.phase_events = C.cast(ev_arr, C.c_void_p)
-    o._keep = (keep, ev_arr)
+    o._keep = (keep, ev_arr, plan_arr)
     return o
 
 
@@ -210,6 +224,17 @@ def mem_integrate_batch(groups, seed, opts, prob, err, n_used=None, ev_status=No
     _check(lib().mem_integrate_batch(n, C.cast(evs, C.c_void_p), C.cast(prs, C.c_void_p),
                                      C.cast(tfs, C.c_void_p), seed, C.byref(opts), _ptr(prob),
                                      _ptr(err), _ptr(n_used), _ptr(ev_status), stream))
+
+
+def mem_autotune(events, proc, tf, seed, opts, stream=None):
+    """Best batched schedule for one process on calibration events:
+    (mem_plan, converged events/s, plans timed)."""
+    best = mem_plan()
+    rate = C.c_double()
+    tried = C.c_int32()
+    _check(lib().mem_autotune(events, proc, C.byref(tf), seed, C.byref(opts), C.byref(best),
+                              C.byref(rate), C.byref(tried), stream))
+    return best, rate.value, tried.value
 
 
 def mem_integrate_noalloc(desc, tf, records, n_points, seed, event_id_base, prob, err,

@@ -186,10 +186,7 @@ extern "C" mem_status mem_integrate_batch(int32_t n_groups, const mem_events* co
     return bfail(MEM_ERR_INVALID_ARG, "invalid argument");
   if (!(opts->target_rel_err > 0.0)) return bfail(MEM_ERR_INVALID_ARG, "target_rel_err must be > 0");
   if (opts->flow_guided != 0) return bfail(MEM_ERR_INVALID_ARG, "flow_guided must be 0");
-  const int iters = opts->n_adapt_iters;
-  if (iters < 1 || iters > 64) return bfail(MEM_ERR_INVALID_ARG, "n_adapt_iters must be in [1, 64] for adaptive budgets");
   const uint64_t cap_ev = opts->max_points ? opts->max_points : (uint64_t)1 << 24;
-  const uint64_t min_ev = opts->min_points ? opts->min_points : (uint64_t)1 << 14;
   const double alpha = opts->alpha > 0 ? opts->alpha : 1.5;
   if (opts->grid_in) return bfail(MEM_ERR_INVALID_ARG, "grid_in is not supported with adaptive budgets");
 
@@ -217,9 +214,22 @@ extern "C" mem_status mem_integrate_batch(int32_t n_groups, const mem_events* co
       return bfail(MEM_ERR_INVALID_ARG, "lepton TF parameters invalid");
     if (kind != PROC_DY && !(T.met_sigma > 0 && T.met_box_k > 0))
       return bfail(MEM_ERR_INVALID_ARG, "MET TF parameters invalid");
+    // this group's schedule: its plan entry where given, else the common options
+    const mem_plan* pl = opts->plans ? &opts->plans[g] : nullptr;
+    const int iters = pl && pl->n_adapt_iters ? pl->n_adapt_iters : opts->n_adapt_iters;
+    if (iters < 1 || iters > 64)
+      return bfail(MEM_ERR_INVALID_ARG, "group " + std::to_string(g) + ": n_adapt_iters must be in [1, 64]");
+    const uint64_t adapt_pts = pl && pl->adapt_points ? pl->adapt_points
+                                                      : (opts->adapt_points ? opts->adapt_points : 8192);
+    const uint64_t min_ev = pl && pl->min_points ? pl->min_points
+                                                 : (opts->min_points ? opts->min_points : (uint64_t)1 << 14);
+    const int tiles = pl && pl->tiles_per_cta ? pl->tiles_per_cta : 4;
+    if (adapt_pts > (1u << 24) || tiles < 1 || tiles > 64)
+      return bfail(MEM_ERR_INVALID_ARG, "group " + std::to_string(g) + ": plan out of range");
     Plan& p = plans[g];
     BatchArgs& b = p.b;
     IntegrateArgs& a = b.base;
+    b.tiles_per_cta = tiles;
     a.recs = ev->d_recs;
     a.n_events = ev->n;
     a.n_items = ev->n * np;
@@ -228,7 +238,7 @@ extern "C" mem_status mem_integrate_batch(int32_t n_groups, const mem_events* co
     a.seed = seed;
     a.event_id_base = opts->event_id_base + (uint64_t)ev_total;
     a.n_iters = iters;
-    a.n_adapt = (uint32_t)(opts->adapt_points ? opts->adapt_points : 8192);
+    a.n_adapt = (uint32_t)adapt_pts;
     a.alpha = alpha;
     a.grid_in = nullptr;
     a.phase_events = nullptr;

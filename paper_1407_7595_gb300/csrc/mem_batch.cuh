@@ -159,6 +159,7 @@ struct BatchArgs {
   Slot* slots;
   int32_t* ev_state;         // 0 active, 1 converged, 2 cap reached, 3 invalid record
   int grid_ctas;             // persistent sampling CTAs
+  int tiles_per_cta;         // sampling tiles per CTA and round
   int target_tiles;
   double* prob;              // device outputs of this group (n_events each)
   double* err;
@@ -209,7 +210,7 @@ cudaError_t run_batch(BatchArgs b, cudaStream_t st) {
       a.recs, a.P, a.T, a.n_items, a.seed, a.event_id_base, a.n_iters, a.n_adapt, a.alpha,
       a.grid_in, a.grid32, reinterpret_cast<typename PH::Cache*>(a.caches));
   b.grid_ctas = round_sample_ctas<PH, MINB>();
-  b.target_tiles = 4 * b.grid_ctas;
+  b.target_tiles = b.tiles_per_cta * b.grid_ctas;
   cudaMemsetAsync(b.flags, 1, (size_t)a.n_items, st);
   cudaMemsetAsync(b.acc, 0, (size_t)a.n_items * sizeof(ItemAcc), st);
   cudaMemsetAsync(b.ev_state, 0, (size_t)a.n_events * sizeof(int32_t), st);

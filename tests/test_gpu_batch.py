@@ -85,3 +85,37 @@ def test_single_group_through_mem_integrate(env):
         abi.mem_integrate_batch([(g.events, g.proc, g.tf)], 3,
                                 abi.make_opts(target_rel_err=0.0), prob, err)
     g.close()
+
+
+def test_per_group_plans_and_autotune(env):
+    """Each group follows its own schedule (mem_plan), and the autotuner returns
+    a plan from its candidate list that integrates its calibration events."""
+    abi, synth, O = env
+    groups = [make_group(abi, synth, k, n, 8300 + k) for k, n in ((0, 16), (2, 2))]
+    n_tot = sum(len(r) for r, _ in groups)
+    prob, err = np.zeros(n_tot), np.zeros(n_tot)
+    used, st = np.zeros(n_tot, dtype=np.uint64), np.zeros(n_tot, dtype=np.int32)
+    plans = [abi.mem_plan(n_adapt_iters=2, tiles_per_cta=2, adapt_points=1024, min_points=1 << 13),
+             abi.mem_plan(n_adapt_iters=3, tiles_per_cta=8, adapt_points=2048, min_points=1 << 14)]
+    opts = abi.make_opts(target_rel_err=0.02, max_points=1 << 22, plans=plans)
+    abi.mem_integrate_batch([(g.events, g.proc, g.tf) for _, g in groups], 5, opts, prob, err, used, st)
+    assert np.all((st == 0) | (st == 3))
+    # adaptation points are part of n_used: 2 x 1024 per DY event, >= one ttbar item's 3 x 2048
+    assert np.all(used[:16] >= 2 * 1024 + ((1 << 13) // 256) * 256)
+    assert np.all(used[16:] >= 3 * 2048)
+    ok = st == 0
+    assert np.all(err[ok] <= 0.02 * prob[ok] * (1 + 1e-12))
+    recs, integ = groups[0]
+    plan, rate, tried = abi.mem_autotune(integ.events, integ.proc, integ.tf, 9,
+                                         abi.make_opts(target_rel_err=0.02, max_points=1 << 22))
+    assert tried >= 9 and rate > 0
+    assert plan.n_adapt_iters in (2, 3, 4, 5) and plan.adapt_points in (2048, 4096, 8192)
+    assert plan.tiles_per_cta in (2, 4, 8) and plan.min_points in (1 << 13, 1 << 14, 1 << 15)
+    p2, e2 = np.zeros(16), np.zeros(16)
+    u2, s2 = np.zeros(16, dtype=np.uint64), np.zeros(16, dtype=np.int32)
+    abi.mem_integrate_batch([(integ.events, integ.proc, integ.tf)], 11,
+                            abi.make_opts(target_rel_err=0.02, max_points=1 << 22, plans=[plan]),
+                            p2, e2, u2, s2)
+    assert np.mean(s2 == 0) >= 0.9
+    for _, g in groups:
+        g.close()
