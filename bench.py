@@ -452,14 +452,19 @@ def flow_ab_leg(abi, torch, sp, n_train=4096, n_eval=4096, batch=304, steps=2000
 
     def summary(ms, res, cfg):
         p, e, u, s = res[:4]
+        conv = float((s == 0).double().mean().item())
         return {"setting": cfg, "events_per_s": n_eval / (ms * 1e-3), "ms": ms,
+                "converged_events_per_s": conv * n_eval / (ms * 1e-3),
                 "mean_points_per_event": float(u.double().mean().item()),
                 "median_points_per_event": float(u.double().median().item()),
-                "converged_fraction": float((s == 0).double().mean().item())}
+                "converged_fraction": conv}
+
+    def conv_rate(r):
+        return float((r[1][3] == 0).double().mean().item()) / r[0]
 
     target = dict(target_rel_err=0.01, max_points=1 << 24)
     v_set = ((3, 4096, 1 << 14), (5, 8192, 1 << 14), (2, 8192, 1 << 14), (3, 2048, 1 << 13))
-    f_set = ((1, 2048, 1 << 14), (2, 4096, 1 << 14), (1, 2048, 1 << 13), (1, 4096, 1 << 13))
+    f_set = ((1, 2048, 1 << 14), (2, 4096, 1 << 14), (1, 1024, 12288), (2, 2048, 12288))
     if arm == "vegas":
         v_set, f_set = v_set[:1], ()
     elif arm == "flow":
@@ -481,8 +486,9 @@ def flow_ab_leg(abi, torch, sp, n_train=4096, n_eval=4096, batch=304, steps=2000
             abi.mem_destroy(h)
         r = (v_runs or f_runs)[0]
         return {"arm": arm, "run": summary(*r), "flow_point_cost_vs_vegas": cost}
-    bv = min(v_runs, key=lambda r: r[0])
-    bf = min(f_runs, key=lambda r: r[0])
+    # each arm's best setting by converged events per second
+    bv = max(v_runs, key=conv_rate)
+    bf = max(f_runs, key=conv_rate)
     ok = (bv[1][3] == 0) & (bf[1][3] == 0)
     pull = ((bf[1][0] - bv[1][0]) / torch.sqrt(bf[1][1] ** 2 + bv[1][1] ** 2))[ok]
     smp = bf[1][4]
@@ -501,6 +507,8 @@ def flow_ab_leg(abi, torch, sp, n_train=4096, n_eval=4096, batch=304, steps=2000
                                   "n": int(pull.numel())}}
     out["points_ratio_flow_over_vegas"] = out["flow"]["mean_points_per_event"] / out["vegas"]["mean_points_per_event"]
     out["time_ratio_flow_over_vegas"] = out["flow"]["ms"] / out["vegas"]["ms"]
+    out["converged_rate_ratio_flow_over_vegas"] = (out["flow"]["converged_events_per_s"] /
+                                                   out["vegas"]["converged_events_per_s"])
     for h in (f, ev_tr, ev_ev, proc):
         abi.mem_destroy(h)
     return out

@@ -34,21 +34,19 @@ __global__ void k_flow_bf16(const FlowW* __restrict__ W, FlowB* __restrict__ B) 
     const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
     B->W1t[k][o][i] = q <= 1 ? hi : (q == 2 ? lo : __float2bfloat16_rn(0.f));
   }
-  // the same layers in the tcgen05 operand layout
-  for (int t = threadIdx.x; t < FH * 16; t += blockDim.x) {
-    const int n = t / 16, i = t % 16, q = i >> 2;
-    const float v = i < 12 ? W->W1a[k][i & 3][n] : 0.f;
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-    B->W1u[k][umma_kmajor(n, i, 16)] = q <= 1 ? hi : (q == 2 ? lo : __float2bfloat16_rn(0.f));
-  }
-  for (int t = threadIdx.x; t < FH * FH; t += blockDim.x) {
-    const int n = t / FH, i = t % FH;
-    B->W2u[k][umma_kmajor(n, i, FH)] = __float2bfloat16_rn(W->W2[k][i][n]);
-  }
-  for (int t = threadIdx.x; t < 16 * FH; t += blockDim.x) {
-    const int n = t / FH, i = t % FH;
-    B->W3u[k][umma_kmajor(n, i, FH)] = __float2bfloat16_rn(n < 8 ? W->W3[k][i][n] : 0.f);
+  // the hidden layer as the tcgen05 operand, bias folded into k 128 (high) and 129 (low)
+  for (int t = threadIdx.x; t < FH * FKH; t += blockDim.x) {
+    const int n = t / FKH, i = t % FKH;
+    __nv_bfloat16 v;
+    if (i < FH) {
+      v = __float2bfloat16_rn(W->W2[k][i][n]);
+    } else {
+      const float b = W->b2[k][n];
+      const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+      v = i == FH ? hi : (i == FH + 1 ? __float2bfloat16_rn(b - __bfloat162float(hi))
+                                      : __float2bfloat16_rn(0.f));
+    }
+    B->W2u[k][umma_kmajor(n, i, FKH)] = v;
   }
 }
 

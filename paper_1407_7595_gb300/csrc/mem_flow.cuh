@@ -27,6 +27,7 @@ constexpr int FC = 16;           // conditioning features
 constexpr int FD = 7;            // dimensions (ttbar)
 constexpr int FLD = FH + 8;      // padded BF16 row stride (conflict-free fragment loads)
 constexpr int FW1 = 24;          // padded row of the first-layer BF16 operand (16 used)
+constexpr int FKH = FH + 16;     // K of the tcgen05 hidden product: 128 inputs, 1, 1, 14 zeros
 constexpr float F_SMAX = 2.f;
 
 __host__ __device__ constexpr int flow_na(int k) { return k % 2 == 0 ? (FD + 1) / 2 : FD / 2; }
@@ -49,16 +50,15 @@ struct FlowW {
 // K = 16 operand for z_A split into two BF16 parts (z = z_hi + z_lo):
 // k 0-3 = W1a_hi (times z_hi), 4-7 = W1a_hi (times z_lo), 8-11 = W1a_lo
 // (times z_hi), 12-15 = 0, so the product keeps ~16 significant bits.
-// W1u, W2u, W3u are the same three layers as tcgen05 B operands (N x K,
-// K-major, no swizzle; see umma_kmajor): first layer N 128 x K 16 (the split
-// form above), hidden N 128 x K 128, output N 16 x K 128 (rows 8-15 zero).
+// W2u is the hidden layer as a tcgen05 B operand (N 128 x K 144, K-major, no
+// swizzle; see umma_kmajor) with its bias folded in: k 0-127 = W2[k][n],
+// k 128 = b2 high part, k 129 = b2 low part (BF16 split, ~16 bits), k 130-143
+// = 0; the activation operand carries 1, 1, 0 ... in those columns.
 struct FlowB {
   __nv_bfloat16 W2t[FK][FH][FLD];
   __nv_bfloat16 W3t[FK][8][FLD];
   __nv_bfloat16 W1t[FK][FH][FW1];
-  __nv_bfloat16 W1u[FK][FH * 16];
-  __nv_bfloat16 W2u[FK][FH * FH];
-  __nv_bfloat16 W3u[FK][16 * FH];
+  __nv_bfloat16 W2u[FK][FH * FKH];
 };
 
 // Element index of (row m, column k) of a K-column tile in the tcgen05
@@ -75,6 +75,13 @@ __host__ __device__ constexpr int flow_layer_params(int k) {
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// Two floats -> ReLU -> BF16 pair (lo in the low half), one conversion.
+__device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;\n" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
 }
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,

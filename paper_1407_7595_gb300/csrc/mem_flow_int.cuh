@@ -21,9 +21,9 @@
 
 namespace mem {
 
-constexpr int FCH = 1024;        // points per pass of a sampling CTA (z state in shared memory)
+constexpr int FCH = 768;         // points per pass of a sampling CTA (z state in shared memory)
 constexpr int FROWS = 128;       // rows per tensor-core tile (M of the MMA)
-constexpr uint32_t F_TMEM_COLS = 256;  // hidden accumulator 0..127, output 128..143
+constexpr uint32_t F_TMEM_COLS = 128;  // hidden-layer accumulator (128 x 128 FP32)
 constexpr uint32_t F_WAIT_LIMIT = 1u << 20;  // polls of one MMA-completion wait
 constexpr int FTS = 128;         // training samples per item
 
@@ -134,15 +134,14 @@ __global__ void k_flow_normalise(int64_t n_items, int nperm, int per_event,
 }
 
 // Shared memory of a sampling CTA (about 112 KB: two CTAs per SM; tensor
-// memory 256 columns each, the SM's 512 between them).
+// memory 128 columns each).
 template <class PH>
 struct __align__(1024) FlowSampSmem {
-  __nv_bfloat16 W2u[FH * FH];     // hidden layer, B operand
-  __nv_bfloat16 Act[FROWS * FH];  // A operand: first-layer input (K 16) or activations (K 128)
-  __nv_bfloat16 W1u[FH * 16];     // first layer, B operand
-  __nv_bfloat16 W3u[16 * FH];     // output layer, B operand
+  __nv_bfloat16 W2u[FH * FKH];    // hidden layer with its bias, tcgen05 B operand
+  __nv_bfloat16 Act[FROWS * FKH]; // hidden-layer input (+ constant columns), then output-layer input
+  __nv_bfloat16 W1t[FH][FW1];     // first layer, mma.sync B fragments (split form)
+  __nv_bfloat16 W3t[8][FLD];      // output layer, mma.sync B fragments
   float cb1[FH];                  // c W1c + b1 for the CTA's item
-  float b2[FH];
   float b3[16];
   float zs[FCH * 8];              // per point: z[0..6], running log-Jacobian
   typename PH::Cache cache;
@@ -178,6 +177,13 @@ __device__ inline uint32_t flow_tc_begin(FlowSampSmem<PH>& S) {
     tmem_alloc(smem_u32(&S.tmem), F_TMEM_COLS);
     tmem_relinquish();
   }
+  // columns 128-143 of the activation operand are constant: 1, 1, 0, ..., 0
+  // (they multiply the two parts of the hidden bias)
+  for (int r = threadIdx.x; r < FROWS; r += blockDim.x) {
+    const uint32_t one = pack_bf16(1.f, 1.f);
+    *reinterpret_cast<uint4*>(&S.Act[umma_kmajor(r, FH, FKH)]) = make_uint4(one, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(&S.Act[umma_kmajor(r, FH + 8, FKH)]) = make_uint4(0u, 0u, 0u, 0u);
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -201,28 +207,27 @@ __device__ inline void flow_tc_load_layer(FlowSampSmem<PH>& S, const FlowW* __re
                                           const FlowB* __restrict__ Bw, int k) {
   const uint4* s2 = reinterpret_cast<const uint4*>(&Bw->W2u[k][0]);
   uint4* d2 = reinterpret_cast<uint4*>(S.W2u);
-  for (int t = threadIdx.x; t < FH * FH / 8; t += blockDim.x) d2[t] = s2[t];
-  const uint4* s1 = reinterpret_cast<const uint4*>(&Bw->W1u[k][0]);
-  uint4* d1 = reinterpret_cast<uint4*>(S.W1u);
-  for (int t = threadIdx.x; t < FH * 16 / 8; t += blockDim.x) d1[t] = s1[t];
-  const uint4* s3 = reinterpret_cast<const uint4*>(&Bw->W3u[k][0]);
-  uint4* d3 = reinterpret_cast<uint4*>(S.W3u);
-  for (int t = threadIdx.x; t < 16 * FH / 8; t += blockDim.x) d3[t] = s3[t];
+  for (int t = threadIdx.x; t < FH * FKH / 8; t += blockDim.x) d2[t] = s2[t];
+  const uint4* s1 = reinterpret_cast<const uint4*>(&Bw->W1t[k][0][0]);
+  uint4* d1 = reinterpret_cast<uint4*>(&S.W1t[0][0]);
+  for (int t = threadIdx.x; t < (int)(sizeof(S.W1t) / 16); t += blockDim.x) d1[t] = s1[t];
+  const uint4* s3 = reinterpret_cast<const uint4*>(&Bw->W3t[k][0][0]);
+  uint4* d3 = reinterpret_cast<uint4*>(&S.W3t[0][0]);
+  for (int t = threadIdx.x; t < (int)(sizeof(S.W3t) / 16); t += blockDim.x) d3[t] = s3[t];
   for (int n = threadIdx.x; n < FH; n += blockDim.x) {
     float v = W->b1[k][n];
 #pragma unroll
     for (int q = 0; q < FC; ++q) v = fmaf(S.c[q], W->W1c[k][q][n], v);
     S.cb1[n] = v;
-    S.b2[n] = W->b2[k][n];
   }
   if (threadIdx.x < 16) S.b3[threadIdx.x] = threadIdx.x < 8 ? W->b3[k][threadIdx.x] : 0.f;
 }
 
-// Accumulator columns col0 .. col0 + 63 of this warp's 32 rows -> bias, ReLU,
-// BF16 -> activation operand (K 128).
+// Accumulator columns col0 .. col0 + 63 of this warp's 32 rows (the bias is
+// already in the product) -> ReLU + BF16 in one conversion -> the output
+// layer's operand in Act.
 template <class PH>
-__device__ inline void flow_tc_hidden_epilogue(FlowSampSmem<PH>& S, uint32_t tmem,
-                                               const float* bias) {
+__device__ inline void flow_tc_hidden_epilogue(FlowSampSmem<PH>& S, uint32_t tmem) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = warp & 3, row = 32 * q + lane;
   const int cbase = 64 * (warp >> 2);
@@ -233,19 +238,103 @@ __device__ inline void flow_tc_hidden_epilogue(FlowSampSmem<PH>& S, uint32_t tme
     const int col0 = cbase + 8 * cc;
     uint32_t pk[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-      pk[i] = pack_bf16(fmaxf(v[8 * cc + 2 * i] + bias[col0 + 2 * i], 0.f),
-                        fmaxf(v[8 * cc + 2 * i + 1] + bias[col0 + 2 * i + 1], 0.f));
-    *reinterpret_cast<uint4*>(&S.Act[umma_kmajor(row, col0, FH)]) =
+    for (int i = 0; i < 4; ++i) pk[i] = pack_bf16_relu(v[8 * cc + 2 * i], v[8 * cc + 2 * i + 1]);
+    *reinterpret_cast<uint4*>(&S.Act[umma_kmajor(row, col0, FKH)]) =
         make_uint4(pk[0], pk[1], pk[2], pk[3]);
+  }
+}
+
+// One warp, first layer of coupling layer k for the 16 tile rows rl .. rl + 15
+// (z rows at zr, stride 8): h1 = ReLU(z_A W1a + c W1c + b1) as mma.sync products
+// of the two-part BF16 split of z_A, written as BF16 into the UMMA operand Act.
+template <class PH>
+__device__ inline void flow_first_layer(FlowSampSmem<PH>& S, int k, int rl, const float* zr) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int na = flow_na(k), j0 = (2 * t) & 3;
+  float zv[2][2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int j = j0 + q;
+      zv[h][q] = j < na ? zr[(g + 8 * h) * 8 + flow_a(k, j)] : 0.f;
+    }
+  uint32_t a1[4];
+  if (t < 2) {
+    a1[0] = pack_bf16(zv[0][0], zv[0][1]);
+    a1[1] = pack_bf16(zv[1][0], zv[1][1]);
+    a1[2] = a1[0];
+    a1[3] = a1[1];
+  } else {
+    a1[0] = pack_bf16(zv[0][0] - bf16_hi(zv[0][0]), zv[0][1] - bf16_hi(zv[0][1]));
+    a1[1] = pack_bf16(zv[1][0] - bf16_hi(zv[1][0]), zv[1][1] - bf16_hi(zv[1][1]));
+    a1[2] = 0u;
+    a1[3] = 0u;
+  }
+#pragma unroll
+  for (int j = 0; j < FH / 8; ++j) {
+    const int n0 = 8 * j;
+    const float c0 = S.cb1[n0 + 2 * t], c1 = S.cb1[n0 + 2 * t + 1];
+    float acc[4] = {c0, c1, c0, c1};
+    const __nv_bfloat16* brow = &S.W1t[n0 + g][0];
+    mma_bf16(acc, a1, *reinterpret_cast<const uint32_t*>(brow + 2 * t),
+             *reinterpret_cast<const uint32_t*>(brow + 2 * t + 8));
+    *reinterpret_cast<uint32_t*>(&S.Act[umma_kmajor(rl + g, n0 + 2 * t, FKH)]) =
+        pack_bf16_relu(acc[0], acc[1]);
+    *reinterpret_cast<uint32_t*>(&S.Act[umma_kmajor(rl + g + 8, n0 + 2 * t, FKH)]) =
+        pack_bf16_relu(acc[2], acc[3]);
+  }
+}
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], uint32_t saddr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(saddr));
+}
+
+// One warp, output layer of coupling layer k for tile rows rl .. rl + 15: the
+// hidden activations come from Act (each 8 x 8 core matrix of the UMMA layout
+// is one ldmatrix tile), (s_raw | t) = h2 W3 + b3 by mma.sync, then the affine
+// update of the z rows at zr and their log-Jacobian.
+template <class PH>
+__device__ inline void flow_output_layer(FlowSampSmem<PH>& S, int k, int rl, float* zr) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const uint32_t base = smem_u32(S.Act);
+  const int lrow = rl + (lane & 7) + ((lane >> 3) & 1) * 8, lcol = (lane >> 4) * 8;
+  float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int kk = 0; kk < FH / 16; ++kk) {
+    uint32_t a[4];
+    ldmatrix_x4(a, base + 2u * (uint32_t)umma_kmajor(lrow, 16 * kk + lcol, FKH));
+    const __nv_bfloat16* brow = &S.W3t[g][0];
+    mma_bf16(o, a, *reinterpret_cast<const uint32_t*>(brow + 16 * kk + 2 * t),
+             *reinterpret_cast<const uint32_t*>(brow + 16 * kk + 2 * t + 8));
+  }
+  const float bo0 = S.b3[2 * t], bo1 = S.b3[2 * t + 1];
+  const float v0 = o[0] + bo0, v1 = o[1] + bo1, v2 = o[2] + bo0, v3 = o[3] + bo1;
+  float v[8];
+#pragma unroll
+  for (int src = 0; src < 4; ++src) {
+    const int sl = (lane & ~3) | src;
+    const float x0 = __shfl_sync(0xffffffffu, v0, sl), x1 = __shfl_sync(0xffffffffu, v1, sl);
+    const float x2 = __shfl_sync(0xffffffffu, v2, sl), x3 = __shfl_sync(0xffffffffu, v3, sl);
+    v[2 * src] = t == 1 ? x2 : x0;
+    v[2 * src + 1] = t == 1 ? x3 : x1;
+  }
+  if (t < 2) {
+    float* row = zr + (g + 8 * t) * 8;
+    if (k & 1) flow_update_row<FD / 2 + 1>(row, v, k);
+    else flow_update_row<FD / 2>(row, v, k);
   }
 }
 
 // One pass of a CTA over points q0 .. q0 + nrow of an item (nrow a multiple of
 // FROWS, at most FCH; rows at or past p1 are computed but not used): base draw,
-// the coupling layers on the tensor cores, then out(r, y, yc, log|dy/du|) per
-// used row, threads striding over rows. False if an MMA-completion wait gave up
-// (the CTA then stops issuing work).
+// the coupling layers, then out(r, y, yc, log|dy/du|) per used row, threads
+// striding over rows. Per 128-row tile and layer, the 128 x 128 hidden product
+// runs on tcgen05 (one MMA round trip); the first (K 16) and output (N 8)
+// products run per warp on mma.sync around it. False if an MMA-completion wait
+// gave up (the CTA then stops issuing work).
 template <class PH, class Out>
 __device__ inline bool flow_pass(FlowSampSmem<PH>& S, uint32_t tmem, uint32_t& phase,
                                  const FlowW* __restrict__ W, const FlowB* __restrict__ Bw,
@@ -253,7 +342,7 @@ __device__ inline bool flow_pass(FlowSampSmem<PH>& S, uint32_t tmem, uint32_t& p
                                  uint32_t q0, uint32_t nrow, uint32_t p1, Out& out) {
   constexpr int D = PH::D;
   static_assert(D == FD, "the flow is built for the 7-dimensional ttbar integral");
-  constexpr uint32_t ID_H = umma_idesc_bf16(FROWS, FH), ID_O = umma_idesc_bf16(FROWS, 16);
+  constexpr uint32_t ID_H = umma_idesc_bf16(FROWS, FH);
   for (uint32_t r = threadIdx.x; r < nrow; r += THREADS) {
     const uint32_t p = q0 + r;
     float u[D];
@@ -272,94 +361,38 @@ __device__ inline bool flow_pass(FlowSampSmem<PH>& S, uint32_t tmem, uint32_t& p
     }
     S.zs[r * 8 + 7] = lj;
   }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t a_addr = smem_u32(S.Act), w1 = smem_u32(S.W1u), w2 = smem_u32(S.W2u),
-                 w3 = smem_u32(S.W3u), mbar = smem_u32(&S.mbar);
+  const int warp = threadIdx.x >> 5;
+  const uint32_t a_addr = smem_u32(S.Act), w2 = smem_u32(S.W2u), mbar = smem_u32(&S.mbar);
   for (int k = 0; k < FK; ++k) {
-    const int na = flow_na(k);
     // the previous layer's products are complete and its z updates visible
     tc_fence_before();
     __syncthreads();
     if (S.abort) return false;
     flow_tc_load_layer(S, W, Bw, k);
     for (uint32_t t0 = 0; t0 < nrow; t0 += FROWS) {
-      // first-layer operand (K 16): [z_A hi | z_A lo] and [z_A hi | 0] per row
-      {
-        const int r = threadIdx.x >> 1, half = threadIdx.x & 1;
-        const float* zr = &S.zs[(t0 + r) * 8];
-        float zv[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) zv[j] = j < na ? zr[flow_a(k, j)] : 0.f;
-        uint4 v;
-        v.x = pack_bf16(zv[0], zv[1]);
-        v.y = pack_bf16(zv[2], zv[3]);
-        if (half == 0) {
-          v.z = pack_bf16(zv[0] - bf16_hi(zv[0]), zv[1] - bf16_hi(zv[1]));
-          v.w = pack_bf16(zv[2] - bf16_hi(zv[2]), zv[3] - bf16_hi(zv[3]));
-        } else {
-          v.z = 0u;
-          v.w = 0u;
-        }
-        *reinterpret_cast<uint4*>(&S.Act[umma_kmajor(r, 8 * half, 16)]) = v;
-      }
+      // first layer: warp w produces rows 16 w .. 16 w + 15 of the hidden input
+      __syncthreads();   // Act is free: the previous tile's output layer has read it
+      flow_first_layer(S, k, 16 * warp, &S.zs[(t0 + 16 * warp) * 8]);
       fence_async_smem();
       tc_fence_before();
       __syncthreads();
       if (threadIdx.x == 0) {
         tc_fence_after();
-        umma_bf16(tmem, umma_desc(a_addr, 128, 256), umma_desc(w1, 128, 256), ID_H, 0u);
+#pragma unroll
+        for (uint32_t s = 0; s < FKH / 16; ++s)
+          umma_bf16(tmem, umma_desc(a_addr + 256 * s, 128, 16 * FKH),
+                    umma_desc(w2 + 256 * s, 128, 16 * FKH), ID_H, s > 0 ? 1u : 0u);
         umma_commit(mbar);
         if (!mbar_wait(mbar, phase, F_WAIT_LIMIT)) S.abort = 1;
       }
       phase ^= 1u;
-      __syncthreads();   // the issuing thread saw the products complete
+      __syncthreads();   // the issuing thread saw the product complete
       tc_fence_after();
-      flow_tc_hidden_epilogue(S, tmem, S.cb1);
-      fence_async_smem();
-      tc_fence_before();
-      __syncthreads();
       if (S.abort) return false;
-      if (threadIdx.x == 0) {
-        tc_fence_after();
-#pragma unroll
-        for (uint32_t s = 0; s < FH / 16; ++s)
-          umma_bf16(tmem, umma_desc(a_addr + 256 * s, 128, 2048), umma_desc(w2 + 256 * s, 128, 2048),
-                    ID_H, s > 0 ? 1u : 0u);
-        umma_commit(mbar);
-        if (!mbar_wait(mbar, phase, F_WAIT_LIMIT)) S.abort = 1;
-      }
-      phase ^= 1u;
-      __syncthreads();
-      tc_fence_after();
-      flow_tc_hidden_epilogue(S, tmem, S.b2);
-      fence_async_smem();
+      flow_tc_hidden_epilogue(S, tmem);   // h2 -> Act (the product has read Act)
       tc_fence_before();
       __syncthreads();
-      if (S.abort) return false;
-      if (threadIdx.x == 0) {
-        tc_fence_after();
-#pragma unroll
-        for (uint32_t s = 0; s < FH / 16; ++s)
-          umma_bf16(tmem + 128, umma_desc(a_addr + 256 * s, 128, 2048),
-                    umma_desc(w3 + 256 * s, 128, 2048), ID_O, s > 0 ? 1u : 0u);
-        umma_commit(mbar);
-        if (!mbar_wait(mbar, phase, F_WAIT_LIMIT)) S.abort = 1;
-      }
-      phase ^= 1u;
-      __syncthreads();
-      tc_fence_after();
-      if (warp < 4) {
-        float v[8];
-        tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + 128u, v);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] += S.b3[i];
-        float* zr = &S.zs[(t0 + 32 * warp + lane) * 8];
-        if (k & 1) flow_update_row<FD / 2 + 1>(zr, v, k);
-        else flow_update_row<FD / 2>(zr, v, k);
-      }
-      // no barrier here: the next tile's operand build touches other rows of zs
-      // and the first 4 KB of Act (read by products that have completed), and
-      // its barrier orders this tile's tensor-memory loads before the next MMA
+      flow_output_layer(S, k, 16 * warp, &S.zs[(t0 + 16 * warp) * 8]);
     }
   }
   __syncthreads();

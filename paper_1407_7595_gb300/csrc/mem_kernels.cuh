@@ -142,7 +142,8 @@ struct AdaptSmem {
 // points, each filling the per-bin histograms of w^2 and refining every
 // dimension (one warp per dimension, FP64). With MOM, the moments of the last
 // iteration (sum w, sum w^2, compensated) are written to *mom: the variance of
-// the sampler the adapted grid replaces, for comparing samplers. With hist0,
+// the sampler the adapted grid replaces, for comparing samplers (the per-item
+// constants are then read from `caches`, filled by the caller). With hist0,
 // the starting grid is first refined once with the item's histogram
 // hist0[item] (D x NG sums of w^2 over bins of the starting grid, gathered by
 // another sampler).
@@ -157,7 +158,14 @@ __device__ void adapt_item(AdaptSmem<PH>& S, const float* __restrict__ recs, con
   const int64_t ev = item / PH::NPERM;
   const int perm = (int)(item % PH::NPERM);
   const float* rec = recs + ev * REC;
-  if (threadIdx.x == 0) {
+  if (MOM) {
+    // the judge of another sampler: the per-item constants are already in HBM
+    static_assert(sizeof(typename PH::Cache) % 4 == 0, "cache must be word sized");
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(caches + item);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&S.cache);
+    for (int t = threadIdx.x; t < (int)(sizeof(typename PH::Cache) / 4); t += blockDim.x)
+      dst[t] = src[t];
+  } else if (threadIdx.x == 0) {
     // per-item constants, computed once in FP64 and kept for the sampling kernel
     PH::setup(rec, perm, P, T, S.cache);
     caches[item] = S.cache;
