@@ -378,7 +378,8 @@ def flow_ab_leg(abi, torch, sp, n_train=4096, n_eval=4096, batch=304, steps=2000
     permutations). The flow is trained on VEGAS-weighted samples of n_train
     events (128 per item: 4096 x 24 x 128 = 1.26e7 samples), then n_eval fresh
     events are integrated to 1 % relative error (cap 2^24 points per event) by
-    each arm; each arm's best setting (by time) from a small sweep is reported.
+    each arm; each arm's best setting (by converged events per second) from a
+    small sweep is reported.
     Flow arm: flow pilot -> VEGAS judge seeded by the pilot -> cheaper sampler per
     item, with the judge's cost ratio measured here (flow point vs VEGAS point)."""
     K = synth.PROC_TTBAR
