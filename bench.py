@@ -332,7 +332,7 @@ def run_ours(args):
                "gpu_launches": 3 * args.steps}
         if not args.no_adaptive:
             out["to_1pct"] = adaptive_leg(abi, torch, events, proc, tf, n_ev,
-                                          shard(rank, n_ev)["event_id_base"], sp)
+                                          shard(rank, n_ev)["event_id_base"], sp, recs=recs)
         if not args.no_flow:
             out["flow_ab"] = flow_ab_leg(abi, torch, sp, args.flow_train, args.flow_eval,
                                          steps=args.flow_steps)
@@ -345,31 +345,47 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def adaptive_leg(abi, torch, events, proc, tf, n_ev, eid_base, sp, target=0.01, reps=3):
+def adaptive_leg(abi, torch, events, proc, tf, n_ev, eid_base, sp, recs=None, target=0.01,
+                 reps=3):
     """The same events integrated with the per-event stop rule (err/prob <= 1 %,
-    cap 2^24 points per event): events brought to 1 % per second."""
+    cap 2^24 points per event): events brought to 1 % per second, with the
+    schedule the autotuner picks on the first 256 events (and, for reference,
+    with the library's default schedule)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     prob = torch.zeros(n_ev, dtype=torch.float64, device=dev)
     err = torch.zeros_like(prob)
     used = torch.zeros(n_ev, dtype=torch.int64, device=dev)
     st = torch.zeros(n_ev, dtype=torch.int32, device=dev)
-    opts = abi.make_opts(target_rel_err=target, max_points=1 << 24, event_id_base=eid_base)
-    abi.mem_integrate(events, proc, tf, 0, 4242, opts, prob, err, used, st, sp)  # warm-up
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ms = []
-    for i in range(reps):
-        t0.record()
-        abi.mem_integrate(events, proc, tf, 0, 4300 + i, opts, prob, err, used, st, sp)
-        t1.record()
-        t1.synchronize()
-        ms.append(t0.elapsed_time(t1))
-    m = statistics.mean(ms) * 1e-3
+    base = dict(target_rel_err=target, max_points=1 << 24, event_id_base=eid_base)
+
+    def run(opts):
+        abi.mem_integrate(events, proc, tf, 0, 4242, opts, prob, err, used, st, sp)  # warm-up
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for i in range(reps):
+            t0.record()
+            abi.mem_integrate(events, proc, tf, 0, 4300 + i, opts, prob, err, used, st, sp)
+            t1.record()
+            t1.synchronize()
+            ms.append(t0.elapsed_time(t1))
+        return statistics.mean(ms) * 1e-3
+
+    m_default = run(abi.make_opts(**base))
+    plan, tuned = None, None
+    if recs is not None:
+        t = time.perf_counter()
+        cal = abi.mem_upload_events(proc, np.ascontiguousarray(recs[:256]), sp)
+        plan, rate, tried = abi.mem_autotune(cal, proc, tf, 77, abi.make_opts(**base), sp)
+        abi.mem_destroy(cal)
+        tuned = {"plan": plan.as_dict(), "plans_timed": tried, "seconds": time.perf_counter() - t}
+    m = run(abi.make_opts(plans=[plan], **base)) if plan is not None else m_default
     conv = float((st == 0).float().mean().item())
     return {"metric": "events integrated to 1% relative error per second",
             "value": n_ev / m, "unit": "events/s", "ms_per_step": m * 1e3,
             "converged_fraction": conv,
             "mean_points_per_event": float(used.double().mean().item()),
-            "evals_per_s": float(used.double().sum().item()) / m}
+            "evals_per_s": float(used.double().sum().item()) / m,
+            "autotune": tuned, "default_schedule_events_per_s": n_ev / m_default}
 
 
 def flow_ab_leg(abi, torch, sp, n_train=4096, n_eval=4096, batch=304, steps=20000, reps=2,

@@ -124,13 +124,12 @@ cudaError_t launch_final(const Slot* slots, int64_t n_events, int nperm, uint32_
   return cudaGetLastError();
 }
 
-__global__ void k_philox(uint64_t seed, uint32_t eid, uint32_t perm, uint32_t point0, int64_t n,
-                         int d, float* __restrict__ out) {
+__global__ void k_philox(const __grid_constant__ PhiloxKey key, uint32_t eid, uint32_t perm,
+                         uint32_t point0, int64_t n, int d, float* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   for (int b = 0; 4 * b < d; ++b) {
-    const u32x4 o = philox4x32_10(point0 + (uint32_t)i, (uint32_t)b << 8, eid, perm, k0, k1);
+    const u32x4 o = philox4x32_10(point0 + (uint32_t)i, (uint32_t)b << 8, eid, perm, key);
     const uint32_t w[4] = {o.a, o.b, o.c, o.d};
     for (int j = 0; j < 4 && 4 * b + j < d; ++j) out[i * d + 4 * b + j] = u01(w[j]);
   }
@@ -519,7 +518,7 @@ mem_status mem_philox_uniforms(uint64_t seed, uint64_t event_id, int32_t perm, u
   const bool dev_out = is_device_ptr(out);
   float* buf = out;
   if (!dev_out) MEM_CK(cudaMallocAsync((void**)&buf, (size_t)n * d * sizeof(float), st));
-  k_philox<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(seed, (uint32_t)event_id, (uint32_t)perm,
+  k_philox<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(philox_key(seed), (uint32_t)event_id, (uint32_t)perm,
                                                         (uint32_t)point0, n, d, buf);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && !dev_out) {

@@ -44,7 +44,7 @@ __device__ __forceinline__ void neu2(double& s, double& c, double x) {
 
 template <class PH, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB)
-k_round_sample(const float* __restrict__ recs, ProcConst P, uint64_t seed,
+k_round_sample(const float* __restrict__ recs, ProcConst P, const __grid_constant__ PhiloxKey key,
                uint64_t event_id_base, const int32_t* __restrict__ active,
                const RoundCtl* __restrict__ ctl, uint32_t idx_base, uint32_t pts_item,
                const GridBin* __restrict__ grid32, const typename PH::Cache* __restrict__ caches,
@@ -78,7 +78,7 @@ k_round_sample(const float* __restrict__ recs, ProcConst P, uint64_t seed,
       for (uint32_t p = p0 + threadIdx.x; p < p1; p += THREADS) {
         float u[D], x[D], xc[D];
         int bin[D];
-        point_uniforms<D>(seed, eid, (uint32_t)perm, idx_base + p, u);
+        point_uniforms<D>(key, eid, (uint32_t)perm, idx_base + p, u);
         const float J = vegas_map<D>(S.gb, u, x, xc, bin);
         const float w = PH::eval(S.cache, P, x, xc) * J;
         if (isfinite(w)) {
@@ -183,7 +183,7 @@ cudaError_t run_batch_rounds(const BatchArgs& b, cudaStream_t st) {
   uint32_t pts = b.pts0;
   for (int r = 0; r < b.n_rounds; ++r) {
     k_round_sample<PH, MINB><<<b.grid_ctas, THREADS, 0, st>>>(
-        b.base.recs, b.base.P, b.base.seed, b.base.event_id_base, b.active, b.ctl, idx, pts,
+        b.base.recs, b.base.P, philox_key(b.base.seed), b.base.event_id_base, b.active, b.ctl, idx, pts,
         b.base.grid32, reinterpret_cast<const typename PH::Cache*>(b.base.caches), b.slots);
     k_round_reduce<<<(unsigned)((b.base.n_items + 255) / 256), 256, 0, st>>>(b.active, b.ctl, pts,
                                                                             b.slots, b.acc);
@@ -207,7 +207,7 @@ cudaError_t run_batch(BatchArgs b, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const IntegrateArgs& a = b.base;
   k_adapt<PH, MINB><<<(unsigned)a.n_items, THREADS, smem, st>>>(
-      a.recs, a.P, a.T, a.n_items, a.seed, a.event_id_base, a.n_iters, a.n_adapt, a.alpha,
+      a.recs, a.P, a.T, a.n_items, philox_key(a.seed), a.event_id_base, a.n_iters, a.n_adapt, a.alpha,
       a.grid_in, a.grid32, reinterpret_cast<typename PH::Cache*>(a.caches));
   b.grid_ctas = round_sample_ctas<PH, MINB>();
   b.target_tiles = b.tiles_per_cta * b.grid_ctas;

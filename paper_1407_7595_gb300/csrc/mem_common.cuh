@@ -20,18 +20,35 @@ constexpr double PI_D = 3.14159265358979323846;
 // ---------------------------------------------------------------------------
 struct u32x4 { uint32_t a, b, c, d; };
 
+// The key schedule of all 10 rounds (key + r x the Weyl constants), built once
+// on the host and passed to the kernels as a __grid_constant__ parameter, so
+// that each round's key is a constant-bank operand of its XOR.
+struct PhiloxKey {
+  uint32_t k0[10], k1[10];
+};
+
+__host__ __device__ inline PhiloxKey philox_key(uint64_t seed) {
+  PhiloxKey k;
+  uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    k.k0[r] = a;
+    k.k1[r] = b;
+    a += 0x9E3779B9u;
+    b += 0xBB67AE85u;
+  }
+  return k;
+}
+
 __device__ __forceinline__ u32x4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
-                                               uint32_t c3, uint32_t k0, uint32_t k1) {
+                                               uint32_t c3, const PhiloxKey& key) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
     const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
-    c0 = hi1 ^ c1 ^ k0;
+    c0 = hi1 ^ c1 ^ key.k0[r];
     c1 = lo1;
-    c2 = hi0 ^ c3 ^ k1;
+    c2 = hi0 ^ c3 ^ key.k1[r];
     c3 = lo0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
   }
   return {c0, c1, c2, c3};
 }
@@ -47,13 +64,12 @@ __device__ __forceinline__ float u01(uint32_t x) {
 constexpr uint32_t TAG_VEGAS = 0, TAG_FLOW = 2;
 
 template <int D>
-__device__ __forceinline__ void point_uniforms(uint64_t seed, uint32_t event_id, uint32_t perm,
-                                               uint32_t idx, float (&u)[D],
+__device__ __forceinline__ void point_uniforms(const PhiloxKey& key, uint32_t event_id,
+                                               uint32_t perm, uint32_t idx, float (&u)[D],
                                                uint32_t tag = TAG_VEGAS) {
-  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
 #pragma unroll
   for (int b = 0; b < (D + 3) / 4; ++b) {
-    u32x4 o = philox4x32_10(idx, ((uint32_t)b << 8) | tag, event_id, perm, k0, k1);
+    u32x4 o = philox4x32_10(idx, ((uint32_t)b << 8) | tag, event_id, perm, key);
     if (4 * b + 0 < D) u[4 * b + 0] = u01(o.a);
     if (4 * b + 1 < D) u[4 * b + 1] = u01(o.b);
     if (4 * b + 2 < D) u[4 * b + 2] = u01(o.c);

@@ -377,24 +377,4 @@ __device__ inline void flow_layer_rows(const FlowInferLayer& L, int k, float* zs
   __syncwarp();
 }
 
-// Forward coupling layer k on 16 rows: z[B] <- z[B] e^s + t, log|J| (slot 7) += sum s.
-__device__ inline void flow_mlp_rows(const FlowLayerSmem& L, int k, const float* zs, int r0,
-                                     float (*st)[8]) {
-  flow_mlp_st(L, k, zs, r0, st);
-  const int lane = threadIdx.x & 31;
-  if (lane < 16) {
-    const int nb = flow_nb(k);
-    float* zr = const_cast<float*>(zs) + (r0 + lane) * 8;
-    float ls = 0.f;
-    for (int j = 0; j < nb; ++j) {
-      const float s = F_SMAX * tanhf(st[lane][j] * (1.f / F_SMAX));
-      const int idx = flow_b(k, j);
-      zr[idx] = fmaf(zr[idx], __expf(s), st[lane][nb + j]);
-      ls += s;
-    }
-    zr[7] += ls;  // running log-Jacobian kept in the padding slot
-  }
-  __syncwarp();
-}
-
 }  // namespace mem

@@ -158,10 +158,10 @@ mem_status mem_flow_samples(const mem_events* events, const mem_process* process
   e = set_smem(k_adapt<PhysTT, MINB_FLOW>, smem);
   if (e == cudaSuccess) {
     k_adapt<PhysTT, MINB_FLOW><<<(unsigned)n_items, THREADS, smem, st>>>(
-        events->d_recs, P, T, n_items, seed, eid0, iters, (uint32_t)n_adapt, alpha, nullptr,
+        events->d_recs, P, T, n_items, philox_key(seed), eid0, iters, (uint32_t)n_adapt, alpha, nullptr,
         grid32, caches);
     k_flow_samples<PhysTT><<<(unsigned)n_items, FTS, 0, st>>>(
-        events->d_recs, P, n_items, seed, eid0, (uint32_t)(iters * n_adapt), grid32, caches, ys,
+        events->d_recs, P, n_items, philox_key(seed), eid0, (uint32_t)(iters * n_adapt), grid32, caches, ys,
         ws, cs, tot, log_jv);
     k_flow_normalise<<<(unsigned)n_items, FTS, 0, st>>>(n_items, PhysTT::NPERM, per_event, tot, ws);
     e = cudaGetLastError();
@@ -191,7 +191,7 @@ mem_status mem_flow_eval_points(const mem_process* process, const mem_tf_desc* t
   if (e == cudaSuccess) {
     const unsigned blocks = (unsigned)((n + FCH - 1) / FCH);
     k_flow_points<PhysTT, MINB_FLOW><<<blocks, THREADS, smem, st>>>(
-        record, perm, process->pc, make_tf_const_from(tf), seed, event_id, point0, (uint32_t)n,
+        record, perm, process->pc, make_tf_const_from(tf), philox_key(seed), event_id, point0, (uint32_t)n,
         flow->W, flow->B, z, logj, w, d_err);
     e = cudaGetLastError();
   }
@@ -317,6 +317,7 @@ mem_status mem_integrate_flow(const mem_events* events, const mem_process* proce
   const ProcConst P = process->pc;
   const TFConst T = make_tf_const_from(tf);
   const uint64_t eid0 = opts->event_id_base;
+  const PhiloxKey key = philox_key(seed);
   const unsigned gi = (unsigned)((n_items + 255) / 256), ge = (unsigned)((n_ev + 127) / 128);
 
   // the whole schedule is captured into one CUDA graph on a private stream
@@ -340,11 +341,11 @@ mem_status mem_integrate_flow(const mem_events* events, const mem_process* proce
     if (guided) {
       cudaMemsetAsync(hist, 0, (size_t)n_items * PhysTT::D * NG * sizeof(float), cs);
       k_flow_round_sample<PhysTT, MINB_FLOW, true><<<ctas_f, THREADS, smem_f, cs>>>(
-          recs, P, seed, eid0, act_f, ctl_f, 0u, (uint32_t)pts0, flow->W, flow->B, caches, feats,
+          recs, P, key, eid0, act_f, ctl_f, 0u, (uint32_t)pts0, flow->W, flow->B, caches, feats,
           sl_f, hist, d_err);
     } else {
       k_flow_round_sample<PhysTT, MINB_FLOW, false><<<ctas_f, THREADS, smem_f, cs>>>(
-          recs, P, seed, eid0, act_f, ctl_f, 0u, (uint32_t)pts0, flow->W, flow->B, caches, feats,
+          recs, P, key, eid0, act_f, ctl_f, 0u, (uint32_t)pts0, flow->W, flow->B, caches, feats,
           sl_f, nullptr, d_err);
     }
     k_round_reduce<<<gi, 256, 0, cs>>>(act_f, ctl_f, (uint32_t)pts0, sl_f, acc);
@@ -352,7 +353,7 @@ mem_status mem_integrate_flow(const mem_events* events, const mem_process* proce
     k_flow_screen<<<ge, 128, 0, cs>>>(n_ev, NP, tau, acc, judge);
     k_round_compact<<<1, 1024, 0, cs>>>(n_items, judge, act_v, ctl_v, tt_v, nullptr, 0);
     k_adapt_list<PhysTT, MINB_FLOW><<<ctas_a, THREADS, smem_a, cs>>>(
-        recs, P, T, act_v, &ctl_v->n_active, seed, eid0, iters, (uint32_t)n_adapt, alpha, grid32,
+        recs, P, T, act_v, &ctl_v->n_active, key, eid0, iters, (uint32_t)n_adapt, alpha, grid32,
         caches, mom, hist);
     k_flow_judge<<<gi, 256, 0, cs>>>(n_items, (uint32_t)n_adapt, cost, judge, mom, acc, sampler);
     k_flow_route<<<gi, 256, 0, cs>>>(n_items, sampler, route);
@@ -364,10 +365,10 @@ mem_status mem_integrate_flow(const mem_events* events, const mem_process* proce
       k_round_compact<<<1, 1024, 0, cs>>>(n_items, flags, act_f, ctl_f, tt_f, route, 0);
       k_round_compact<<<1, 1024, 0, cs>>>(n_items, flags, act_v, ctl_v, tt_v, route, 1);
       k_flow_round_sample<PhysTT, MINB_FLOW, false><<<ctas_f, THREADS, smem_f, cs>>>(
-          recs, P, seed, eid0, act_f, ctl_f, (uint32_t)idx_f, (uint32_t)pts, flow->W, flow->B,
+          recs, P, key, eid0, act_f, ctl_f, (uint32_t)idx_f, (uint32_t)pts, flow->W, flow->B,
           caches, feats, sl_f, nullptr, d_err);
       k_round_sample<PhysTT, MINB_FLOW><<<ctas_v, THREADS, 0, cs>>>(
-          recs, P, seed, eid0, act_v, ctl_v, (uint32_t)(adapt + idx_f), (uint32_t)pts, grid32,
+          recs, P, key, eid0, act_v, ctl_v, (uint32_t)(adapt + idx_f), (uint32_t)pts, grid32,
           caches, sl_v);
       k_round_reduce<<<gi, 256, 0, cs>>>(act_f, ctl_f, (uint32_t)pts, sl_f, acc);
       k_round_reduce<<<gi, 256, 0, cs>>>(act_v, ctl_v, (uint32_t)pts, sl_v, acc);

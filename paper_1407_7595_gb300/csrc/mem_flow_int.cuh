@@ -75,7 +75,8 @@ __global__ void k_flow_setup(const float* __restrict__ recs, ProcConst P, TFCons
 // [2^-24, 1 - 2^-24] for the logit.
 template <class PH>
 __global__ void __launch_bounds__(FTS)
-k_flow_samples(const float* __restrict__ recs, ProcConst P, int64_t n_items, uint64_t seed,
+k_flow_samples(const float* __restrict__ recs, ProcConst P, int64_t n_items,
+               const __grid_constant__ PhiloxKey key,
                uint64_t event_id_base, uint32_t idx0, const GridBin* __restrict__ grid32,
                const typename PH::Cache* __restrict__ caches, float* __restrict__ ys,
                float* __restrict__ ws, float* __restrict__ cs, double* __restrict__ tot_out,
@@ -93,7 +94,7 @@ k_flow_samples(const float* __restrict__ recs, ProcConst P, int64_t n_items, uin
   __syncthreads();
   float u[D], x[D], xc[D];
   int bin[D];
-  point_uniforms<D>(seed, (uint32_t)(event_id_base + (uint64_t)ev), (uint32_t)perm,
+  point_uniforms<D>(key, (uint32_t)(event_id_base + (uint64_t)ev), (uint32_t)perm,
                     idx0 + threadIdx.x, u);
   const float J = vegas_map<D>(gb, u, x, xc, bin);
   float w = cache.ok ? PH::eval(cache, P, x, xc) * J : 0.f;
@@ -338,7 +339,7 @@ __device__ inline void flow_output_layer(FlowSampSmem<PH>& S, int k, int rl, flo
 template <class PH, class Out>
 __device__ inline bool flow_pass(FlowSampSmem<PH>& S, uint32_t tmem, uint32_t& phase,
                                  const FlowW* __restrict__ W, const FlowB* __restrict__ Bw,
-                                 uint64_t seed, uint32_t eid, int perm, uint32_t idx_base,
+                                 const PhiloxKey& key, uint32_t eid, int perm, uint32_t idx_base,
                                  uint32_t q0, uint32_t nrow, uint32_t p1, Out& out) {
   constexpr int D = PH::D;
   static_assert(D == FD, "the flow is built for the 7-dimensional ttbar integral");
@@ -347,7 +348,7 @@ __device__ inline bool flow_pass(FlowSampSmem<PH>& S, uint32_t tmem, uint32_t& p
     const uint32_t p = q0 + r;
     float u[D];
     if (p < p1) {
-      point_uniforms<D>(seed, eid, (uint32_t)perm, idx_base + p, u, TAG_FLOW);
+      point_uniforms<D>(key, eid, (uint32_t)perm, idx_base + p, u, TAG_FLOW);
     } else {
 #pragma unroll
       for (int j = 0; j < D; ++j) u[j] = 0.5f;
@@ -420,7 +421,8 @@ __device__ inline bool flow_pass(FlowSampSmem<PH>& S, uint32_t tmem, uint32_t& p
 // n_items x D x NG), the importance a VEGAS grid refinement starts from.
 template <class PH, int MINB, bool HIST>
 __global__ void __launch_bounds__(THREADS, MINB)
-k_flow_round_sample(const float* __restrict__ recs, ProcConst P, uint64_t seed,
+k_flow_round_sample(const float* __restrict__ recs, ProcConst P,
+                    const __grid_constant__ PhiloxKey key,
                     uint64_t event_id_base, const int32_t* __restrict__ active,
                     const RoundCtl* __restrict__ ctl, uint32_t idx_base, uint32_t pts_item,
                     const FlowW* __restrict__ W, const FlowB* __restrict__ Bw,
@@ -475,7 +477,7 @@ k_flow_round_sample(const float* __restrict__ recs, ProcConst P, uint64_t seed,
 #pragma unroll 1
       for (uint32_t q0 = p0; q0 < p1; q0 += FCH) {
         const uint32_t nrow = min((uint32_t)FCH, (p1 - q0 + FROWS - 1) / FROWS * FROWS);
-        if (!flow_pass<PH>(S, tmem, phase, W, Bw, seed, eid, perm, idx_base, q0, nrow, p1, acc)) {
+        if (!flow_pass<PH>(S, tmem, phase, W, Bw, key, eid, perm, idx_base, q0, nrow, p1, acc)) {
           alive = false;
           break;
         }
@@ -523,7 +525,8 @@ k_flow_round_sample(const float* __restrict__ recs, ProcConst P, uint64_t seed,
 // prefactor. CTA b handles points b FCH .. of the n requested.
 template <class PH, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB)
-k_flow_points(const float* __restrict__ rec, int perm, ProcConst P, TFConst T, uint64_t seed,
+k_flow_points(const float* __restrict__ rec, int perm, ProcConst P, TFConst T,
+              const __grid_constant__ PhiloxKey key,
               uint32_t event_id, uint32_t point0, uint32_t n, const FlowW* __restrict__ W,
               const FlowB* __restrict__ Bw, float* __restrict__ z_out, float* __restrict__ lj_out,
               double* __restrict__ w_out, int* __restrict__ err) {
@@ -544,7 +547,7 @@ k_flow_points(const float* __restrict__ rec, int perm, ProcConst P, TFConst T, u
     lj_out[i] = lj;
     w_out[i] = (double)w * P.prefactor;
   };
-  if (!flow_pass<PH>(S, tmem, phase, W, Bw, seed, event_id, perm, point0 + q0, 0, nrow, n - q0,
+  if (!flow_pass<PH>(S, tmem, phase, W, Bw, key, event_id, perm, point0 + q0, 0, nrow, n - q0,
                      put) &&
       threadIdx.x == 0)
     atomicExch(err, 1);

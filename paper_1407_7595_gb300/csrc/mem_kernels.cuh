@@ -149,7 +149,7 @@ struct AdaptSmem {
 // another sampler).
 template <class PH, bool MOM>
 __device__ void adapt_item(AdaptSmem<PH>& S, const float* __restrict__ recs, const ProcConst& P,
-                           const TFConst& T, int64_t item, uint64_t seed, uint64_t event_id_base,
+                           const TFConst& T, int64_t item, const PhiloxKey& key, uint64_t event_id_base,
                            int n_iters, uint32_t n_adapt, double alpha,
                            const double* __restrict__ grid_in, GridBin* __restrict__ grid32,
                            typename PH::Cache* __restrict__ caches, Slot* __restrict__ mom,
@@ -191,7 +191,7 @@ __device__ void adapt_item(AdaptSmem<PH>& S, const float* __restrict__ recs, con
       for (uint32_t k = threadIdx.x; k < n_adapt; k += blockDim.x) {
         float u[D], x[D], xc[D];
         int bin[D];
-        point_uniforms<D>(seed, eid, (uint32_t)perm, (uint32_t)it * n_adapt + k, u);
+        point_uniforms<D>(key, eid, (uint32_t)perm, (uint32_t)it * n_adapt + k, u);
         const float J = vegas_map<D>(S.gb, u, x, xc, bin);
         const float w = PH::eval(S.cache, P, x, xc) * J;
         if (isfinite(w)) {
@@ -248,14 +248,14 @@ __device__ void adapt_item(AdaptSmem<PH>& S, const float* __restrict__ recs, con
 template <class PH, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB)
 k_adapt(const float* __restrict__ recs, ProcConst P, TFConst T, int64_t n_items,
-        uint64_t seed, uint64_t event_id_base, int n_iters, uint32_t n_adapt, double alpha,
+        const __grid_constant__ PhiloxKey key, uint64_t event_id_base, int n_iters, uint32_t n_adapt, double alpha,
         const double* __restrict__ grid_in, GridBin* __restrict__ grid32,
         typename PH::Cache* __restrict__ caches) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   AdaptSmem<PH>& S = *reinterpret_cast<AdaptSmem<PH>*>(smem_raw);
   const int64_t item = blockIdx.x;
   if (item >= n_items) return;
-  adapt_item<PH, false>(S, recs, P, T, item, seed, event_id_base, n_iters, n_adapt, alpha,
+  adapt_item<PH, false>(S, recs, P, T, item, key, event_id_base, n_iters, n_adapt, alpha,
                         grid_in, grid32, caches, nullptr);
 }
 
@@ -265,7 +265,8 @@ k_adapt(const float* __restrict__ recs, ProcConst P, TFConst T, int64_t n_items,
 template <class PH, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB)
 k_adapt_list(const float* __restrict__ recs, ProcConst P, TFConst T,
-             const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, uint64_t seed,
+             const int32_t* __restrict__ list, const int32_t* __restrict__ n_list,
+             const __grid_constant__ PhiloxKey key,
              uint64_t event_id_base, int n_iters, uint32_t n_adapt, double alpha,
              GridBin* __restrict__ grid32, typename PH::Cache* __restrict__ caches,
              Slot* __restrict__ mom, const float* __restrict__ hist0) {
@@ -274,7 +275,7 @@ k_adapt_list(const float* __restrict__ recs, ProcConst P, TFConst T,
   const int n = *n_list;
   for (int b = blockIdx.x; b < n; b += gridDim.x) {
     const int64_t item = list[b];
-    adapt_item<PH, true>(S, recs, P, T, item, seed, event_id_base, n_iters, n_adapt, alpha,
+    adapt_item<PH, true>(S, recs, P, T, item, key, event_id_base, n_iters, n_adapt, alpha,
                          nullptr, grid32, caches, mom + item, hist0);
   }
 }
@@ -292,7 +293,8 @@ struct MainSmem {
 template <class PH, int PPT, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB)
 k_main(const float* __restrict__ recs, ProcConst P, TFConst T, int64_t n_items,
-       uint32_t chunks_per_item, uint64_t seed, uint64_t event_id_base, uint32_t idx0,
+       uint32_t chunks_per_item, const __grid_constant__ PhiloxKey key, uint64_t event_id_base,
+       uint32_t idx0,
        uint32_t n_main, const GridBin* __restrict__ grid32,
        const typename PH::Cache* __restrict__ caches, Slot* __restrict__ slots) {
   constexpr int D = PH::D;
@@ -324,7 +326,7 @@ k_main(const float* __restrict__ recs, ProcConst P, TFConst T, int64_t n_items,
       if (p < n_main) {
         float u[D], x[D], xc[D];
         int bin[D];
-        point_uniforms<D>(seed, eid, (uint32_t)perm, idx0 + p, u);
+        point_uniforms<D>(key, eid, (uint32_t)perm, idx0 + p, u);
         const float J = vegas_map<D>(S.gb, u, x, xc, bin);
         const float w = PH::eval(S.cache, P, x, xc) * J;
         if (isfinite(w)) {
@@ -375,7 +377,8 @@ __global__ void k_final(const Slot* __restrict__ slots, int64_t n_events, int np
 // Integrand at consecutive points of one item (parity tests): one thread per point.
 template <class PH>
 __global__ void __launch_bounds__(THREADS)
-k_eval(const float* __restrict__ rec, int perm, ProcConst P, TFConst T, uint64_t seed,
+k_eval(const float* __restrict__ rec, int perm, ProcConst P, TFConst T,
+       const __grid_constant__ PhiloxKey key,
        uint32_t event_id, uint32_t point0, int64_t n, const GridBin* __restrict__ gb,
        double* __restrict__ w_out) {
   constexpr int D = PH::D;
@@ -388,7 +391,7 @@ k_eval(const float* __restrict__ rec, int perm, ProcConst P, TFConst T, uint64_t
   if (i >= n) return;
   float u[D], x[D], xc[D];
   int bin[D];
-  point_uniforms<D>(seed, event_id, (uint32_t)perm, point0 + (uint32_t)i, u);
+  point_uniforms<D>(key, event_id, (uint32_t)perm, point0 + (uint32_t)i, u);
   const float J = vegas_map<D>(sg, u, x, xc, bin);
   const float w = cache.ok ? PH::eval(cache, P, x, xc) * J : 0.f;
   w_out[i] = (double)w * P.prefactor;

@@ -19,14 +19,14 @@ cudaError_t run_integrate(const IntegrateArgs& a, cudaStream_t st) {
   if (a.phase_events) cudaEventRecord(a.phase_events[0], st);
   // with n_iters == 0 the starting grid is frozen as given
   k_adapt<PH, MINB><<<(unsigned)a.n_items, THREADS, smem, st>>>(
-      a.recs, a.P, a.T, a.n_items, a.seed, a.event_id_base, a.n_iters, a.n_adapt, a.alpha,
+      a.recs, a.P, a.T, a.n_items, philox_key(a.seed), a.event_id_base, a.n_iters, a.n_adapt, a.alpha,
       a.grid_in, a.grid32, reinterpret_cast<typename PH::Cache*>(a.caches));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (a.phase_events) cudaEventRecord(a.phase_events[1], st);
   const uint64_t blocks = (uint64_t)a.n_items * a.chunks_per_item;
   k_main<PH, PPT, MINB><<<(unsigned)blocks, THREADS, 0, st>>>(
-      a.recs, a.P, a.T, a.n_items, a.chunks_per_item, a.seed, a.event_id_base, a.idx0, a.n_main,
+      a.recs, a.P, a.T, a.n_items, a.chunks_per_item, philox_key(a.seed), a.event_id_base, a.idx0, a.n_main,
       a.grid32, reinterpret_cast<const typename PH::Cache*>(a.caches), a.slots);
   return cudaGetLastError();
 }
@@ -39,7 +39,7 @@ size_t cache_bytes() {
 template <class PH>
 cudaError_t run_eval(const EvalArgs& a, cudaStream_t st) {
   const unsigned blocks = (unsigned)((a.n + THREADS - 1) / THREADS);
-  k_eval<PH><<<blocks, THREADS, 0, st>>>(a.rec, a.perm, a.P, a.T, a.seed, a.event_id, a.point0,
+  k_eval<PH><<<blocks, THREADS, 0, st>>>(a.rec, a.perm, a.P, a.T, philox_key(a.seed), a.event_id, a.point0,
                                          a.n, a.gb, a.w_out);
   return cudaGetLastError();
 }
