@@ -6,7 +6,9 @@
 
 namespace mem {
 
-template <class PH, int PPT, int MINB>
+// MINB: resident CTAs per SM the adaptation kernel is built for; MINB_MAIN: the
+// same for the frozen-grid kernel (its register budget is 65536 / (256 MINB_MAIN)).
+template <class PH, int PPT, int MINB, int MINB_MAIN = MINB>
 cudaError_t run_integrate(const IntegrateArgs& a, cudaStream_t st) {
   const size_t smem = sizeof(AdaptSmem<PH>);
   static bool attr_set = false;
@@ -25,7 +27,7 @@ cudaError_t run_integrate(const IntegrateArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   if (a.phase_events) cudaEventRecord(a.phase_events[1], st);
   const uint64_t blocks = (uint64_t)a.n_items * a.chunks_per_item;
-  k_main<PH, PPT, MINB><<<(unsigned)blocks, THREADS, 0, st>>>(
+  k_main<PH, PPT, MINB_MAIN><<<(unsigned)blocks, THREADS, 0, st>>>(
       a.recs, a.P, a.T, a.n_items, a.chunks_per_item, philox_key(a.seed), a.event_id_base, a.idx0, a.n_main,
       a.grid32, reinterpret_cast<const typename PH::Cache*>(a.caches), a.slots);
   return cudaGetLastError();
