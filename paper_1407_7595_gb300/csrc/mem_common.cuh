@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "mem_fastmath.cuh"
+
 namespace mem {
 
 constexpr int NG = 128;          // VEGAS bins per dimension
@@ -195,14 +197,14 @@ struct BW {
 __device__ __forceinline__ BW bw_map(float lo, float hi_minus_lo, float m2, float mg, float v,
                                      float w /* = 1 - v, exact */, float psi_hi) {
   const float hi = lo + hi_minus_lo;
-  const float psi_lo = atan2f(mg, m2 - lo);
-  const float R = atan2f(hi_minus_lo * mg, fmaf(hi - m2, lo - m2, mg * mg));
+  const float psi_lo = atan2_ypos(mg, m2 - lo);
+  const float R = atan2_ypos(hi_minus_lo * mg, fmaf(hi - m2, lo - m2, mg * mg));
   const float a_lo = fmaf(R, v, psi_lo);  // pi/2 + theta
   const float a_hi = fmaf(R, w, psi_hi);  // pi/2 - theta
-  const float c = sinf(a_lo <= a_hi ? a_lo : a_hi);  // cos(theta)
+  const float c = sin_0pi(a_lo <= a_hi ? a_lo : a_hi);  // cos(theta)
   const float s_lo = mg * rsqrtf(fmaf(m2 - lo, m2 - lo, mg * mg));  // sin(psi_lo)
   BW r;
-  r.d_lo = mg * sinf(R * v) / (c * s_lo);
+  r.d_lo = mg * sin_0pi(R * v) / (c * s_lo);
   r.q2 = lo + r.d_lo;
   r.R = R;
   r.inv_c2 = 1.f / (c * c);

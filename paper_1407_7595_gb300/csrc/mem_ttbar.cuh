@@ -247,14 +247,14 @@ struct PhysTT {
     const float lo_wh = aw * ju.lo;
     const float dw_wh = aw * ju.dw;
     const BW bwh = bw_map(lo_wh, dw_wh, P.mw2, P.mwgw, x[1], xc[1],
-                          atan2f(P.mwgw, lo_wh + dw_wh - P.mw2));
+                          atan2_ypos(P.mwgw, lo_wh + dw_wh - P.mw2));
     const float Eu = ju.lo + bwh.d_lo / aw;
     // antitop: q^2 = q^2_Wh + 2 E_bbar K, K = E_Wh - n_bbar . p_Wh
     const float K = fmaf(Ed, c.omc_bbd, Eu * c.omc_bbu);
     const float lo_tb = fmaf(2.f * K, jbb.lo, bwh.q2);
     const float dw_tb = 2.f * K * jbb.dw;
     const BW btb = bw_map(lo_tb, dw_tb, P.mt2, P.mtgt, x[2], xc[2],
-                          atan2f(P.mtgt, lo_tb + dw_tb - P.mt2));
+                          atan2_ypos(P.mtgt, lo_tb + dw_tb - P.mt2));
     const float Ebb = jbb.lo + btb.d_lo / (2.f * K);
     // neutrino transverse momentum
     const float sx = fmaf(2.f, x[3], -1.f), sy = fmaf(2.f, x[4], -1.f);
@@ -311,7 +311,7 @@ struct PhysTT {
       const float lo_t = fmaf(2.f * Kb, jb.lo, bwl.q2);
       const float dw_t = 2.f * Kb * jb.dw;
       const BW bt = bw_map(lo_t, dw_t, P.mt2, P.mtgt, x[6], xc[6],
-                           atan2f(P.mtgt, lo_t + dw_t - P.mt2));
+                           atan2_ypos(P.mtgt, lo_t + dw_t - P.mt2));
       const float Eb = jb.lo + bt.d_lo / (2.f * Kb);
       const float pbn = Eb * kbn;              // p_b . p_nu
       // lab totals and the transverse boost
