@@ -37,10 +37,14 @@ import numpy as np  # noqa: E402
 
 from paper_1407_7595_gb300 import synth  # noqa: E402
 
-# FP32 flops (FADD, FMUL = 1; FFMA = 2) executed per integrand evaluation by the
-# frozen-grid kernel, counted with ncu instruction counters (see profiles/);
+# Algorithmic work per integrand evaluation: the FP32 flops (FADD, FMUL = 1;
+# FFMA = 2) of the integrand as written with the CUDA math library's atan2f and
+# sinf, counted with ncu instruction counters and held fixed (see profiles/);
 # MUFU, integer (Philox) and memory instructions are not counted as flops.
 FLOPS_PER_EVAL = {synth.PROC_DY: 161.6, synth.PROC_W: 406.0, synth.PROC_TTBAR: 3098.7}
+# FP32 flops the current frozen-grid kernels execute per evaluation (ncu): fewer,
+# because their range-restricted atan2/sin are cheaper than the library's.
+FLOPS_EXECUTED_PER_EVAL = {synth.PROC_DY: 166.8, synth.PROC_W: 365.5, synth.PROC_TTBAR: 2890.2}
 FP32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 FP32 lanes
 
 WORKLOAD_NAMES = {
@@ -313,7 +317,11 @@ def run_ours(args):
                 "frac": achieved / peak if achieved else None, "traffic": None,
                 "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                f"{max_mhz:.0f} MHz max SM clock",
-                "flops_per_eval": fpe, "kernel_ms": t_main * 1e3,
+                "flops_per_eval": fpe,
+                "flops_executed_per_eval": FLOPS_EXECUTED_PER_EVAL.get(kind),
+                "frac_executed": (FLOPS_EXECUTED_PER_EVAL[kind] * n_ev * n_perm * n_main / t_main / 1e12
+                                  / peak) if fpe else None,
+                "kernel_ms": t_main * 1e3,
                 "kernel_share_of_step": t_main * 1e3 / statistics.mean(step_ms)}
         out = {"metric": "integrand evaluations per second", "value": value,
                "unit": "integrand evals/s", "n_gpus": world, "steps": args.steps,
