@@ -206,6 +206,8 @@ ProcConst make_proc_const(const mem_process_desc& d) {
     const double b = d.pdf_b[t];
     P.pdf_bint[t] = (b >= 0.0 && b <= 16.0 && b == std::floor(b)) ? (int)b : -1;
   }
+  P.pdf_std = P.pdf_amode[0] == 1 && P.pdf_amode[1] == 1 && P.pdf_amode[2] == 2 &&
+              P.pdf_bint[0] == 3 && P.pdf_bint[1] == 5 && P.pdf_bint[2] == 5;
   const double tp = 2.0 * PI_D;
   if (d.kind == PROC_DY) P.prefactor = (2.0 / s) / (4.0 * tp * tp);
   else if (d.kind == PROC_W) P.prefactor = (2.0 / s) / (8.0 * tp * tp);

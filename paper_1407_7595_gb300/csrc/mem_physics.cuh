@@ -34,6 +34,7 @@ struct ProcConst {
   float pdfA[3], pdfa[3], pdfb[3];
   int pdf_amode[3];         // 1: x^-1/2, 2: x^-1, 0: general power
   int pdf_bint[3];          // integer exponent of (1-x) if >= 0, else general power
+  int pdf_std;              // 1: (q, qbar, g) = x^-1/2 (1-x)^3, x^-1/2 (1-x)^5, x^-1 (1-x)^5
   double prefactor;         // FP64 constant multiplying every FP32 weight
 };
 
@@ -59,6 +60,31 @@ __device__ __forceinline__ float pdf(const ProcConst& P, int t, float x) {
     fb = exp2f(P.pdfb[t] * log2f(y));
   }
   return P.pdfA[t] * fa * fb;
+}
+
+// The three parton densities at one x (quark, antiquark, gluon). For the
+// standard shapes the powers of 1 - x and x^-1/2 are shared; other shapes take
+// the general form (the choice is uniform over a kernel: no divergence).
+struct PdfX {
+  float q, qb, g;
+};
+
+__device__ __forceinline__ PdfX pdf_all(const ProcConst& P, float x) {
+  PdfX f;
+  if (!(x > 0.f && x < 1.f)) {
+    f.q = f.qb = f.g = 0.f;
+  } else if (P.pdf_std) {
+    const float y = 1.f - x, y2 = y * y, y3 = y2 * y, y5 = y3 * y2;
+    const float rs = rsqrtf(x);
+    f.q = P.pdfA[0] * rs * y3;
+    f.qb = P.pdfA[1] * rs * y5;
+    f.g = P.pdfA[2] * y5 / x;
+  } else {
+    f.q = pdf(P, 0, x);
+    f.qb = pdf(P, 1, x);
+    f.g = pdf(P, 2, x);
+  }
+  return f;
 }
 
 // Per-object constants, computed in FP64 from (E, eta, phi) once per item.
@@ -202,7 +228,8 @@ struct PhysDY {
                                                     P.dy_opp[2] * inv_den));
     const float mA = fmaf(u * u, S, t * t * O);  // quark from beam 1
     const float mB = fmaf(t * t, S, u * u * O);  // quark from beam 2: t <-> u
-    const float fl = pdf(P, 0, b.x1) * pdf(P, 1, b.x2) * mA + pdf(P, 1, b.x1) * pdf(P, 0, b.x2) * mB;
+    const PdfX f1 = pdf_all(P, b.x1), f2 = pdf_all(P, b.x2);
+    const float fl = f1.q * f2.qb * mA + f1.qb * f2.q * mB;
     return c.cst * E[0] * E[1] * __expf(-0.5f * z2) * (4.f * is) * fl * (1.f / 3.f);
   }
 };
@@ -294,8 +321,8 @@ struct PhysW {
       light_cone(c.e, Ee, b, lm, lp);
       const float uA = b.x1 * P.sqrt_s * lm;  // -(k1 - p_e)^2
       const float uB = b.x2 * P.sqrt_s * lp;  // -(k2 - p_e)^2
-      const float fq1 = pdf(P, 0, b.x1), fqb1 = pdf(P, 1, b.x1);
-      const float fq2 = pdf(P, 0, b.x2), fqb2 = pdf(P, 1, b.x2);
+      const PdfX f1 = pdf_all(P, b.x1), f2 = pdf_all(P, b.x2);
+      const float fq1 = f1.q, fqb1 = f1.qb, fq2 = f2.q, fqb2 = f2.qb;
       // W+: (k_u . p_e+)^2 ; W-: (k_ubar . p_e-)^2
       acc += c.charge > 0 ? fmaf(fq1 * fqb2, uA * uA, fqb1 * fq2 * uB * uB)
                           : fmaf(fq1 * fqb2, uB * uB, fqb1 * fq2 * uA * uA);

@@ -405,9 +405,8 @@ struct PhysTT {
               (4.f / 3.f) * fmaf(A1.re, A2.re, A1.im * A2.im);
       }
       const float qqs = (4.f / shat) * (norm2(dot4(rx, Y)) + norm2(dot4(ry, Y)));
-      const float fg1 = pdf(P, 2, x1), fg2 = pdf(P, 2, x2);
-      const float fq1 = pdf(P, 0, x1), fq2 = pdf(P, 0, x2);
-      const float fqb1 = pdf(P, 1, x1), fqb2 = pdf(P, 1, x2);
+      const PdfX f1 = pdf_all(P, x1), f2 = pdf_all(P, x2);
+      const float fg1 = f1.g, fg2 = f2.g, fq1 = f1.q, fq2 = f2.q, fqb1 = f1.qb, fqb2 = f2.qb;
       const float init = fmaf(P.tt_gg * fg1 * fg2, gg,
                               P.tt_qq * 2.f * fmaf(fq1, fqb2, fqb1 * fq2) * qqs);
       const float gb = dgauss_g(c, jb.E, Eb);

@@ -195,3 +195,24 @@ def test_device_outputs_and_edge_cases(env):
         abi.Integrator(0, recs, synth.DEFAULT_PROCESS, synth.DEFAULT_TF[0])
     integ.close()
     bad_integ.close()
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_points_general_pdf_shapes(env, kind):
+    """Parton densities outside the standard shapes take the general path
+    (fractional exponents via exp2/log2, other integer powers): same per-point
+    rule against the oracle."""
+    abi, synth, O = env
+    params = dict(synth.DEFAULT_PROCESS)
+    params["pdf_a"] = (-0.4, -0.5, -1.0)
+    params["pdf_b"] = (3.5, 4.0, 5.0)
+    params["pdf_A"] = (1.3, 0.7, 1.0)
+    recs = synth.gen_events(kind, 3, 9300 + kind)
+    integ = abi.Integrator(kind, recs, params, synth.DEFAULT_TF[kind])
+    P = O.process(kind, params)
+    T = O.tf(synth.DEFAULT_TF[kind])
+    for e in range(len(recs)):
+        w_gpu = integ.eval_points(e, 0, 55, 0, 2048)
+        w_ora = O.eval_points(P, T, recs[e], e, 0, 55, 0, 2048)
+        check_points(w_gpu, w_ora)
+    integ.close()
