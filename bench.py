@@ -43,8 +43,9 @@ from paper_1407_7595_gb300 import synth  # noqa: E402
 # MUFU, integer (Philox) and memory instructions are not counted as flops.
 FLOPS_PER_EVAL = {synth.PROC_DY: 161.6, synth.PROC_W: 406.0, synth.PROC_TTBAR: 3098.7}
 # FP32 flops the current frozen-grid kernels execute per evaluation (ncu): fewer,
-# because their range-restricted atan2/sin are cheaper than the library's.
-FLOPS_EXECUTED_PER_EVAL = {synth.PROC_DY: 166.8, synth.PROC_W: 365.5, synth.PROC_TTBAR: 2890.2}
+# because their range-restricted atan2/sin and shared parton densities are
+# cheaper than the library functions and the per-flavour evaluation.
+FLOPS_EXECUTED_PER_EVAL = {synth.PROC_DY: 157.0, synth.PROC_W: 345.7, synth.PROC_TTBAR: 2842.3}
 FP32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 FP32 lanes
 
 WORKLOAD_NAMES = {
