@@ -163,3 +163,47 @@ int ora_integrate(const ora_process* P, const ora_tf* T, const float* recs, int6
   free(J.item_var);
   return 0;
 }
+
+/* Parton-level ttbar weights of n records on n_threads threads (static blocks of
+ * events): w_out[2 i + bperm] per b-quark assignment, prob_out[i] = their mean
+ * (Sec. 4, parton level: the average over the b-quark assignments). */
+typedef struct {
+  const ora_process* P;
+  const float* recs;
+  int64_t lo, hi;
+  double *prob, *w;
+} parton_job_t;
+
+static void* parton_worker(void* arg) {
+  parton_job_t* J = (parton_job_t*)arg;
+  for (int64_t i = J->lo; i < J->hi; ++i) {
+    double w0 = ora_parton_ttbar(J->P, J->recs + i * ORA_REC, 0, NULL);
+    double w1 = ora_parton_ttbar(J->P, J->recs + i * ORA_REC, 1, NULL);
+    if (J->w) {
+      J->w[2 * i] = w0;
+      J->w[2 * i + 1] = w1;
+    }
+    J->prob[i] = 0.5 * (w0 + w1);
+  }
+  return NULL;
+}
+
+void ora_parton_batch(const ora_process* P, const float* recs, int64_t n, int n_threads,
+                      double* prob_out, double* w_out) {
+  int nt = n_threads > 0 ? n_threads : 1;
+  if (nt > n) nt = n > 0 ? (int)n : 1;
+  parton_job_t* jobs = (parton_job_t*)malloc(sizeof(parton_job_t) * nt);
+  pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * nt);
+  for (int t = 0; t < nt; ++t) {
+    jobs[t].P = P;
+    jobs[t].recs = recs;
+    jobs[t].lo = n * t / nt;
+    jobs[t].hi = n * (t + 1) / nt;
+    jobs[t].prob = prob_out;
+    jobs[t].w = w_out;
+    pthread_create(&th[t], NULL, parton_worker, &jobs[t]);
+  }
+  for (int t = 0; t < nt; ++t) pthread_join(th[t], NULL);
+  free(th);
+  free(jobs);
+}

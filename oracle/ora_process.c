@@ -346,22 +346,57 @@ static double flavour_sum(const ora_process* P, const rv4* b, rv4 k1, rv4 k2, do
   return sum;
 }
 
+/* Weight of one final state: PDF-weighted |M|^2, flux 1/(|q1||q2|), (2 pi)^4 and the
+ * 2/s of the consumed dx1 dx2, times the state's measure, TF and Jacobian factors.
+ * aux (optional): x1, x2, s-hat, PDF-weighted |M|^2. */
+static double state_weight(const ora_process* P, const state_t* S, const float* rec,
+                           double* aux) {
+  rv4 b[6], k1, k2;
+  double x1, x2;
+  to_parton_frame(P, S, b, &k1, &k2, &x1, &x2);
+  if (!(x1 > 0.0 && x1 < 1.0 && x2 > 0.0 && x2 < 1.0)) return 0.0;
+  double s = P->sqrt_s * P->sqrt_s;
+  double msq = flavour_sum(P, b, k1, k2, x1, x2, rec);
+  double flux = 1.0 / (k1.v[0] * k2.v[0]); /* 1/(|q1||q2|) */
+  if (aux) {
+    aux[0] = x1;
+    aux[1] = x2;
+    aux[2] = x1 * x2 * s;
+    aux[3] = msq;
+  }
+  return msq * flux * pow(TWO_PI, 4) * (2.0 / s) * S->meas * S->tf * S->jac;
+}
+
 double ora_integrand(const ora_process* P, const ora_tf* T, const float* rec, int perm,
                      const double* x) {
   state_t st[2];
   int n = build_states(P, T, rec, perm, x, st);
-  double s = P->sqrt_s * P->sqrt_s;
   double total = 0.0;
-  for (int r = 0; r < n; ++r) {
-    rv4 b[6], k1, k2;
-    double x1, x2;
-    to_parton_frame(P, &st[r], b, &k1, &k2, &x1, &x2);
-    if (!(x1 > 0.0 && x1 < 1.0 && x2 > 0.0 && x2 < 1.0)) continue;
-    double msq = flavour_sum(P, b, k1, k2, x1, x2, rec);
-    double flux = 1.0 / (k1.v[0] * k2.v[0]); /* 1/(|q1||q2|) */
-    total += msq * flux * pow(TWO_PI, 4) * (2.0 / s) * st[r].meas * st[r].tf * st[r].jac;
-  }
+  for (int r = 0; r < n; ++r) total += state_weight(P, &st[r], rec, NULL);
   return total;
+}
+
+/* Parton-level ttbar weight (Sec. 4, parton level): every final-state momentum is
+ * known, so all transfer functions are delta functions and nothing is integrated.
+ * The record holds l+, the two b quarks, d, ubar and the neutrino as objects 0..5;
+ * bperm = 0 takes object 1 as the b and object 2 as the bbar, bperm = 1 the reverse.
+ * Weight = the integrand's density at these momenta: PDF-weighted |M|^2, flux,
+ * (2 pi)^4 2/s and prod_i 1/((2 pi)^3 2 E_i) over the six final-state particles. */
+double ora_parton_ttbar(const ora_process* P, const float* rec, int bperm, double* aux) {
+  if (P->kind != 2 || bperm < 0 || bperm > 1) return 0.0;
+  const int slot[6] = {1 + bperm, 0, 5, 2 - bperm, 3, 4}; /* b, l+, nu, bbar, d, ubar */
+  state_t S;
+  memset(&S, 0, sizeof(S));
+  S.nfs = 6;
+  S.meas = 1.0;
+  S.tf = 1.0;
+  S.jac = 1.0;
+  for (int i = 0; i < 6; ++i) {
+    obj_t o = get_obj(rec, slot[i]);
+    S.lab[i] = massless(o.E, o.n);
+    S.meas *= inv_ps(o.E);
+  }
+  return state_weight(P, &S, rec, aux);
 }
 
 int ora_kinematics(const ora_process* P, const ora_tf* T, const float* rec, int perm,

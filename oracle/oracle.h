@@ -78,6 +78,16 @@ double ora_integrand(const ora_process* P, const ora_tf* T, const float* rec, in
  * fs_lab receives the same momenta before the boost (lab frame).
  * Returns the number of root branches (0 if the point has no solution).
  * `root` picks the branch. Extra diagnostics in aux (process dependent). */
+/* Parton-level ttbar weight (Sec. 4): delta TFs for all six final-state partons of a
+ * parton-level record (objects l+, b-quark, b-quark, d, ubar, neutrino); bperm 0/1
+ * assigns objects 1/2 to (b, bbar) or (bbar, b). aux (NULL or 4 doubles): x1, x2,
+ * s-hat, PDF-weighted |M|^2. */
+double ora_parton_ttbar(const ora_process* P, const float* rec, int bperm, double* aux);
+/* The above for n records on n_threads threads: w_out (NULL or 2n) per assignment,
+ * prob_out (n) their mean. */
+void ora_parton_batch(const ora_process* P, const float* recs, int64_t n, int n_threads,
+                      double* prob_out, double* w_out);
+
 int ora_kinematics(const ora_process* P, const ora_tf* T, const float* rec, int perm,
                    const double* x, int root, double* fs, double* fs_lab, double* k12,
                    double* aux);

@@ -90,6 +90,9 @@ def load():
     lib.ora_msq_dy.restype = C.c_double
     lib.ora_msq_w.argtypes = [P, C.c_int, _dp, _dp, _dp, _dp]
     lib.ora_msq_w.restype = C.c_double
+    lib.ora_parton_ttbar.argtypes = [P, fp, C.c_int, _dp]
+    lib.ora_parton_ttbar.restype = C.c_double
+    lib.ora_parton_batch.argtypes = [P, fp, C.c_int64, C.c_int, _dp, _dp]
     lib.ora_msq_ttbar.argtypes = [P, C.c_int] + [_dp] * 8
     lib.ora_msq_ttbar.restype = C.c_double
     lib.ora_msq_ttbar_production.argtypes = [P, C.c_int, _dp, _dp, _dp, _dp]
@@ -184,6 +187,27 @@ def kinematics(P, T, rec, perm, x, root):
                               k12.ctypes.data_as(_dp), aux.ctypes.data_as(_dp))
     return {"n": n, "fs": fs.reshape(6, 4), "lab": lab.reshape(6, 4), "k12": k12.reshape(2, 4),
             "aux": aux}
+
+
+def parton_ttbar(P, rec, bperm):
+    """Parton-level ttbar weight of one record and b-quark assignment (Sec. 4);
+    returns (weight, aux = (x1, x2, s-hat, PDF-weighted |M|^2))."""
+    rec, rp = _rec_ptr(rec)
+    aux = np.zeros(4)
+    w = load().ora_parton_ttbar(C.byref(P), rp, bperm, aux.ctypes.data_as(_dp))
+    return w, aux
+
+
+def parton_batch(P, recs, n_threads=None):
+    """Parton-level weights of many records: (prob (n,), w (n, 2))."""
+    recs = np.ascontiguousarray(recs, dtype=np.float32).reshape(-1, REC)
+    n = recs.shape[0]
+    prob = np.zeros(n)
+    w = np.zeros((n, 2))
+    load().ora_parton_batch(C.byref(P), recs.ctypes.data_as(C.POINTER(C.c_float)), n,
+                            n_threads or os.cpu_count() or 1, prob.ctypes.data_as(_dp),
+                            w.ctypes.data_as(_dp))
+    return prob, w
 
 
 def msq_dy(P, flavour, kq, kqb, plm, plp):

@@ -19,9 +19,16 @@ Event record: 32 float32 values per event.
                                       jet permutation that matches the partons
                                       (diagnostic only, never read by the method)
   [29..31]                          : zero
-Object kinds: 1 mu-, 2 mu+, 3 e-, 4 e+, 5 jet.
+Object kinds: 1 mu-, 2 mu+, 3 e-, 4 e+, 5 jet, 6 neutrino.
 Object order: DY (mu-, mu+); W (charged lepton); ttbar (l+, 4 jets by
 decreasing measured energy).
+
+Parton-level ttbar record (the parton-level analysis of Sec. 4: every final-state
+momentum known exactly): the same layout with exact energies and
+  objects 0..5 : l+, the two b quarks (by decreasing energy), d, ubar, neutrino
+  [24], [25]   : neutrino (px, py);  [26] = 6;  [27] = 2 (ttbar)
+  [28]         : generator truth: 0 if object 1 is the b (object 2 the bbar), else 1
+  [29]         : 1 (marks a parton-level record)
 """
 from __future__ import annotations
 
@@ -31,7 +38,7 @@ import math
 import numpy as np
 
 RECORD_FLOATS = 32
-KIND_NONE, KIND_MU_MINUS, KIND_MU_PLUS, KIND_E_MINUS, KIND_E_PLUS, KIND_JET = range(6)
+KIND_NONE, KIND_MU_MINUS, KIND_MU_PLUS, KIND_E_MINUS, KIND_E_PLUS, KIND_JET, KIND_NU = range(7)
 PROC_DY, PROC_W, PROC_TTBAR = 0, 1, 2
 
 SQRT_S = 13000.0
@@ -245,6 +252,102 @@ def gen_ttbar(n, seed, tf=None):
         r[27] = PROC_TTBAR
         r[28] = perms.index(truth)
         i += 1
+    return out
+
+
+# ------------------------------------------------ parton-level ttbar (vectorised)
+def _bw_mass_v(rng, m, w, k, n):
+    """n Breit-Wigner masses (Cauchy in m^2) truncated to m -+ k w."""
+    a = np.arctan(((m - k * w) ** 2 - m * m) / (m * w))
+    b = np.arctan(((m + k * w) ** 2 - m * m) / (m * w))
+    return np.sqrt(m * m + m * w * np.tan(rng.uniform(a, b, n)))
+
+
+def _two_body_v(rng, M, m1, m2):
+    """Isotropic two-body decays at rest of masses M (array) into m1, m2 (arrays
+    or scalars); (n, 4) momenta of both daughters."""
+    lam = (M * M - (m1 + m2) ** 2) * (M * M - (m1 - m2) ** 2)
+    p = np.sqrt(np.maximum(lam, 0.0)) / (2.0 * M)
+    c = rng.uniform(-1.0, 1.0, M.shape)
+    s = np.sqrt(np.maximum(0.0, 1.0 - c * c))
+    ph = rng.uniform(0.0, 2.0 * math.pi, M.shape)
+    d = np.stack([s * np.cos(ph), s * np.sin(ph), c], axis=1)
+    p1 = np.concatenate([np.sqrt(p * p + m1 * m1 + 0 * M)[:, None], p[:, None] * d], axis=1)
+    p2 = np.concatenate([np.sqrt(p * p + m2 * m2 + 0 * M)[:, None], -p[:, None] * d], axis=1)
+    return p1, p2
+
+
+def _boost_v(p, parent):
+    """Row-wise version of _boost_to_lab."""
+    E = parent[:, 0]
+    bvec = parent[:, 1:] / E[:, None]
+    b2 = np.sum(bvec * bvec, axis=1)
+    m = np.sqrt(np.maximum(E * E - np.sum(parent[:, 1:] ** 2, axis=1), 0.0))
+    g = E / m
+    bp = np.sum(bvec * p[:, 1:], axis=1)
+    g2 = np.where(b2 > 0, (g - 1.0) / np.where(b2 > 0, b2, 1.0), 0.0)
+    out = np.empty_like(p)
+    out[:, 0] = g * (p[:, 0] + bp)
+    out[:, 1:] = p[:, 1:] + (g2 * bp)[:, None] * bvec + (g * p[:, 0])[:, None] * bvec
+    return out
+
+
+def _eta_phi_v(p):
+    pt = np.hypot(p[:, 1], p[:, 2])
+    return np.arcsinh(p[:, 3] / pt), np.arctan2(p[:, 2], p[:, 1]), pt
+
+
+def gen_ttbar_parton(n, seed):
+    """Parton-level semileptonic ttbar events (Sec. 4, parton level): the same
+    production and decay chain as gen_ttbar, no smearing, the neutrino kept as
+    object 5; l+ and the quarks within |eta| <= 2.5, quarks with E >= 20 GeV."""
+    P = DEFAULT_PROCESS
+    rng = np.random.Generator(np.random.Philox(seed))
+    out = np.zeros((n, RECORD_FLOATS), dtype=np.float32)
+    have = 0
+    while have < n:
+        m = max(1024, 2 * (n - have))
+        mtt = rng.uniform(350.0, 1000.0, m)
+        mt1 = _bw_mass_v(rng, P["mt"], P["wt"], 15.0, m)
+        mt2 = _bw_mass_v(rng, P["mt"], P["wt"], 15.0, m)
+        mw1 = _bw_mass_v(rng, P["mw"], P["ww"], 15.0, m)
+        mw2 = _bw_mass_v(rng, P["mw"], P["ww"], 15.0, m)
+        y = rng.uniform(-1.5, 1.5, m)
+        ok = mt1 + mt2 < mtt
+        mtt = np.where(ok, mtt, mt1 + mt2 + 1.0)
+        sysp = np.stack([mtt * np.cosh(y), 0 * y, 0 * y, mtt * np.sinh(y)], axis=1)
+        t, tb = _two_body_v(rng, mtt, mt1, mt2)
+        t, tb = _boost_v(t, sysp), _boost_v(tb, sysp)
+        b, wp = _two_body_v(rng, mt1, 0.0, mw1)
+        b, wp = _boost_v(b, t), _boost_v(wp, t)
+        lep, nu = _two_body_v(rng, mw1, 0.0, 0.0)
+        lep, nu = _boost_v(lep, wp), _boost_v(nu, wp)
+        bb, wm = _two_body_v(rng, mt2, 0.0, mw2)
+        bb, wm = _boost_v(bb, tb), _boost_v(wm, tb)
+        d, ub = _two_body_v(rng, mw2, 0.0, 0.0)
+        d, ub = _boost_v(d, wm), _boost_v(ub, wm)
+        for q in (lep, b, bb, d, ub):
+            ok &= np.abs(_eta_phi_v(q)[0]) <= 2.5
+        for q in (b, bb, d, ub):
+            ok &= q[:, 0] >= 20.0
+        swap = (bb[:, 0] > b[:, 0])[:, None]   # object 1 = the more energetic b quark
+        objs = [lep, np.where(swap, bb, b), np.where(swap, b, bb), d, ub, nu]
+        kinds = [KIND_E_PLUS, KIND_JET, KIND_JET, KIND_JET, KIND_JET, KIND_NU]
+        idx = np.nonzero(ok)[0][: n - have]
+        r = out[have: have + len(idx)]
+        for slot, q in enumerate(objs):
+            eta, phi, _ = _eta_phi_v(q[idx])
+            r[:, 4 * slot] = q[idx, 0]
+            r[:, 4 * slot + 1] = eta
+            r[:, 4 * slot + 2] = phi
+            r[:, 4 * slot + 3] = kinds[slot]
+        r[:, 24] = nu[idx, 1]
+        r[:, 25] = nu[idx, 2]
+        r[:, 26] = 6
+        r[:, 27] = PROC_TTBAR
+        r[:, 28] = swap[idx, 0].astype(np.float32)
+        r[:, 29] = 1.0
+        have += len(idx)
     return out
 
 

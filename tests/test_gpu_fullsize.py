@@ -53,8 +53,8 @@ def test_w_full_size_frozen_grid(env):
     with ThreadPoolExecutor(len(picks)) as ex:
         outs = list(ex.map(oracle_one, picks))
     for e, o in zip(picks, outs):
-        assert g["prob"][e] == pytest.approx(o["prob"][0], rel=1e-6), e
-        assert g["err"][e] == pytest.approx(o["err"][0], rel=1e-4), e
+        assert g["prob"][e] == pytest.approx(o["prob"][0], rel=1e-6, abs=0), e
+        assert g["err"][e] == pytest.approx(o["err"][0], rel=1e-4, abs=0), e
     integ.close()
 
 

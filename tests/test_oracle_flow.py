@@ -88,7 +88,7 @@ def test_features_closed_form():
         rec[4 * o:4 * o + 4] = (40.0, 0.0, 0.0, 5.0)
     rec[24:26] = (0.0, -30.0)
     f = F.features(rec, 0)
-    assert f[0] == pytest.approx(0.5) and abs(f[1]) < 1e-12
+    assert f[0] == pytest.approx(0.5, rel=1e-12, abs=0) and abs(f[1]) < 1e-12
     assert f[2:5] == pytest.approx([0.0, 0.64, 0.48], abs=1e-6)
     assert f[5:8] == pytest.approx([0.0, -0.4, 0.0], abs=1e-6)   # phi = 0 jet -> -y
     assert f[14:16] == pytest.approx([-0.3, 0.0], abs=1e-6)
@@ -116,6 +116,6 @@ def test_features_invariances():
             assert np.allclose(f[2 + 3 * k:5 + 3 * k], base[2 + 3 * j:5 + 3 * j])
     for k in range(4):
         E, eta = rec[4 * (k + 1)], rec[4 * (k + 1) + 1]
-        assert np.linalg.norm(base[2 + 3 * k:5 + 3 * k]) == pytest.approx(E / 100, rel=1e-6)
-        assert np.hypot(*base[2 + 3 * k:4 + 3 * k]) == pytest.approx(E / np.cosh(eta) / 100, rel=1e-6)
-    assert np.hypot(base[14], base[15]) == pytest.approx(np.hypot(rec[24], rec[25]) / 100, rel=1e-6)
+        assert np.linalg.norm(base[2 + 3 * k:5 + 3 * k]) == pytest.approx(E / 100, rel=1e-6, abs=0)
+        assert np.hypot(*base[2 + 3 * k:4 + 3 * k]) == pytest.approx(E / np.cosh(eta) / 100, rel=1e-6, abs=0)
+    assert np.hypot(base[14], base[15]) == pytest.approx(np.hypot(rec[24], rec[25]) / 100, rel=1e-6, abs=0)

@@ -66,13 +66,13 @@ def test_conservation_and_masses(ora, synth, events, kind):
                     assert abs(dot(p, p)) < 1e-10 * p[0] ** 2
                 if kind == 1:
                     w = fs[0] + fs[1]
-                    assert dot(w, w) == pytest.approx(aux[0], rel=1e-10)
+                    assert dot(w, w) == pytest.approx(aux[0], rel=1e-10, abs=0)
                 if kind == 2:
                     b, l, n, bb, dq, ub = fs[:6]
-                    assert dot(dq + ub, dq + ub) == pytest.approx(aux[0], rel=1e-10)
-                    assert dot(bb + dq + ub, bb + dq + ub) == pytest.approx(aux[1], rel=1e-10)
-                    assert dot(l + n, l + n) == pytest.approx(aux[2], rel=1e-10)
-                    assert dot(b + l + n, b + l + n) == pytest.approx(aux[3], rel=1e-10)
+                    assert dot(dq + ub, dq + ub) == pytest.approx(aux[0], rel=1e-10, abs=0)
+                    assert dot(bb + dq + ub, bb + dq + ub) == pytest.approx(aux[1], rel=1e-10, abs=0)
+                    assert dot(l + n, l + n) == pytest.approx(aux[2], rel=1e-10, abs=0)
+                    assert dot(b + l + n, b + l + n) == pytest.approx(aux[3], rel=1e-10, abs=0)
                 checked += 1
     assert checked > 50
 
@@ -106,24 +106,23 @@ def test_jacobian_is_determinant_of_the_map(ora, synth, events, kind):
                     M[:, j] = (physical_vars(kind, kp["lab"]) - physical_vars(kind, km["lab"])) / (2 * h)
                 if not ok:
                     continue
-                assert abs(np.linalg.det(M)) == pytest.approx(jac, rel=2e-5)
+                assert abs(np.linalg.det(M)) == pytest.approx(jac, rel=2e-5, abs=0)
                 n_ok += 1
     assert n_ok >= 10
 
 
 def test_parton_level_limit_dy(ora, synth, events):
     """Vanishing resolution: int f dx -> the delta-TF evaluation at the measured
-    momenta, times the Gaussian mass inside the +-5 sigma window per lepton."""
-    r = 1e-4
-    P, T = _setup(ora, synth, 0, {"lep_rel": r})
+    momenta, times the Gaussian mass inside the +-5 sigma window per lepton. At
+    relative resolution r the deviation is O(r^2) (the resonance is smeared over
+    sigma_q2 ~ r m^2): it must shrink fourfold when r halves, and the Richardson
+    extrapolation to r = 0 must vanish."""
     p = synth.DEFAULT_PROCESS
     s = p["sqrt_s"] ** 2
     xg, wg = np.polynomial.legendre.leggauss(48)
     xg = 0.5 * (xg + 1)
     wg = 0.5 * wg
     for rec in events[0][:2]:
-        quad = sum(wa * wb * ora.integrand(P, T, rec, 0, [a, b])
-                   for a, wa in zip(xg, wg) for b, wb in zip(xg, wg))
         # delta-TF value at the measured momenta
         mom = []
         meas = 1.0
@@ -148,10 +147,19 @@ def test_parton_level_limit_dy(ora, synth, events):
         rs = p["sqrt_s"]
         k1 = np.array([x1 * rs / 2, 0, 0, x1 * rs / 2])
         k2 = np.array([x2 * rs / 2, 0, 0, -x2 * rs / 2])
+        P0, _ = _setup(ora, synth, 0)
         fsum = 0.0
         for fl in (0, 1):
-            fsum += ora.pdf(P, 0, x1) * ora.pdf(P, 1, x2) * ora.msq_dy(P, fl, k1, k2, lm, lp)
-            fsum += ora.pdf(P, 1, x1) * ora.pdf(P, 0, x2) * ora.msq_dy(P, fl, k2, k1, lm, lp)
+            fsum += ora.pdf(P0, 0, x1) * ora.pdf(P0, 1, x2) * ora.msq_dy(P0, fl, k1, k2, lm, lp)
+            fsum += ora.pdf(P0, 1, x1) * ora.pdf(P0, 0, x2) * ora.msq_dy(P0, fl, k2, k1, lm, lp)
         want = fsum / (k1[0] * k2[0]) * (2 * math.pi) ** 4 * (2 / s) * meas
         window = math.erf(5 / math.sqrt(2)) ** 2
-        assert quad == pytest.approx(want * window, rel=2e-5)
+        dev = []
+        for r in (2e-4, 1e-4):
+            P, T = _setup(ora, synth, 0, {"lep_rel": r})
+            quad = sum(wa * wb * ora.integrand(P, T, rec, 0, [a, b])
+                       for a, wa in zip(xg, wg) for b, wb in zip(xg, wg))
+            dev.append(quad / (want * window) - 1.0)
+        assert abs(dev[1]) < 1e-4
+        assert 3.0 < dev[0] / dev[1] < 5.0
+        assert abs((4.0 * dev[1] - dev[0]) / 3.0) < 2e-6

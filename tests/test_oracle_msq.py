@@ -98,10 +98,10 @@ def test_dy_vs_helicity_form(ora, params):
             for fl in (0, 1):
                 want = dy_helicity(params, fl, k1, k2, pm, pp)
                 got = ora.msq_dy(P, fl, k1, k2, pm, pp)
-                assert got == pytest.approx(want, rel=1e-12)
+                assert got == pytest.approx(want, rel=1e-12, abs=0)
                 # quark from the other beam
                 got2 = ora.msq_dy(P, fl, k2, k1, pm, pp)
-                assert got2 == pytest.approx(dy_helicity(params, fl, k2, k1, pm, pp), rel=1e-12)
+                assert got2 == pytest.approx(dy_helicity(params, fl, k2, k1, pm, pp), rel=1e-12, abs=0)
 
 
 def test_dy_forward_backward_sign(ora, params):
@@ -124,7 +124,7 @@ def test_dy_photon_only_cross_section(ora, params):
     for fl, Q in ((0, 2 / 3), (1, -1 / 3)):
         avg = sum(w * ora.msq_dy(P, fl, *two_to_two(rs, c)) for c, w in zip(xg, wg)) / 2.0
         sigma = avg / (8 * math.pi) / (2 * s)   # int dPhi_2 = 1/(8 pi); flux 1/(2s)
-        assert sigma == pytest.approx(4 * math.pi * p["alpha"] ** 2 * Q * Q / (9 * s), rel=1e-9)
+        assert sigma == pytest.approx(4 * math.pi * p["alpha"] ** 2 * Q * Q / (9 * s), rel=1e-9, abs=0)
 
 
 def test_w_vs_closed_forms(ora, params):
@@ -140,17 +140,17 @@ def test_w_vs_closed_forms(ora, params):
             # W+: u(k1) dbar(k2) -> e+(p3) nu(p4); |M|^2 = g^4 u^2/(12 D2), u = (k_u - p_e+)^2
             u = dot(k1 - p3, k1 - p3)
             assert ora.msq_w(P, +1, k1, k2, p3, p4) == pytest.approx(g2 * g2 * u * u / (12 * D2),
-                                                                     rel=1e-12)
+                                                                     rel=1e-12, abs=0)
             # W-: d(k1) ubar(k2) -> e-(p3) nubar(p4); |M|^2 = g^4 (k_d - p_nubar)^4/(12 D2)
             u2 = dot(k1 - p4, k1 - p4)
             assert ora.msq_w(P, -1, k1, k2, p3, p4) == pytest.approx(g2 * g2 * u2 * u2 / (12 * D2),
-                                                                     rel=1e-12)
+                                                                     rel=1e-12, abs=0)
         # total: sigma = G_F^2 m_W^4 s / (18 pi D2) with G_F = sqrt2 g^2 / (8 m_W^2)
         xg, wg = np.polynomial.legendre.leggauss(16)
         avg = sum(w * ora.msq_w(P, +1, *two_to_two(rs, c)) for c, w in zip(xg, wg)) / 2.0
         sigma = avg / (8 * math.pi) / (2 * s)
         GF = math.sqrt(2) * g2 / (8 * mw * mw)
-        assert sigma == pytest.approx(GF ** 2 * mw ** 4 * s / (18 * math.pi * D2), rel=1e-9)
+        assert sigma == pytest.approx(GF ** 2 * mw ** 4 * s / (18 * math.pi * D2), rel=1e-9, abs=0)
 
 
 def _tt_kinematics(rng, rs, m):
@@ -176,8 +176,8 @@ def test_ttbar_production_vs_closed_forms(ora, params):
             t1, t2, rho = 2 * dot(k1, pt) / s, 2 * dot(k2, pt) / s, 4 * m * m / s
             gg = g4 * (1 / (6 * t1 * t2) - 3 / 8) * (t1 * t1 + t2 * t2 + rho - rho * rho / (4 * t1 * t2))
             qq = g4 * (4 / 9) * (t1 * t1 + t2 * t2 + rho / 2)
-            assert ora.msq_ttbar_production(P, 0, k1, k2, pt, ptb) == pytest.approx(gg, rel=1e-11)
-            assert ora.msq_ttbar_production(P, 1, k1, k2, pt, ptb) == pytest.approx(qq, rel=1e-11)
+            assert ora.msq_ttbar_production(P, 0, k1, k2, pt, ptb) == pytest.approx(gg, rel=1e-11, abs=0)
+            assert ora.msq_ttbar_production(P, 1, k1, k2, pt, ptb) == pytest.approx(qq, rel=1e-11, abs=0)
 
 
 def test_ttbar_gauge_invariance(ora, params):
@@ -207,14 +207,14 @@ def test_top_decay_spin_analyser(ora, params):
         pb, pl, pn = (_random_massless(rng) for _ in range(3))
         out = ora.top_decay_probe(P, pb, pl, pn)
         base = 32 * m ** 3 * dot(pb, pn)
-        assert out[0] == pytest.approx(base * (pl[0] + pl[3]), rel=1e-12)
-        assert out[1] == pytest.approx(base * (pl[0] - pl[3]), rel=1e-12)
+        assert out[0] == pytest.approx(base * (pl[0] + pl[3]), rel=1e-12, abs=0)
+        assert out[1] == pytest.approx(base * (pl[0] - pl[3]), rel=1e-12, abs=0)
         # antitop: the down-type quark d is the analyser, (p_bbar . p_ubar) the other factor
         pbb, pd, pu = (_random_massless(rng) for _ in range(3))
         out = ora.top_decay_probe(P, pbb, pd, pu, anti=True)
         base = 32 * m ** 3 * dot(pbb, pu)
         want = sorted([base * (pd[0] + pd[3]), base * (pd[0] - pd[3])])
-        assert sorted(out) == pytest.approx(want, rel=1e-12)
+        assert sorted(out) == pytest.approx(want, rel=1e-12, abs=0)
 
 
 def _decay3(rng, M, m12):
@@ -270,7 +270,7 @@ def test_ttbar_full_factorises_after_parity_average(ora, params, channel):
                 ct = 8 * dot(pt, pl) * dot(pb, pn)
                 ctb = 8 * dot(ptb, pd) * dot(pbb, pu)
         prod = ora.msq_ttbar_production(P, channel, k1, k2, pt, ptb)
-        assert acc / 4 == pytest.approx(prod * (gw2 / 2) ** 4 * 6 * ct * ctb, rel=1e-9)
+        assert acc / 4 == pytest.approx(prod * (gw2 / 2) ** 4 * 6 * ct * ctb, rel=1e-9, abs=0)
 
 
 def test_lorentz_invariance(ora, params, synth):
@@ -281,10 +281,10 @@ def test_lorentz_invariance(ora, params, synth):
         L = rot_boost(rng)
         a = ora.msq_dy(Pd, 0, k1, k2, p3, p4)
         b = ora.msq_dy(Pd, 0, L @ k1, L @ k2, L @ p3, L @ p4)
-        assert b == pytest.approx(a, rel=1e-11)
+        assert b == pytest.approx(a, rel=1e-11, abs=0)
         a = ora.msq_w(Pw, 1, k1, k2, p3, p4)
         b = ora.msq_w(Pw, 1, L @ k1, L @ k2, L @ p3, L @ p4)
-        assert b == pytest.approx(a, rel=1e-11)
+        assert b == pytest.approx(a, rel=1e-11, abs=0)
     # ttbar: gluon polarisations are defined transverse to the beam axis, so use
     # transformations that keep the beams on the z axis (z rotations and z boosts)
     for ch in (0, 1):
@@ -295,4 +295,4 @@ def test_lorentz_invariance(ora, params, synth):
         a = ora.msq_ttbar(Pt, ch, k1, k2, *mom)
         L = rot_boost(rng, general=False)
         b2 = ora.msq_ttbar(Pt, ch, L @ k1, L @ k2, *[L @ v for v in mom])
-        assert b2 == pytest.approx(a, rel=1e-10)
+        assert b2 == pytest.approx(a, rel=1e-10, abs=0)
