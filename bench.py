@@ -48,7 +48,13 @@ FLOPS_PER_EVAL = {synth.PROC_DY: 161.6, synth.PROC_W: 406.0, synth.PROC_TTBAR: 3
 FLOPS_EXECUTED_PER_EVAL = {synth.PROC_DY: 157.0, synth.PROC_W: 345.7, synth.PROC_TTBAR: 2842.3}
 FP32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 FP32 lanes
 
+# FP32 flops of the parton-level kernel per event (both b-quark assignments; FADD,
+# FMUL = 1, FFMA = 2), counted with ncu instruction counters and held fixed.
+FLOPS_PER_PARTON_EVENT = 2224.0
+
 WORKLOAD_NAMES = {
+    "parton": "parton-level semileptonic ttbar (delta transfer functions): PDF-weighted "
+              "|M|^2 density per event, averaged over the 2 b-quark assignments",
     "w": "W->e nu LO, 4-dim integral (E_e, nu px, nu py, q^2_W), 1024 events x 2^20 "
          "evaluations/event, FP32 integrand + FP64 accumulation",
     "dy": "Drell-Yan Z/photon->mu mu, 2-dim integral, 64 events x 2^16 evaluations/event",
@@ -63,7 +69,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["w", "dy", "ttbar", "mix", "flow"], default="w")
+    ap.add_argument("--workload", choices=["w", "dy", "ttbar", "mix", "flow", "parton"],
+                    default="w")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the events-to-1%% leg")
     ap.add_argument("--events", type=int, default=None, help="override the event count")
     ap.add_argument("--points", type=int, default=None, help="override points per event")
@@ -220,6 +227,25 @@ def run_reference(args):
     w = workload(args)
     kind = w["proc"]
     from oracle import oracle as O
+    if args.workload == "parton":
+        vals = []
+        for step in range(args.warmup + args.steps):
+            b = cpu_baseline_parton(synth.WORKLOADS["parton"]["seed"] + step, n=4096)
+            if step >= args.warmup:
+                vals.append(b)
+        value = len(vals) * 4096 / sum(4096 / b["value"] for b in vals)
+        b = dict(vals[-1], value=value)
+        out = {"impl": "reference", "metric": "parton-level events per second", "value": value,
+               "unit": "events/s", "n_gpus": args.gpus, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": 4096 / value * 1e3,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic",
+               "config": {"workload": WORKLOAD_NAMES["parton"], "runs_on": "host CPU (FP64 oracle)"},
+               "cpu_baseline": b,
+               "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": 0}}
+        print(json.dumps(out), flush=True)
+        return
     if args.workload in ("mix", "flow"):
         value, cores, sample = reference_to_target(args, O)
         out = {"impl": "reference", "metric": "events integrated to 1% relative error per second",
@@ -705,6 +731,133 @@ def run_mix(args):
         torch.distributed.destroy_process_group()
 
 
+def run_parton(args):
+    """Parton-level weights (Sec. 4, Table "time_parton"): one step = one
+    mem_parton_weights call over the batch; value = events per second."""
+    import torch
+    from paper_1407_7595_gb300 import abi
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = workload(args)
+    n_ev = w["n_events"]
+    recs = synth.gen_ttbar_parton(n_ev, w["seed"] + shard(rank, n_ev)["seed_offset"])
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    proc = abi.mem_create_process(abi.process_desc(synth.PROC_TTBAR, synth.DEFAULT_PROCESS))
+    events = abi.mem_upload_events(proc, recs, sp)
+    dev = torch.device("cuda", local)
+    prob = torch.zeros(n_ev, dtype=torch.float64, device=dev)
+    st = torch.zeros(n_ev, dtype=torch.int32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step():
+        abi.mem_parton_weights(events, proc, prob, None, st, sp)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    step_ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        t0.record(stream)
+        step()
+        t1.record(stream)
+        t1.synchronize()
+        step_ms.append(t0.elapsed_time(t1))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    clocks = sampler.stop() if rank == 0 else None
+    ms_step = total_ms / args.steps
+    value = world * n_ev / (ms_step * 1e-3)
+    ok = bool(torch.all(st == 0).item())
+    # the paper's table size: 1e5 events in one call (launch-latency included)
+    n_tab = min(100_000, n_ev)
+    ev_tab = abi.mem_upload_events(proc, recs[:n_tab], sp)
+    tab_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(float(i))
+        t0.record(stream)
+        abi.mem_parton_weights(ev_tab, proc, prob[:n_tab], None, None, sp)
+        t1.record(stream)
+        t1.synchronize()
+        if i >= args.warmup:
+            tab_ms.append(t0.elapsed_time(t1))
+    abi.mem_destroy(ev_tab)
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.from_numpy(recs).pin_memory()
+        hp = torch.zeros(n_ev, dtype=torch.float64).pin_memory()
+        hs = torch.zeros(n_ev, dtype=torch.int32).pin_memory()
+        n_e2e = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(n_e2e):
+            ev2 = abi.mem_upload_events(proc, pinned, sp)
+            abi.mem_parton_weights(ev2, proc, hp.numpy(), None, hs.numpy(), sp)
+            abi.mem_destroy(ev2)
+        torch.cuda.synchronize()
+        dt = max_over_ranks((time.perf_counter() - t) / n_e2e, world, dev)
+        e2e = {"value": world * n_ev / dt, "unit": "events/s",
+               "h2d_bytes_per_step": int(recs.nbytes), "d2h_bytes_per_step": int(n_ev * (8 + 4)),
+               "ms_per_step": dt * 1e3}
+    if rank == 0:
+        props = torch.cuda.get_device_properties(local)
+        sms = props.multi_processor_count
+        max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+        peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+        fpe = FLOPS_PER_PARTON_EVENT
+        t_k = statistics.mean(step_ms) * 1e-3
+        achieved = fpe * n_ev / t_k / 1e12 if fpe else None
+        out = {"metric": "parton-level events per second", "value": value, "unit": "events/s",
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "ours",
+               "config": {"workload": WORKLOAD_NAMES["parton"], "events_per_gpu": n_ev,
+                          "l2": "flushed (256 MB write) between timed steps",
+                          "parallelism": f"{world} independent event shards"},
+               "ms_for_1e5_events": statistics.median(tab_ms),
+               "status_ok": ok,
+               "roofline": {"bound": "alu", "kernel": "k_parton_tt", "achieved": achieved,
+                            "peak": peak, "unit": "TFLOP/s",
+                            "frac": achieved / peak if achieved else None, "traffic": None,
+                            "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 "
+                                           f"lanes x 2 x {max_mhz:.0f} MHz max SM clock",
+                            "flops_per_event": fpe, "kernel_ms": t_k * 1e3},
+               "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps}
+        if not args.no_baseline:
+            out["cpu_baseline"] = cpu_baseline_parton(w["seed"])
+        print(json.dumps(out), flush=True)
+    abi.mem_destroy(events)
+    abi.mem_destroy(proc)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline_parton(seed, n=8192):
+    """The oracle's parton-level weights on n events, all host cores."""
+    from oracle import oracle as O
+    recs = synth.gen_ttbar_parton(n, seed)
+    P = O.process(synth.PROC_TTBAR, synth.DEFAULT_PROCESS)
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    O.parton_batch(P, recs, n_threads=cores)
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} parton-level events x 2 b-quark assignments, {dt:.1f} s"}
+
+
 def run_flow(args):
     """The learned-proposal A/B alone (ttbar): one JSON line whose value is the flow
     arm's events brought to 1 % per second; the VEGAS arm and the sweeps inside."""
@@ -738,6 +891,8 @@ def main():
         run_mix(args)
     elif args.workload == "flow":
         run_flow(args)
+    elif args.workload == "parton":
+        run_parton(args)
     else:
         run_ours(args)
 

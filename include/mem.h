@@ -182,6 +182,31 @@ mem_status mem_autotune(const mem_events* events, const mem_process* process,
                         const mem_tf_desc* tf, uint64_t seed, const mem_opts* opts,
                         mem_plan* best, double* events_per_s, int32_t* n_tried, void* stream);
 
+/* Parton-level weights of semileptonic ttbar events (Sec. 4, "parton level"):
+ * every final-state momentum is known, so every transfer function is a delta
+ * function and nothing is integrated. Each record (uploaded with
+ * mem_upload_events for the ttbar process) holds, as objects 0..5 with
+ * (E [GeV], eta, phi, kind): the l+ (kind 4 or 2), two b quarks (kind 5), the
+ * d and the ubar (kind 5) and the neutrino (kind 6); |eta| < 40.
+ * For each of the two assignments of the b quarks (0: object 1 is the b and
+ * object 2 the bbar; 1: the reverse) the weight is the density of Eq.
+ * "mem_def" at these momenta: the final state is boosted transversely to zero
+ * pT, which fixes x1 and x2 through its E + p_z and E - p_z; weight =
+ * sum_flavours f(x1) f(x2) |M|^2 / (|q1||q2|) x (2 pi)^4 (2/s) x
+ * prod_i 1/((2 pi)^3 2 E_i) over the six final-state particles (0 if x1 or x2
+ * reaches 1).
+ * Outputs (all host or all device memory, caller-owned): prob (n_events
+ * doubles) = the mean over the two assignments; w_assign (NULL or 2 n_events
+ * doubles, event-major) = the weight per assignment; ev_status (NULL or
+ * n_events int32) = MEM_OK, or MEM_ERR_INVALID_ARG for a record whose object
+ * kinds, energies or eta do not fit the layout above (its outputs are 0).
+ * Asynchronous on `stream` with device outputs; synchronous with host outputs.
+ * Errors: MEM_ERR_INVALID_ARG (NULL handle or prob, a process or events other
+ * than ttbar, outputs mixing host and device memory, device outputs not aligned
+ * to their element size), MEM_ERR_OOM, MEM_ERR_CUDA. */
+mem_status mem_parton_weights(const mem_events* events, const mem_process* process, double* prob,
+                              double* w_assign, int32_t* ev_status, void* stream);
+
 /* Working memory of mem_integrate_noalloc, fixed at build time (32 MiB per GPU). */
 #define MEM_NOALLOC_SCRATCH_BYTES (32u << 20)
 

@@ -94,6 +94,7 @@ SIGNATURES = [
                                        _vp, _vp]),
     ("mem_autotune", C.c_int, [_vp, _vp, C.POINTER(mem_tf_desc), C.c_uint64, C.POINTER(mem_opts),
                                C.POINTER(mem_plan), C.POINTER(C.c_double), C.POINTER(C.c_int32), _vp]),
+    ("mem_parton_weights", C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("mem_destroy", None, [_vp]),
     ("mem_last_error", C.c_char_p, []),
     ("mem_eval_points", C.c_int, [_vp, _vp, C.POINTER(mem_tf_desc), C.c_int64, C.c_int32,
@@ -237,6 +238,14 @@ def mem_autotune(events, proc, tf, seed, opts, stream=None):
     return best, rate.value, tried.value
 
 
+def mem_parton_weights(events, proc, prob, w_assign=None, ev_status=None, stream=None):
+    """Parton-level ttbar weights (delta transfer functions): prob (n_events float64)
+    and optionally the weight per b-quark assignment (n_events x 2 float64) and the
+    per-event status (int32); all host or all device tensors."""
+    _check(lib().mem_parton_weights(events, proc, _ptr(prob), _ptr(w_assign), _ptr(ev_status),
+                                    stream))
+
+
 def mem_integrate_noalloc(desc, tf, records, n_points, seed, event_id_base, prob, err,
                           ev_status=None, stream=None):
     """Allocation-free integration: records, prob, err, ev_status are device tensors."""
@@ -366,6 +375,15 @@ class Integrator:
         mem_integrate(self.events, self.proc, self.tf, n_points, seed, opts, prob, err, used, st,
                       stream)
         return {"prob": prob, "err": err, "n_used": used, "status": st}
+
+    def parton_weights(self, stream=None):
+        """Parton-level ttbar weights of the uploaded parton-level records:
+        (prob (n,), per-assignment weights (n, 2), status (n,))."""
+        prob = np.zeros(self.n)
+        w = np.zeros((self.n, 2))
+        st = np.zeros(self.n, dtype=np.int32)
+        mem_parton_weights(self.events, self.proc, prob, w, st, stream)
+        return prob, w, st
 
     def eval_points(self, event_index, perm, seed, point0, n, grid=None):
         w = np.zeros(n)

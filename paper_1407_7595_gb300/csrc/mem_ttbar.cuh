@@ -115,6 +115,79 @@ __device__ __forceinline__ LCv boost_lc(float E, float px, float py, float lab_p
   return o;
 }
 
+// Helicity-summed squared amplitudes of the Fierz-collapsed production and decay
+// chain from the transversely boosted l+, d, top and antitop light-cone momenta
+// (k1p = x1 sqrt(s), k2m = x2 sqrt(s), shat = k1p k2m, top mass m, m2 = m^2):
+// gg = g g -> t tbar with its colour matrix, qq = q qbar -> g* -> t tbar. The decay
+// factors (p_b.p_nu)(p_bbar.p_ubar), couplings, averages and the resonant
+// propagators are applied by the caller.
+struct TTAmp2 { float gg, qq; };
+
+__device__ __forceinline__ TTAmp2 tt_amp2(const LCv& l, const LCv& d, const LCv& tp,
+                                          const LCv& tm, float m, float m2, float k1p,
+                                          float k2m, float shat) {
+  // effective top row and antitop column (Fierz-collapsed decays)
+  cf la, lb, da, db;
+  weyl(l, la, lb);
+  weyl(d, da, db);
+  const cf w1 = lb, w2 = -la;                 // w = eps lambda(l)
+  const cf z1 = conjf(db), z2 = -conjf(da);   // z = eps conj(lambda(d))
+  Sp U;   // (m w, w^T (p_t.sigma)), p_t.sigma = [[p-, -conj(pT)], [-pT, p+]]
+  U.l1 = m * w1;
+  U.l2 = m * w2;
+  U.r1 = tp.pm * w1 - w2 * tp.pt;
+  U.r2 = tp.pp * w2 - w1 * conjf(tp.pt);
+  Sp Y;   // (-(p_tbar.sigma) z, m z)
+  Y.l1 = conjf(tm.pt) * z2 - tm.pm * z1;
+  Y.l2 = tm.pt * z1 - tm.pp * z2;
+  Y.r1 = m * z1;
+  Y.r2 = m * z2;
+  // t- and u-channel top momenta: p_t - k1 = k2 - p_tbar, p_t - k2 = k1 - p_tbar
+  LCv q1, q2;
+  q1.pp = -tm.pp;
+  q1.pm = tp.pm;
+  q1.pt = tp.pt;
+  q2.pp = tp.pp;
+  q2.pm = -tm.pm;
+  q2.pt = tp.pt;
+  const float ptt2 = norm2(tp.pt);
+  const float d1 = -(fmaf(tm.pp, tp.pm, ptt2) + m2);   // (p_t - k1)^2 - m^2 < 0
+  const float d2 = -(fmaf(tp.pp, tm.pm, ptt2) + m2);   // (p_t - k2)^2 - m^2 < 0
+  const float id1 = 1.f / d1, id2 = 1.f / d2;
+  // s-channel: U (k1/ - k2/) Y, k1 - k2 = (p+ = k1p, p- = -k2m, pT = 0)
+  LCv kk;
+  kk.pp = k1p;
+  kk.pm = -k2m;
+  kk.pt = C(0.f);
+  const cf Q = dot4(row_slash_m(U, kk, 0.f), Y);
+  const cf sq = (-1.f / shat) * Q;            // V/ = (e1.e2)(k1 - k2)/, e1.e2 = -delta
+  const Sp rx = row_ex(U), ry = row_ey(U);
+  const Sp tx = row_slash_m(rx, q1, m), ty = row_slash_m(ry, q1, m);
+  const Sp ux = row_slash_m(rx, q2, m), uy = row_slash_m(ry, q2, m);
+  const Sp ex = ex_col(Y), ey = ey_col(Y);
+  float gg = 0.f;
+#pragma unroll
+  for (int ab = 0; ab < 4; ++ab) {
+    const int ia = ab >> 1, ib = ab & 1;
+    const Sp& ta = ia ? ty : tx;
+    const Sp& ub = ib ? uy : ux;
+    const Sp& eb = ib ? ey : ex;
+    const Sp& ea = ia ? ey : ex;
+    cf A1 = id1 * dot4(ta, eb);   // U e1/ (q1/ + m) e2/ Y / d1
+    cf A2 = id2 * dot4(ub, ea);   // U e2/ (q2/ + m) e1/ Y / d2
+    if (ia == ib) {
+      A1 = A1 + sq;
+      A2 = A2 - sq;
+    }
+    gg += (16.f / 3.f) * (norm2(A1) + norm2(A2)) -
+          (4.f / 3.f) * fmaf(A1.re, A2.re, A1.im * A2.im);
+  }
+  TTAmp2 r;
+  r.gg = gg;
+  r.qq = (4.f / shat) * (norm2(dot4(rx, Y)) + norm2(dot4(ry, Y)));
+  return r;
+}
+
 struct JetC {
   float E, nx, ny, nz, sin_t, lcp, lcm;
   float lo, dw;             // window [lo, lo + dw] of the parton energy
@@ -347,68 +420,11 @@ struct PhysTT {
       const float x1 = k1p / P.sqrt_s, x2 = k2m / P.sqrt_s;
       if (!(x1 < 1.f && x2 < 1.f)) continue;
       const float shat = k1p * k2m;
-      // effective top row and antitop column (Fierz-collapsed decays)
-      cf la, lb, da, db;
-      weyl(l, la, lb);
-      weyl(d, da, db);
-      const cf w1 = lb, w2 = -la;                 // w = eps lambda(l)
-      const cf z1 = conjf(db), z2 = -conjf(da);   // z = eps conj(lambda(d))
-      Sp U;   // (m w, w^T (p_t.sigma)), p_t.sigma = [[p-, -conj(pT)], [-pT, p+]]
-      U.l1 = m * w1;
-      U.l2 = m * w2;
-      U.r1 = tp.pm * w1 - w2 * tp.pt;
-      U.r2 = tp.pp * w2 - w1 * conjf(tp.pt);
-      Sp Y;   // (-(p_tbar.sigma) z, m z)
-      Y.l1 = conjf(tm.pt) * z2 - tm.pm * z1;
-      Y.l2 = tm.pt * z1 - tm.pp * z2;
-      Y.r1 = m * z1;
-      Y.r2 = m * z2;
-      // t- and u-channel top momenta: p_t - k1 = k2 - p_tbar, p_t - k2 = k1 - p_tbar
-      LCv q1, q2;
-      q1.pp = -tm.pp;
-      q1.pm = tp.pm;
-      q1.pt = tp.pt;
-      q2.pp = tp.pp;
-      q2.pm = -tm.pm;
-      q2.pt = tp.pt;
-      const float ptt2 = norm2(tp.pt);
-      const float m2 = P.mt2;
-      const float d1 = -(fmaf(tm.pp, tp.pm, ptt2) + m2);   // (p_t - k1)^2 - m^2 < 0
-      const float d2 = -(fmaf(tp.pp, tm.pm, ptt2) + m2);   // (p_t - k2)^2 - m^2 < 0
-      const float id1 = 1.f / d1, id2 = 1.f / d2;
-      // s-channel: U (k1/ - k2/) Y, k1 - k2 = (p+ = k1p, p- = -k2m, pT = 0)
-      LCv kk;
-      kk.pp = k1p;
-      kk.pm = -k2m;
-      kk.pt = C(0.f);
-      const cf Q = dot4(row_slash_m(U, kk, 0.f), Y);
-      const cf sq = (-1.f / shat) * Q;            // V/ = (e1.e2)(k1 - k2)/, e1.e2 = -delta
-      const Sp rx = row_ex(U), ry = row_ey(U);
-      const Sp tx = row_slash_m(rx, q1, m), ty = row_slash_m(ry, q1, m);
-      const Sp ux = row_slash_m(rx, q2, m), uy = row_slash_m(ry, q2, m);
-      const Sp ex = ex_col(Y), ey = ey_col(Y);
-      float gg = 0.f;
-#pragma unroll
-      for (int ab = 0; ab < 4; ++ab) {
-        const int ia = ab >> 1, ib = ab & 1;
-        const Sp& ta = ia ? ty : tx;
-        const Sp& ub = ib ? uy : ux;
-        const Sp& eb = ib ? ey : ex;
-        const Sp& ea = ia ? ey : ex;
-        cf A1 = id1 * dot4(ta, eb);   // U e1/ (q1/ + m) e2/ Y / d1
-        cf A2 = id2 * dot4(ub, ea);   // U e2/ (q2/ + m) e1/ Y / d2
-        if (ia == ib) {
-          A1 = A1 + sq;
-          A2 = A2 - sq;
-        }
-        gg += (16.f / 3.f) * (norm2(A1) + norm2(A2)) -
-              (4.f / 3.f) * fmaf(A1.re, A2.re, A1.im * A2.im);
-      }
-      const float qqs = (4.f / shat) * (norm2(dot4(rx, Y)) + norm2(dot4(ry, Y)));
+      const TTAmp2 amp = tt_amp2(l, d, tp, tm, m, P.mt2, k1p, k2m, shat);
       const PdfX f1 = pdf_all(P, x1), f2 = pdf_all(P, x2);
       const float fg1 = f1.g, fg2 = f2.g, fq1 = f1.q, fq2 = f2.q, fqb1 = f1.qb, fqb2 = f2.qb;
-      const float init = fmaf(P.tt_gg * fg1 * fg2, gg,
-                              P.tt_qq * 2.f * fmaf(fq1, fqb2, fqb1 * fq2) * qqs);
+      const float init = fmaf(P.tt_gg * fg1 * fg2, amp.gg,
+                              P.tt_qq * 2.f * fmaf(fq1, fqb2, fqb1 * fq2) * amp.qq);
       const float gb = dgauss_g(c, jb.E, Eb);
       acc += init * (4.f / shat) * pbn * gb * bt.R / Kb;
     }

@@ -81,6 +81,8 @@ WORKLOADS = {
     "ttbar": dict(proc=PROC_TTBAR, n_events=4096, n_points=1 << 22, seed=SEED_BASE + 2),
     "mix": dict(proc=None, n_events=16384, n_points=1 << 24, seed=SEED_BASE + 3),
     "flow": dict(proc=PROC_TTBAR, n_events=4096, n_points=1 << 22, seed=SEED_BASE + 4),
+    # parton-level ttbar (Sec. 4): no integration, one weight per b-quark assignment
+    "parton": dict(proc=PROC_TTBAR, n_events=1 << 20, n_points=0, seed=SEED_BASE + 5),
 }
 
 
