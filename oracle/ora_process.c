@@ -28,6 +28,31 @@ double ora_pdf(const ora_process* P, int type, double x) {
   return P->pdf_A[type] * pow(x, P->pdf_a[type]) * pow(1.0 - x, P->pdf_b[type]);
 }
 
+/* Bilinear interpolation in (ln x, ln Q) between the four nodes around the
+ * point (Sec. 3 and its PDF listing: per-flavour (x, Q) grids evaluated by
+ * bilinear interpolation; here the nodes include both ends of each range, so
+ * the step is range/(N - 1)). Outside the table the edge cell's bilinear form
+ * continues linearly; a negative result is set to 0. f = 0 unless 0 < x < 1. */
+static double grid_pdf(const ora_process* P, int type, double x, double Q) {
+  if (!(x > 0.0 && x < 1.0)) return 0.0;
+  const int nx = P->grid_nx, nq = P->grid_nq;
+  const double hx = (P->grid_lx[1] - P->grid_lx[0]) / (nx - 1);
+  const double hq = (P->grid_lq[1] - P->grid_lq[0]) / (nq - 1);
+  const double tx = (log(x) - P->grid_lx[0]) / hx;
+  const double tq = (log(Q) - P->grid_lq[0]) / hq;
+  int i = tx < 0.0 ? 0 : tx > nx - 2 ? nx - 2 : (int)floor(tx);
+  int j = tq < 0.0 ? 0 : tq > nq - 2 ? nq - 2 : (int)floor(tq);
+  const double a = tx - i, b = tq - j;
+  const double* T = P->pdf_grid + (size_t)type * nq * nx;
+  const double f = (1.0 - a) * (1.0 - b) * T[j * nx + i] + a * (1.0 - b) * T[j * nx + i + 1] +
+                   (1.0 - a) * b * T[(j + 1) * nx + i] + a * b * T[(j + 1) * nx + i + 1];
+  return f > 0.0 ? f : 0.0;
+}
+
+double ora_pdf_q(const ora_process* P, int type, double x, double Q) {
+  return P->pdf_grid ? grid_pdf(P, type, x, Q) : ora_pdf(P, type, x);
+}
+
 static double gauss(double x, double mu, double sig) {
   double z = (x - mu) / sig;
   return exp(-0.5 * z * z) / (sqrt(2.0 * M_PI) * sig);
@@ -321,8 +346,9 @@ static void to_parton_frame(const ora_process* P, const state_t* S, rv4* boo, rv
 /* PDF-weighted, flavour- and orientation-summed |M|^2 (Eq. "mem_def"). */
 static double flavour_sum(const ora_process* P, const rv4* b, rv4 k1, rv4 k2, double x1,
                           double x2, const float* rec) {
-  double fq1 = ora_pdf(P, 0, x1), fqb1 = ora_pdf(P, 1, x1), fg1 = ora_pdf(P, 2, x1);
-  double fq2 = ora_pdf(P, 0, x2), fqb2 = ora_pdf(P, 1, x2), fg2 = ora_pdf(P, 2, x2);
+  double Q = sqrt(x1 * x2) * P->sqrt_s; /* factorisation scale: the partonic mass */
+  double fq1 = ora_pdf_q(P, 0, x1, Q), fqb1 = ora_pdf_q(P, 1, x1, Q), fg1 = ora_pdf_q(P, 2, x1, Q);
+  double fq2 = ora_pdf_q(P, 0, x2, Q), fqb2 = ora_pdf_q(P, 1, x2, Q), fg2 = ora_pdf_q(P, 2, x2, Q);
   double sum = 0.0;
   if (P->kind == 0) {
     for (int fl = 0; fl < 2; ++fl) {
@@ -374,6 +400,14 @@ double ora_integrand(const ora_process* P, const ora_tf* T, const float* rec, in
   double total = 0.0;
   for (int r = 0; r < n; ++r) total += state_weight(P, &st[r], rec, NULL);
   return total;
+}
+
+int ora_integrand_roots(const ora_process* P, const ora_tf* T, const float* rec, int perm,
+                        const double* x, double* w_root) {
+  state_t st[2];
+  int n = build_states(P, T, rec, perm, x, st);
+  for (int r = 0; r < n; ++r) w_root[r] = state_weight(P, &st[r], rec, NULL);
+  return n;
 }
 
 /* Parton-level ttbar weight (Sec. 4, parton level): every final-state momentum is

@@ -38,6 +38,15 @@ typedef struct {
   double mz, wz, mw, ww, mt, wt;
   double alpha, sw2, alpha_s;
   double pdf_A[3], pdf_a[3], pdf_b[3]; /* quark, antiquark, gluon */
+  /* Optional tabulated PDFs (Sec. 3: per-flavour grids in (x, Q), bilinear
+   * interpolation). NULL: the parametric f(x) = A x^a (1-x)^b above. Else
+   * pdf_grid[(t * grid_nq + j) * grid_nx + i] = f_t(x_i, Q_j) for t = quark,
+   * antiquark, gluon on the uniform nodes ln x_i = grid_lx[0] + i h_x,
+   * h_x = (grid_lx[1] - grid_lx[0]) / (grid_nx - 1), likewise ln Q_j; the
+   * factorisation scale is Q = sqrt(x1 x2 s). */
+  const double* pdf_grid;
+  int32_t grid_nx, grid_nq;
+  double grid_lx[2], grid_lq[2];
 } ora_process;
 
 typedef struct {
@@ -88,6 +97,10 @@ double ora_parton_ttbar(const ora_process* P, const float* rec, int bperm, doubl
 void ora_parton_batch(const ora_process* P, const float* recs, int64_t n, int n_threads,
                       double* prob_out, double* w_out);
 
+/* The integrand's contribution of each kinematic root (neutrino p_z solution) at
+ * point x; returns the number of roots (0..2). Their sum is ora_integrand. */
+int ora_integrand_roots(const ora_process* P, const ora_tf* T, const float* rec, int perm,
+                        const double* x, double* w_root);
 int ora_kinematics(const ora_process* P, const ora_tf* T, const float* rec, int perm,
                    const double* x, int root, double* fs, double* fs_lab, double* k12,
                    double* aux);
@@ -118,6 +131,9 @@ void ora_antitop_decay_probe(const ora_process* P, const double* pbb, const doub
 
 /* Parametric PDF f(x) = A x^a (1-x)^b, zero outside (0,1). type 0 q, 1 qbar, 2 g. */
 double ora_pdf(const ora_process* P, int type, double x);
+/* PDF of type t (0 quark, 1 antiquark, 2 gluon) at x and factorisation scale Q:
+ * the grid's bilinear interpolation if one is attached, else ora_pdf. */
+double ora_pdf_q(const ora_process* P, int type, double x, double Q);
 
 /* VEGAS */
 void ora_grid_uniform(int d, double* grid /* d x (NG+1) */);

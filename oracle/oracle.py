@@ -28,7 +28,9 @@ class OraProcess(C.Structure):
                 ("mz", C.c_double), ("wz", C.c_double), ("mw", C.c_double), ("ww", C.c_double),
                 ("mt", C.c_double), ("wt", C.c_double), ("alpha", C.c_double),
                 ("sw2", C.c_double), ("alpha_s", C.c_double), ("pdf_A", C.c_double * 3),
-                ("pdf_a", C.c_double * 3), ("pdf_b", C.c_double * 3)]
+                ("pdf_a", C.c_double * 3), ("pdf_b", C.c_double * 3),
+                ("pdf_grid", C.POINTER(C.c_double)), ("grid_nx", C.c_int32),
+                ("grid_nq", C.c_int32), ("grid_lx", C.c_double * 2), ("grid_lq", C.c_double * 2)]
 
 
 class OraTF(C.Structure):
@@ -90,6 +92,9 @@ def load():
     lib.ora_msq_dy.restype = C.c_double
     lib.ora_msq_w.argtypes = [P, C.c_int, _dp, _dp, _dp, _dp]
     lib.ora_msq_w.restype = C.c_double
+    lib.ora_integrand_roots.argtypes = [P, T, fp, C.c_int, _dp, _dp]
+    lib.ora_pdf_q.argtypes = [P, C.c_int, C.c_double, C.c_double]
+    lib.ora_pdf_q.restype = C.c_double
     lib.ora_parton_ttbar.argtypes = [P, fp, C.c_int, _dp]
     lib.ora_parton_ttbar.restype = C.c_double
     lib.ora_parton_batch.argtypes = [P, fp, C.c_int64, C.c_int, _dp, _dp]
@@ -124,13 +129,24 @@ def _d(a):
     return a, a.ctypes.data_as(_dp)
 
 
-def process(kind, params):
+def process(kind, params, pdf_grid=None):
+    """Process parameters; pdf_grid (optional) = dict(table=(3, nq, nx) array of
+    f(x_i, Q_j) for quark, antiquark, gluon, lx=(ln x_min, ln x_max),
+    lq=(ln Q_min, ln Q_max)) replaces the parametric PDFs."""
     p = OraProcess()
     p.kind = kind
     for k in ("sqrt_s", "mz", "wz", "mw", "ww", "mt", "wt", "alpha", "sw2", "alpha_s"):
         setattr(p, k, float(params[k]))
     for k in ("pdf_A", "pdf_a", "pdf_b"):
         getattr(p, k)[:] = [float(v) for v in params[k]]
+    if pdf_grid is not None:
+        t = np.ascontiguousarray(pdf_grid["table"], dtype=np.float64)
+        assert t.ndim == 3 and t.shape[0] == 3 and t.shape[1] >= 2 and t.shape[2] >= 2
+        p._table = t  # keeps the array alive with the structure
+        p.pdf_grid = t.ctypes.data_as(_dp)
+        p.grid_nq, p.grid_nx = t.shape[1], t.shape[2]
+        p.grid_lx[:] = [float(v) for v in pdf_grid["lx"]]
+        p.grid_lq[:] = [float(v) for v in pdf_grid["lq"]]
     return p
 
 
@@ -187,6 +203,19 @@ def kinematics(P, T, rec, perm, x, root):
                               k12.ctypes.data_as(_dp), aux.ctypes.data_as(_dp))
     return {"n": n, "fs": fs.reshape(6, 4), "lab": lab.reshape(6, 4), "k12": k12.reshape(2, 4),
             "aux": aux}
+
+
+def integrand_roots(P, T, rec, perm, x):
+    """Per-root contributions of the integrand at x (a list of 0-2 floats)."""
+    rec, rp = _rec_ptr(rec)
+    x, xp = _d(x)
+    w = np.zeros(2)
+    n = load().ora_integrand_roots(C.byref(P), C.byref(T), rp, perm, xp, w.ctypes.data_as(_dp))
+    return list(w[:n])
+
+
+def pdf_q(P, t, x, Q):
+    return load().ora_pdf_q(C.byref(P), t, x, Q)
 
 
 def parton_ttbar(P, rec, bperm):

@@ -257,6 +257,32 @@ def gen_ttbar(n, seed, tf=None):
     return out
 
 
+# ---------------------------------------------------------- tabulated PDFs
+def pdf_grid_table(params=None, n_x=512, n_q=64, x_min=1e-6, q_min=10.0, q_max=SQRT_S,
+                   q0=91.19, kappa=(0.5, 0.5, 0.5), lam=(0.0, 0.02, 0.04)):
+    """Synthetic stand-in for a tabulated PDF set (the LHAPDF/CTEQ grids of Sec. 3
+    are not available): f_t(x, Q) = A_t x^(a_t - lam_t L) (1 - x)^(b_t + kappa_t L),
+    L = ln(Q / q0), for t = quark, antiquark, gluon, with (A, a, b) of the
+    parametric set; at Q = q0 (or with kappa = lam = 0) it is that set. The
+    high-x fall-off steepens and the low-x sea and gluon rise with Q, as under
+    QCD evolution. Nodes: n_x uniform in ln x over [ln x_min, 0] and n_q uniform
+    in ln Q over [ln q_min, ln q_max]. Returns dict(table=(3, n_q, n_x) float32,
+    lx=(ln x_min, 0), lq=(ln q_min, ln q_max))."""
+    P = params or DEFAULT_PROCESS
+    lx = np.linspace(math.log(x_min), 0.0, n_x)
+    lq = np.linspace(math.log(q_min), math.log(q_max), n_q)
+    x = np.exp(lx)[None, :]
+    x[:, -1] = 1.0
+    L = (lq - math.log(q0))[:, None]
+    tab = np.zeros((3, n_q, n_x))
+    for t in range(3):
+        a = P["pdf_a"][t] - lam[t] * L
+        b = P["pdf_b"][t] + kappa[t] * L
+        tab[t] = P["pdf_A"][t] * x ** a * (1.0 - x) ** b
+    return {"table": tab.astype(np.float32), "lx": (float(lx[0]), 0.0),
+            "lq": (float(lq[0]), float(lq[-1]))}
+
+
 # ------------------------------------------------ parton-level ttbar (vectorised)
 def _bw_mass_v(rng, m, w, k, n):
     """n Breit-Wigner masses (Cauchy in m^2) truncated to m -+ k w."""
