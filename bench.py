@@ -52,6 +52,9 @@ FP32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 FP32 lanes
 # FMUL = 1, FFMA = 2), counted with ncu instruction counters and held fixed.
 FLOPS_PER_PARTON_EVENT = 2224.0
 
+PDF_NAME = {False: "parametric A x^a (1-x)^b",
+            True: "tabulated: synthetic 512 (ln x) x 64 (ln Q) table, bilinear, Q = sqrt(x1 x2 s)"}
+
 WORKLOAD_NAMES = {
     "parton": "parton-level semileptonic ttbar (delta transfer functions): PDF-weighted "
               "|M|^2 density per event, averaged over the 2 b-quark assignments",
@@ -72,6 +75,9 @@ def parse():
     ap.add_argument("--workload", choices=["w", "dy", "ttbar", "mix", "flow", "parton"],
                     default="w")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the events-to-1%% leg")
+    ap.add_argument("--pdf-grid", action="store_true",
+                    help="tabulated PDFs (synthetic 512 x 64 table, bilinear in ln x, ln Q) "
+                         "instead of the parametric set")
     ap.add_argument("--events", type=int, default=None, help="override the event count")
     ap.add_argument("--points", type=int, default=None, help="override points per event")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
@@ -303,6 +309,8 @@ def run_ours(args):
     sp = stream.cuda_stream
     tf = abi.tf_desc(synth.DEFAULT_TF[kind])
     proc = abi.mem_create_process(abi.process_desc(kind, synth.DEFAULT_PROCESS))
+    if args.pdf_grid:
+        abi.mem_process_set_pdf_grid(proc, synth.pdf_grid_table())
     events = abi.mem_upload_events(proc, recs, sp)
     dev = torch.device("cuda", local)
     prob = torch.zeros(n_ev, dtype=torch.float64, device=dev)
@@ -408,6 +416,7 @@ def run_ours(args):
                           "events_per_gpu": n_ev, "points_per_event": n_pts,
                           "adapt": "5 x %d points (excluded from the estimate)" % n_adapt,
                           "l2": "flushed (256 MB write) between timed steps",
+                          "pdf": PDF_NAME[args.pdf_grid],
                           "parallelism": f"{world} independent event shards"},
                "phases_ms": {"adapt": statistics.mean(adapt_ms), "main": statistics.mean(main_ms),
                              "step": statistics.mean(step_ms)},
@@ -747,6 +756,8 @@ def run_parton(args):
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
     proc = abi.mem_create_process(abi.process_desc(synth.PROC_TTBAR, synth.DEFAULT_PROCESS))
+    if args.pdf_grid:
+        abi.mem_process_set_pdf_grid(proc, synth.pdf_grid_table())
     events = abi.mem_upload_events(proc, recs, sp)
     dev = torch.device("cuda", local)
     prob = torch.zeros(n_ev, dtype=torch.float64, device=dev)
@@ -826,6 +837,7 @@ def run_parton(args):
                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "ours",
                "config": {"workload": WORKLOAD_NAMES["parton"], "events_per_gpu": n_ev,
                           "l2": "flushed (256 MB write) between timed steps",
+                          "pdf": PDF_NAME[args.pdf_grid],
                           "parallelism": f"{world} independent event shards"},
                "ms_for_1e5_events": statistics.median(tab_ms),
                "status_ok": ok,

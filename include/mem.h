@@ -125,6 +125,27 @@ int32_t mem_process_nperm(int32_t kind);
  * masses/widths/energy, reserved != 0). */
 mem_status mem_create_process(const mem_process_desc* desc, mem_process** out);
 
+/* Tabulated parton densities (Sec. 3: PDF values stored on (x, Q) grids per
+ * flavour and evaluated by bilinear interpolation) in place of the parametric
+ * set of the descriptor. `table` (host, caller-owned, copied): 3 x n_q x n_x
+ * float32, table[(t * n_q + j) * n_x + i] = f_t(x_i, Q_j) for t = quark,
+ * antiquark, gluon (the flavour classes of the parametric set), at the nodes
+ * ln x_i = lnx_min + i (lnx_max - lnx_min) / (n_x - 1) and
+ * ln Q_j = lnq_min + j (lnq_max - lnq_min) / (n_q - 1), Q in GeV. Every
+ * integrand of the process then takes f(x, Q) by bilinear interpolation in
+ * (ln x, ln Q) between the four nodes around the point, with the factorisation
+ * scale Q = sqrt(x1 x2 s) (the partonic invariant mass); outside the table the
+ * edge cell continues linearly, negative values become 0, and f = 0 unless
+ * 0 < x < 1. table = NULL restores the parametric set. Synchronous; affects
+ * calls made after it returns (mem_integrate_noalloc takes a descriptor and
+ * always uses the parametric set).
+ * Errors: MEM_ERR_INVALID_ARG (invalid handle; n_x or n_q < 2 or
+ * n_x n_q > 2^24; bounds not finite, not increasing, or lnx_max > 0; a
+ * value negative or not finite), MEM_ERR_OOM, MEM_ERR_CUDA. */
+mem_status mem_process_set_pdf_grid(mem_process* process, const float* table, int32_t n_x,
+                                    int32_t n_q, double lnx_min, double lnx_max,
+                                    double lnq_min, double lnq_max);
+
 /* Copy n_events event records (32 float32 each, layout in the package's
  * synth module docs: 6 x (E, eta, phi, kind), MET x, y, n_obj, kind, ...)
  * into library-owned device memory. `records` is host memory if

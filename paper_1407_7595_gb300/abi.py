@@ -95,6 +95,8 @@ SIGNATURES = [
     ("mem_autotune", C.c_int, [_vp, _vp, C.POINTER(mem_tf_desc), C.c_uint64, C.POINTER(mem_opts),
                                C.POINTER(mem_plan), C.POINTER(C.c_double), C.POINTER(C.c_int32), _vp]),
     ("mem_parton_weights", C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    ("mem_process_set_pdf_grid", C.c_int, [_vp, _vp, C.c_int32, C.c_int32, C.c_double,
+                                           C.c_double, C.c_double, C.c_double]),
     ("mem_destroy", None, [_vp]),
     ("mem_last_error", C.c_char_p, []),
     ("mem_eval_points", C.c_int, [_vp, _vp, C.POINTER(mem_tf_desc), C.c_int64, C.c_int32,
@@ -238,6 +240,19 @@ def mem_autotune(events, proc, tf, seed, opts, stream=None):
     return best, rate.value, tried.value
 
 
+def mem_process_set_pdf_grid(proc, grid):
+    """Attach tabulated PDFs: grid = dict(table=(3, n_q, n_x) float32,
+    lx=(ln x_min, ln x_max), lq=(ln Q_min, ln Q_max)); None restores the
+    parametric set."""
+    if grid is None:
+        _check(lib().mem_process_set_pdf_grid(proc, None, 0, 0, 0.0, 0.0, 0.0, 0.0))
+        return
+    t = np.ascontiguousarray(grid["table"], dtype=np.float32)
+    _check(lib().mem_process_set_pdf_grid(proc, t.ctypes.data, t.shape[2], t.shape[1],
+                                          grid["lx"][0], grid["lx"][1], grid["lq"][0],
+                                          grid["lq"][1]))
+
+
 def mem_parton_weights(events, proc, prob, w_assign=None, ev_status=None, stream=None):
     """Parton-level ttbar weights (delta transfer functions): prob (n_events float64)
     and optionally the weight per b-quark assignment (n_events x 2 float64) and the
@@ -360,10 +375,12 @@ def mem_vegas_refine(hist, grid_in, alpha=1.5):
 class Integrator:
     """Owns a process handle and uploaded events; integrate() returns numpy results."""
 
-    def __init__(self, kind, records, process_params, tf_params, stream=None):
+    def __init__(self, kind, records, process_params, tf_params, stream=None, pdf_grid=None):
         self.kind = kind
         self.tf = tf_desc(tf_params)
         self.proc = mem_create_process(process_desc(kind, process_params))
+        if pdf_grid is not None:
+            mem_process_set_pdf_grid(self.proc, pdf_grid)
         self.events = mem_upload_events(self.proc, records, stream)
         self.n = records.shape[0]
 

@@ -304,7 +304,55 @@ mem_status mem_create_process(const mem_process_desc* desc, mem_process** out) {
   p->magic = MAGIC_PROC;
   p->desc = *desc;
   p->pc = make_proc_const(*desc);
+  p->d_pdf_grid = nullptr;
   *out = p;
+  return MEM_OK;
+}
+
+mem_status mem_process_set_pdf_grid(mem_process* proc, const float* table, int32_t n_x,
+                                    int32_t n_q, double lnx_min, double lnx_max,
+                                    double lnq_min, double lnq_max) {
+  if (!proc || proc->magic != MAGIC_PROC) return fail(MEM_ERR_INVALID_ARG, "invalid process handle");
+  if (!table) {  // back to the parametric set
+    if (proc->d_pdf_grid) cudaFree(proc->d_pdf_grid);
+    proc->d_pdf_grid = nullptr;
+    proc->pc.pdf_grid = nullptr;
+    return MEM_OK;
+  }
+  if (n_x < 2 || n_q < 2 || (int64_t)n_x * n_q > ((int64_t)1 << 24))
+    return fail(MEM_ERR_INVALID_ARG, "PDF grid needs 2 <= n_x, n_q and n_x * n_q <= 2^24");
+  const double b[] = {lnx_min, lnx_max, lnq_min, lnq_max};
+  for (double v : b)
+    if (!std::isfinite(v)) return fail(MEM_ERR_INVALID_ARG, "PDF grid bounds must be finite");
+  if (!(lnx_min < lnx_max && lnx_max <= 0.0 && lnq_min < lnq_max))
+    return fail(MEM_ERR_INVALID_ARG, "PDF grid needs lnx_min < lnx_max <= 0 and lnq_min < lnq_max");
+  const size_t cells = (size_t)n_x * n_q;
+  std::vector<float4> packed(cells);
+  for (size_t k = 0; k < cells; ++k) {
+    const float q = table[k], qb = table[cells + k], g = table[2 * cells + k];
+    if (!(std::isfinite(q) && std::isfinite(qb) && std::isfinite(g) && q >= 0.f && qb >= 0.f &&
+          g >= 0.f))
+      return fail(MEM_ERR_INVALID_ARG, "PDF grid values must be finite and >= 0");
+    packed[k] = make_float4(q, qb, g, 0.f);
+  }
+  float4* d = nullptr;
+  MEM_CK(cudaMalloc(&d, cells * sizeof(float4)));
+  cudaError_t e = cudaMemcpy(d, packed.data(), cells * sizeof(float4), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return cuda_fail(e, "mem_process_set_pdf_grid");
+  }
+  if (proc->d_pdf_grid) cudaFree(proc->d_pdf_grid);
+  proc->d_pdf_grid = d;
+  ProcConst& P = proc->pc;
+  P.pdf_grid = d;
+  P.grid_nx = n_x;
+  P.grid_nq = n_q;
+  P.glx0 = (float)lnx_min;
+  P.g_inv_hx = (float)((n_x - 1) / (lnx_max - lnx_min));
+  P.glq0 = (float)lnq_min;
+  P.g_inv_hq = (float)((n_q - 1) / (lnq_max - lnq_min));
+  P.ln_rs = (float)std::log(proc->desc.sqrt_s);
   return MEM_OK;
 }
 
@@ -348,6 +396,7 @@ void mem_destroy(void* handle) {
   const uint32_t m = *reinterpret_cast<uint32_t*>(handle);
   if (m == MAGIC_PROC) {
     mem_process* p = reinterpret_cast<mem_process*>(handle);
+    if (p->d_pdf_grid) cudaFree(p->d_pdf_grid);
     p->magic = 0;
     delete p;
   } else if (m == MAGIC_EVT) {

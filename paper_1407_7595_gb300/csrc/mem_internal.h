@@ -17,6 +17,7 @@ struct mem_process {
   uint32_t magic;
   mem_process_desc desc;
   mem::ProcConst pc;
+  float4* d_pdf_grid;   // device copy of an attached PDF table (or nullptr)
 };
 
 struct mem_events {
@@ -111,6 +112,14 @@ struct BatchArgs;
 cudaError_t launch_batch_dy(const BatchArgs&, cudaStream_t);
 cudaError_t launch_batch_w(const BatchArgs&, cudaStream_t);
 cudaError_t launch_batch_tt(const BatchArgs&, cudaStream_t);
+// The same with tabulated PDFs (P.pdf_grid set): kernels built for that path
+// (mem_launch_grid.cu); the functions above forward to them.
+cudaError_t launch_integrate_dy_grid(const IntegrateArgs&, cudaStream_t);
+cudaError_t launch_integrate_w_grid(const IntegrateArgs&, cudaStream_t);
+cudaError_t launch_integrate_tt_grid(const IntegrateArgs&, cudaStream_t);
+cudaError_t launch_batch_dy_grid(const BatchArgs&, cudaStream_t);
+cudaError_t launch_batch_w_grid(const BatchArgs&, cudaStream_t);
+cudaError_t launch_batch_tt_grid(const BatchArgs&, cudaStream_t);
 
 cudaError_t launch_final(const Slot* slots, int64_t n_events, int nperm, uint32_t cpi,
                          uint32_t n_main, uint64_t n_per_item, double prefactor, double* prob,

@@ -1,0 +1,15 @@
+// Points per thread and launch bounds of each process's sampling kernels, chosen
+// by measurement on GB300 (shared by the parametric- and tabulated-PDF builds).
+#pragma once
+
+namespace mem {
+
+constexpr int PPT_DY = 16;
+constexpr int PPT_W = 32;
+constexpr int MINB_W = 5;        // adaptation and round kernels: 5 CTAs of 256 threads per SM (<= 51 registers)
+constexpr int MINB_W_MAIN = 6;   // frozen-grid kernel: 6 CTAs per SM (<= 42 registers, 4 bytes of spill)
+constexpr int PPT_TT = 8;
+constexpr int MINB_TT = 2;       // adaptation and round kernels: <= 128 registers, no spills
+constexpr int MINB_TT_MAIN = 3;  // frozen-grid kernel: <= 80 registers (20 bytes of spill), 24 warps/SM
+
+}  // namespace mem

@@ -108,7 +108,8 @@ __device__ void parton_weights2(const float4 (&o)[6], const ProcConst& P, float&
   const float x1 = k1p / P.sqrt_s, x2 = k2m / P.sqrt_s;
   if (!(x1 < 1.f && x2 < 1.f)) return;
   const float shat = k1p * k2m;
-  const PdfX f1 = pdf_all(P, x1), f2 = pdf_all(P, x2);
+  PdfX f1, f2;
+  pdf_pair(P, x1, x2, f1, f2);
   const float cgg = P.tt_gg * f1.g * f2.g;
   const float cqq = P.tt_qq * 2.f * fmaf(f1.q, f2.qb, f1.qb * f2.q);
   const float common = (4.f / shat) * props_w /

@@ -35,6 +35,13 @@ struct ProcConst {
   int pdf_amode[3];         // 1: x^-1/2, 2: x^-1, 0: general power
   int pdf_bint[3];          // integer exponent of (1-x) if >= 0, else general power
   int pdf_std;              // 1: (q, qbar, g) = x^-1/2 (1-x)^3, x^-1/2 (1-x)^5, x^-1 (1-x)^5
+  // tabulated PDFs (nullptr: the parametric set): (quark, antiquark, gluon, 0) at node
+  // (x_i, Q_j) in grid[j * grid_nx + i], nodes uniform in ln x and ln Q
+  const float4* pdf_grid;
+  int grid_nx, grid_nq;
+  float glx0, g_inv_hx;     // ln x of node 0, 1 / node step in ln x
+  float glq0, g_inv_hq;     // the same in ln Q
+  float ln_rs;              // ln sqrt(s): ln Q = (ln x1 + ln x2) / 2 + ln sqrt(s)
   double prefactor;         // FP64 constant multiplying every FP32 weight
 };
 
@@ -85,6 +92,62 @@ __device__ __forceinline__ PdfX pdf_all(const ProcConst& P, float x) {
     f.g = pdf(P, 2, x);
   }
   return f;
+}
+
+// Node index (clamped to the table's cells) and fractional position of t = (ln v -
+// ln v_0) / h; outside the table the edge cell continues linearly.
+__device__ __forceinline__ int grid_cell(float t, int n, float& frac) {
+  const float c = fminf(fmaxf(floorf(t), 0.f), (float)(n - 2));
+  frac = t - c;
+  return (int)c;
+}
+
+// Bilinear interpolation in (ln x, ln Q) of the three densities at x, in row j of
+// the Q nodes at fraction b (Sec. 3: per-flavour (x, Q) grids, bilinear
+// interpolation); 0 unless 0 < x < 1, negative values set to 0.
+__device__ __forceinline__ PdfX pdf_grid_at(const ProcConst& P, float x, float lx, int j,
+                                            float b) {
+  PdfX f;
+  if (!(x > 0.f && x < 1.f)) {
+    f.q = f.qb = f.g = 0.f;
+    return f;
+  }
+  float a;
+  const int i = grid_cell((lx - P.glx0) * P.g_inv_hx, P.grid_nx, a);
+  const float4* r0 = P.pdf_grid + (size_t)j * P.grid_nx + i;
+  const float4* r1 = r0 + P.grid_nx;
+  const float4 c00 = __ldg(r0), c01 = __ldg(r0 + 1), c10 = __ldg(r1), c11 = __ldg(r1 + 1);
+  auto bil = [a, b](float v00, float v01, float v10, float v11) {
+    const float lo = fmaf(a, v01 - v00, v00), hi = fmaf(a, v11 - v10, v10);
+    return fmaxf(fmaf(b, hi - lo, lo), 0.f);
+  };
+  f.q = bil(c00.x, c01.x, c10.x, c11.x);
+  f.qb = bil(c00.y, c01.y, c10.y, c11.y);
+  f.g = bil(c00.z, c01.z, c10.z, c11.z);
+  return f;
+}
+
+// How an integrand takes its parton densities: PDF_ANY decides per call from
+// P.pdf_grid; PDF_PARAM and PDF_GRID fix the choice at compile time, so that the
+// host can launch kernels register-allocated for one path (the hot sampling
+// kernels are built in both forms and chosen per launch).
+enum { PDF_ANY = 0, PDF_PARAM = 1, PDF_GRID = 2 };
+
+// The densities of both beams. Parametric: pdf_all at x1 and x2. Tabulated: at
+// the factorisation scale Q = sqrt(x1 x2 s), whose ln Q row is shared.
+template <int PDFM = PDF_ANY>
+__device__ __forceinline__ void pdf_pair(const ProcConst& P, float x1, float x2, PdfX& f1,
+                                         PdfX& f2) {
+  if (PDFM == PDF_GRID || (PDFM == PDF_ANY && P.pdf_grid)) {
+    const float l1 = logf(x1), l2 = logf(x2);
+    float b;
+    const int j = grid_cell((fmaf(0.5f, l1 + l2, P.ln_rs) - P.glq0) * P.g_inv_hq, P.grid_nq, b);
+    f1 = pdf_grid_at(P, x1, l1, j, b);
+    f2 = pdf_grid_at(P, x2, l2, j, b);
+  } else {
+    f1 = pdf_all(P, x1);
+    f2 = pdf_all(P, x2);
+  }
 }
 
 // Per-object constants, computed in FP64 from (E, eta, phi) once per item.
@@ -165,7 +228,8 @@ struct DYCache {
   int ok;
 };
 
-struct PhysDY {
+template <int PDFM>
+struct PhysDY_ {
   static constexpr int D = 2;
   static constexpr int NPERM = 1;
   using Cache = DYCache;
@@ -228,11 +292,14 @@ struct PhysDY {
                                                     P.dy_opp[2] * inv_den));
     const float mA = fmaf(u * u, S, t * t * O);  // quark from beam 1
     const float mB = fmaf(t * t, S, u * u * O);  // quark from beam 2: t <-> u
-    const PdfX f1 = pdf_all(P, b.x1), f2 = pdf_all(P, b.x2);
+    PdfX f1, f2;
+    pdf_pair<PDFM>(P, b.x1, b.x2, f1, f2);
     const float fl = f1.q * f2.qb * mA + f1.qb * f2.q * mB;
     return c.cst * E[0] * E[1] * __expf(-0.5f * z2) * (4.f * is) * fl * (1.f / 3.f);
   }
 };
+// Densities chosen per call (parity kernels); the hot kernels use PhysDY_<PDF_PARAM / PDF_GRID>.
+using PhysDY = PhysDY_<PDF_ANY>;
 
 // ---------------------------------------------------------------------------
 // W -> e nu: electron energy, neutrino px, py (MET box) and q^2_W (d = 4);
@@ -249,7 +316,8 @@ struct WCache {
   int ok;
 };
 
-struct PhysW {
+template <int PDFM>
+struct PhysW_ {
   static constexpr int D = 4;
   static constexpr int NPERM = 1;
   using Cache = WCache;
@@ -321,7 +389,8 @@ struct PhysW {
       light_cone(c.e, Ee, b, lm, lp);
       const float uA = b.x1 * P.sqrt_s * lm;  // -(k1 - p_e)^2
       const float uB = b.x2 * P.sqrt_s * lp;  // -(k2 - p_e)^2
-      const PdfX f1 = pdf_all(P, b.x1), f2 = pdf_all(P, b.x2);
+      PdfX f1, f2;
+      pdf_pair<PDFM>(P, b.x1, b.x2, f1, f2);
       const float fq1 = f1.q, fqb1 = f1.qb, fq2 = f2.q, fqb2 = f2.qb;
       // W+: (k_u . p_e+)^2 ; W-: (k_ubar . p_e-)^2
       acc += c.charge > 0 ? fmaf(fq1 * fqb2, uA * uA, fqb1 * fq2 * uB * uB)
@@ -331,5 +400,7 @@ struct PhysW {
     return c.cst * Ee * __expf(-0.5f * (z * z + zm2)) * (4.f / bw.q2) * (t * bw.R / sD) * acc;
   }
 };
+// Densities chosen per call (parity kernels); the hot kernels use PhysW_<PDF_PARAM / PDF_GRID>.
+using PhysW = PhysW_<PDF_ANY>;
 
 }  // namespace mem

@@ -226,7 +226,8 @@ __host__ __device__ inline void tt_perm_decode(int perm, int (&p)[4]) {
   }
 }
 
-struct PhysTT {
+template <int PDFM>
+struct PhysTT_ {
   static constexpr int D = 7;
   static constexpr int NPERM = 24;
   using Cache = TTCache;
@@ -421,7 +422,8 @@ struct PhysTT {
       if (!(x1 < 1.f && x2 < 1.f)) continue;
       const float shat = k1p * k2m;
       const TTAmp2 amp = tt_amp2(l, d, tp, tm, m, P.mt2, k1p, k2m, shat);
-      const PdfX f1 = pdf_all(P, x1), f2 = pdf_all(P, x2);
+      PdfX f1, f2;
+      pdf_pair<PDFM>(P, x1, x2, f1, f2);
       const float fg1 = f1.g, fg2 = f2.g, fq1 = f1.q, fq2 = f2.q, fqb1 = f1.qb, fqb2 = f2.qb;
       const float init = fmaf(P.tt_gg * fg1 * fg2, amp.gg,
                               P.tt_qq * 2.f * fmaf(fq1, fqb2, fqb1 * fq2) * amp.qq);
@@ -431,5 +433,8 @@ struct PhysTT {
     return common * pbbu * acc;
   }
 };
+// Densities chosen per call (parity and learned-sampler kernels); the hot kernels use
+// PhysTT_<PDF_PARAM / PDF_GRID>.
+using PhysTT = PhysTT_<PDF_ANY>;
 
 }  // namespace mem
