@@ -8,6 +8,16 @@
  * Event result: average over permutations (Sec. 4 averages over jet
  * assignments), errors added in quadrature. Points are counted over all
  * iterations. Sums use Neumaier's compensated summation.
+ *
+ * Stratified sampling (Sec. 4: the VEGAS integrator used "stratified sampling"
+ * together with its adaptive map; Lepage's vegas): with strat_points = k the
+ * frozen-grid phase divides the map's input cube (0,1)^d into M = n_s^d equal
+ * hypercubes, n_s the largest integer with k n_s^d <= the phase's budget, and
+ * places k points uniformly in each. The estimate is the mean over hypercubes of
+ * the per-cube means; its variance is the sum over hypercubes of the per-cube
+ * sample variance / k, divided by M^2. Point j of hypercube c has Philox index
+ * (phase start) + c k + j; the hypercube's coordinates are the base-n_s digits
+ * of c, dimension 0 the least significant.
  */
 #include <math.h>
 #include <pthread.h>
@@ -54,6 +64,7 @@ typedef struct {
   const ora_opts* opt;
   double* item_mean;
   double* item_var;
+  uint64_t* item_used;
   double* grid_out;
   int64_t next;
   pthread_mutex_t lock;
@@ -90,6 +101,40 @@ static void run_item(job_t* J, int64_t item) {
   }
   free(hist);
   uint64_t nm = n - idx;
+  const int k = J->opt->strat_points;
+  if (k >= 2) {
+    const uint64_t ns = ora_strat_side(nm, d, k);
+    uint64_t M = 1;
+    for (int j = 0; j < d; ++j) M *= ns;
+    nsum_t sm = {0, 0}, sv = {0, 0};
+    for (uint64_t c = 0; c < M; ++c) {
+      double cell[ORA_MAXD], wk[64];
+      uint64_t rest = c;
+      for (int j = 0; j < d; ++j) {
+        cell[j] = (double)(rest % ns);
+        rest /= ns;
+      }
+      double mean = 0.0;
+      for (int i = 0; i < k; ++i) {
+        double u[ORA_MAXD], y[ORA_MAXD], x[ORA_MAXD];
+        ora_point_u(J->seed, eid, perm, idx + c * (uint64_t)k + (uint64_t)i, d, u);
+        for (int j = 0; j < d; ++j) y[j] = (cell[j] + u[j]) / (double)ns;
+        double jac = ora_vegas_map(d, grid, y, x, NULL);
+        wk[i] = ora_integrand(P, J->T, rec, perm, x) * jac;
+        mean += wk[i];
+      }
+      mean /= k;
+      double ss = 0.0;
+      for (int i = 0; i < k; ++i) ss += (wk[i] - mean) * (wk[i] - mean);
+      nadd(&sm, mean);
+      nadd(&sv, ss / (double)(k - 1) / (double)k);
+    }
+    J->item_mean[item] = nval(&sm) / (double)M;
+    J->item_var[item] = nval(&sv) / ((double)M * (double)M);
+    J->item_used[item] = idx + (uint64_t)k * M;
+    if (J->grid_out) memcpy(J->grid_out + item * d * (ORA_NG + 1), grid, sizeof(double) * d * (ORA_NG + 1));
+    return;
+  }
   nsum_t s1 = {0, 0}, s2 = {0, 0};
   for (uint64_t k = 0; k < nm; ++k, ++idx) {
     double u[ORA_MAXD], x[ORA_MAXD];
@@ -104,6 +149,7 @@ static void run_item(job_t* J, int64_t item) {
   if (var < 0.0) var = 0.0;
   J->item_mean[item] = mean;
   J->item_var[item] = var;
+  J->item_used[item] = n;
   if (J->grid_out) memcpy(J->grid_out + item * d * (ORA_NG + 1), grid, sizeof(double) * d * (ORA_NG + 1));
 }
 
@@ -127,6 +173,10 @@ int ora_integrate(const ora_process* P, const ora_tf* T, const float* recs, int6
   int64_t n_items = n_events * np;
   uint64_t na = opt->adapt_points ? opt->adapt_points : (n_points / 8 < 16384 ? n_points / 8 : 16384);
   if (n_points < (uint64_t)opt->n_adapt_iters * na + 2) return 1;
+  if (opt->strat_points == 1 || opt->strat_points < 0 || opt->strat_points > 64) return 1;
+  if (opt->strat_points >= 2 &&
+      n_points - (uint64_t)opt->n_adapt_iters * na < (uint64_t)opt->strat_points)
+    return 1;
   job_t J;
   J.P = P;
   J.T = T;
@@ -137,6 +187,7 @@ int ora_integrate(const ora_process* P, const ora_tf* T, const float* recs, int6
   J.opt = opt;
   J.item_mean = (double*)malloc(sizeof(double) * n_items);
   J.item_var = (double*)malloc(sizeof(double) * n_items);
+  J.item_used = (uint64_t*)malloc(sizeof(uint64_t) * n_items);
   J.grid_out = grid_out;
   J.next = 0;
   pthread_mutex_init(&J.lock, NULL);
@@ -148,20 +199,33 @@ int ora_integrate(const ora_process* P, const ora_tf* T, const float* recs, int6
   pthread_mutex_destroy(&J.lock);
   for (int64_t e = 0; e < n_events; ++e) {
     nsum_t m = {0, 0}, v = {0, 0};
+    uint64_t used = 0;
     for (int p = 0; p < np; ++p) {
       nadd(&m, J.item_mean[e * np + p]);
       nadd(&v, J.item_var[e * np + p]);
+      used += J.item_used[e * np + p];
     }
     prob[e] = nval(&m) / np;
     err[e] = sqrt(nval(&v)) / np;
-    if (n_used) n_used[e] = n_points * (uint64_t)np;
+    if (n_used) n_used[e] = used;
   }
   if (item_mean) memcpy(item_mean, J.item_mean, sizeof(double) * n_items);
   if (item_err)
     for (int64_t i = 0; i < n_items; ++i) item_err[i] = sqrt(J.item_var[i]);
   free(J.item_mean);
   free(J.item_var);
+  free(J.item_used);
   return 0;
+}
+
+uint64_t ora_strat_side(uint64_t n, int d, int k) {
+  uint64_t s = 0;
+  for (;;) { /* increase while k (s+1)^d <= n */
+    uint64_t p = (uint64_t)k;
+    for (int j = 0; j < d && p <= n; ++j) p *= s + 1;
+    if (p > n) return s;
+    ++s;
+  }
 }
 
 /* Parton-level ttbar weights of n records on n_threads threads (static blocks of

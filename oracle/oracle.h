@@ -153,7 +153,14 @@ typedef struct {
   double alpha;            /* grid compression exponent */
   const double* grid_in;   /* optional starting grid shared by all items (d x (NG+1)) */
   uint64_t event_id_base;  /* id of event 0 in the Philox counter */
+  int32_t strat_points;    /* 0: plain sampling after adaptation; k >= 2: stratified
+                              sampling with k points in each of n_s^d hypercubes */
+  int32_t pad;
 } ora_opts;
+
+/* Hypercubes per dimension of the stratified phase: the largest n_s >= 1 with
+ * k n_s^d <= n (0 if n < k). */
+uint64_t ora_strat_side(uint64_t n, int d, int k);
 
 /* Integrate n_events records with n_points per item (item = event x perm).
  * prob/err per event; item_mean/item_err/grid_out optional (per item). */

@@ -42,7 +42,8 @@ class OraTF(C.Structure):
 class OraOpts(C.Structure):
     _fields_ = [("n_adapt_iters", C.c_int32), ("n_threads", C.c_int32),
                 ("adapt_points", C.c_uint64), ("alpha", C.c_double),
-                ("grid_in", C.POINTER(C.c_double)), ("event_id_base", C.c_uint64)]
+                ("grid_in", C.POINTER(C.c_double)), ("event_id_base", C.c_uint64),
+                ("strat_points", C.c_int32), ("pad", C.c_int32)]
 
 
 def _stale():
@@ -93,6 +94,8 @@ def load():
     lib.ora_msq_w.argtypes = [P, C.c_int, _dp, _dp, _dp, _dp]
     lib.ora_msq_w.restype = C.c_double
     lib.ora_integrand_roots.argtypes = [P, T, fp, C.c_int, _dp, _dp]
+    lib.ora_strat_side.argtypes = [C.c_uint64, C.c_int, C.c_int]
+    lib.ora_strat_side.restype = C.c_uint64
     lib.ora_pdf_q.argtypes = [P, C.c_int, C.c_double, C.c_double]
     lib.ora_pdf_q.restype = C.c_double
     lib.ora_parton_ttbar.argtypes = [P, fp, C.c_int, _dp]
@@ -312,9 +315,13 @@ def eval_points(P, T, rec, event_id, perm, seed, point0, n, grid=None):
     return w
 
 
+def strat_side(n, d, k):
+    return load().ora_strat_side(n, d, k)
+
+
 def integrate(P, T, recs, seed, n_points, n_adapt_iters=5, adapt_points=0, alpha=1.5,
               grid_in=None, event_id_base=0, n_threads=None, want_items=False,
-              want_grids=False):
+              want_grids=False, strat_points=0):
     recs = np.ascontiguousarray(recs, dtype=np.float32).reshape(-1, REC)
     n = recs.shape[0]
     npm = nperm(P.kind)
@@ -325,6 +332,7 @@ def integrate(P, T, recs, seed, n_points, n_adapt_iters=5, adapt_points=0, alpha
     o.adapt_points = adapt_points
     o.alpha = alpha
     o.event_id_base = event_id_base
+    o.strat_points = strat_points
     keep = None
     if grid_in is not None:
         keep, gp = _d(grid_in)
