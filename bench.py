@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--workload", choices=["w", "dy", "ttbar", "mix", "flow", "parton"],
                     default="w")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the events-to-1%% leg")
+    ap.add_argument("--strat", type=int, default=0,
+                    help="stratified frozen-grid sampling with this many points per hypercube")
     ap.add_argument("--pdf-grid", action="store_true",
                     help="tabulated PDFs (synthetic 512 x 64 table, bilinear in ln x, ln Q) "
                          "instead of the parametric set")
@@ -320,12 +322,20 @@ def run_ours(args):
     ph = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     for e in ph:
         e.record(stream)  # create the underlying CUDA events
-    opts = abi.make_opts(event_id_base=shard(rank, n_ev)["event_id_base"], phase_events=ph)
+    opts = abi.make_opts(event_id_base=shard(rank, n_ev)["event_id_base"], phase_events=ph,
+                         strat_points=args.strat)
     # the per-event budget is split equally over the jet permutations (items)
     n_perm = synth.NPERM[kind]
     n_item = -(-n_pts // n_perm)
     n_adapt = min(1 << 14, n_item // 8)
     n_main = n_item - 5 * n_adapt
+    if args.strat:   # points actually used: k n_s^d per item in the frozen-grid phase
+        d = synth.DIMS[kind]
+        ns = int((n_main / args.strat) ** (1.0 / d)) + 1
+        while args.strat * ns ** d > n_main:
+            ns -= 1
+        n_main = args.strat * ns ** d
+        n_item = 5 * n_adapt + n_main
     evals_per_step = n_ev * n_perm * n_item
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
@@ -377,7 +387,9 @@ def run_ours(args):
         t = time.perf_counter()
         for i in range(e2e_steps):
             ev2 = abi.mem_upload_events(proc, pinned, sp)
-            abi.mem_integrate(ev2, proc, tf, n_item, 500 + i, abi.make_opts(event_id_base=shard(rank, n_ev)["event_id_base"]),
+            abi.mem_integrate(ev2, proc, tf, n_item, 500 + i,
+                              abi.make_opts(event_id_base=shard(rank, n_ev)["event_id_base"],
+                                            strat_points=args.strat),
                               hp.numpy(), he.numpy(), hu.numpy(), hs.numpy(), sp)
             abi.mem_destroy(ev2)
         torch.cuda.synchronize()
@@ -417,6 +429,8 @@ def run_ours(args):
                           "adapt": "5 x %d points (excluded from the estimate)" % n_adapt,
                           "l2": "flushed (256 MB write) between timed steps",
                           "pdf": PDF_NAME[args.pdf_grid],
+                          "sampling": (f"stratified, {args.strat} points per hypercube"
+                                       if args.strat else "plain (VEGAS map only)"),
                           "parallelism": f"{world} independent event shards"},
                "phases_ms": {"adapt": statistics.mean(adapt_ms), "main": statistics.mean(main_ms),
                              "step": statistics.mean(step_ms)},

@@ -114,6 +114,17 @@ typedef struct {
                              var_flow * flow_cost <= var_vegas (0 = 1.0) */
   const mem_plan* plans;  /* mem_integrate_batch: optional HOST array, one schedule per
                              group (NULL = the fields above for every group) */
+  int32_t strat_points;   /* fixed-budget mem_integrate: 0 = plain sampling on the frozen
+                             grid; k in [2, 64] = stratified sampling (Sec. 4): the map's
+                             input cube is divided into n_s^d equal hypercubes, n_s the
+                             largest side with k n_s^d <= the frozen-grid budget, with k
+                             points in each (Philox index = phase start + c k + j for
+                             point j of hypercube c, whose coordinates are the base-n_s
+                             digits of c, dimension 0 least significant); estimate = mean
+                             of the per-cube means, variance = sum of the per-cube sample
+                             variances / k, over (n_s^d)^2. n_used then counts the points
+                             actually used. Must be 0 in the adaptive mode. */
+  int32_t reserved1;      /* must be 0 */
 } mem_opts;
 
 /* Number of integration dimensions / jet permutations of a process kind (-1 if invalid). */

@@ -57,7 +57,8 @@ class mem_opts(C.Structure):
                 ("flow_guided", C.c_int32), ("adapt_points", C.c_uint64), ("alpha", C.c_double),
                 ("grid_in", C.POINTER(C.c_double)), ("event_id_base", C.c_uint64),
                 ("phase_events", C.c_void_p), ("flow_screen", C.c_double),
-                ("flow_cost", C.c_double), ("plans", C.POINTER(mem_plan))]
+                ("flow_cost", C.c_double), ("plans", C.POINTER(mem_plan)),
+                ("strat_points", C.c_int32), ("reserved1", C.c_int32)]
 
 
 _lib = None
@@ -156,7 +157,7 @@ def tf_desc(params):
 
 def make_opts(n_adapt_iters=5, adapt_points=0, alpha=1.5, grid_in=None, event_id_base=0,
               target_rel_err=0.0, max_points=0, min_points=0, phase_events=None,
-              flow_screen=0.0, flow_cost=0.0, flow_guided=0, plans=None):
+              flow_screen=0.0, flow_cost=0.0, flow_guided=0, plans=None, strat_points=0):
     """phase_events: optional list of 4 torch.cuda.Event (created with
     enable_timing=True) recorded at the phase boundaries on the call's stream."""
     o = mem_opts()
@@ -174,6 +175,7 @@ def make_opts(n_adapt_iters=5, adapt_points=0, alpha=1.5, grid_in=None, event_id
     o.event_id_base = event_id_base
     o.flow_screen = flow_screen
     o.flow_cost = flow_cost
+    o.strat_points = strat_points
     plan_arr = None
     if plans is not None:
         plan_arr = (mem_plan * len(plans))(*plans)

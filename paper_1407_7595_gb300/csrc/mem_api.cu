@@ -46,6 +46,16 @@ bool is_device_ptr(const void* p) {
 
 namespace mem {
 
+uint32_t strat_side(uint64_t n, int d, int k) {
+  uint64_t s = 0;
+  for (;;) {  // increase while k (s+1)^d <= n
+    uint64_t p = (uint64_t)k;
+    for (int j = 0; j < d && p <= n; ++j) p *= s + 1;
+    if (p > n) return (uint32_t)s;
+    ++s;
+  }
+}
+
 int dims_of(int kind) { return kind == PROC_DY ? 2 : kind == PROC_W ? 4 : kind == PROC_TTBAR ? 7 : -1; }
 int nperm_of(int kind) { return kind == PROC_TTBAR ? 24 : (kind == PROC_DY || kind == PROC_W) ? 1 : -1; }
 uint32_t chunk_points(int kind) {
@@ -81,9 +91,11 @@ __device__ __forceinline__ void neu_add(double& s, double& c, double x) {
   s = t;
 }
 
+// n_cubes > 0: the slots hold stratified sums (per-cube means, per-cube variances
+// of the mean), the item estimate is their sum / n_cubes and its variance / n_cubes^2.
 __global__ void k_final(const Slot* __restrict__ slots, int64_t n_events, int nperm,
-                        uint32_t cpi, uint32_t n_main, uint64_t n_per_item, double prefactor,
-                        double* __restrict__ prob, double* __restrict__ err,
+                        uint32_t cpi, uint32_t n_main, uint64_t n_per_item, uint32_t n_cubes,
+                        double prefactor, double* __restrict__ prob, double* __restrict__ err,
                         uint64_t* __restrict__ n_used, int32_t* __restrict__ status) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_events) return;
@@ -103,8 +115,15 @@ __global__ void k_final(const Slot* __restrict__ slots, int64_t n_events, int np
       nbad += q.n_bad & 0x7fffffffu;
       invalid |= (q.n_bad >> 31) != 0;
     }
-    const double mean = (s1 + c1) / N;
-    double var = ((s2 + c2) / N - mean * mean) / (N - 1.0);
+    double mean, var;
+    if (n_cubes) {
+      const double M = (double)n_cubes;
+      mean = (s1 + c1) / M;
+      var = (s2 + c2) / (M * M);
+    } else {
+      mean = (s1 + c1) / N;
+      var = ((s2 + c2) / N - mean * mean) / (N - 1.0);
+    }
     var = var > 0.0 ? var : 0.0;
     neu_add(ms, mc, mean);
     neu_add(vs, vc, var);
@@ -116,11 +135,12 @@ __global__ void k_final(const Slot* __restrict__ slots, int64_t n_events, int np
 }
 
 cudaError_t launch_final(const Slot* slots, int64_t n_events, int nperm, uint32_t cpi,
-                         uint32_t n_main, uint64_t n_per_item, double prefactor, double* prob,
-                         double* err, uint64_t* n_used, int32_t* status, cudaStream_t st) {
+                         uint32_t n_main, uint64_t n_per_item, uint32_t n_cubes,
+                         double prefactor, double* prob, double* err, uint64_t* n_used,
+                         int32_t* status, cudaStream_t st) {
   const unsigned blocks = (unsigned)((n_events + 127) / 128);
-  k_final<<<blocks, 128, 0, st>>>(slots, n_events, nperm, cpi, n_main, n_per_item, prefactor,
-                                  prob, err, n_used, status);
+  k_final<<<blocks, 128, 0, st>>>(slots, n_events, nperm, cpi, n_main, n_per_item, n_cubes,
+                                  prefactor, prob, err, n_used, status);
   return cudaGetLastError();
 }
 
@@ -422,6 +442,12 @@ mem_status mem_integrate(const mem_events* ev, const mem_process* proc, const me
   int iters = opts ? opts->n_adapt_iters : 5;
   if (iters < 0 || iters > 64) return fail(MEM_ERR_INVALID_ARG, "n_adapt_iters out of range [0, 64]");
   if (opts && opts->flow_guided != 0) return fail(MEM_ERR_INVALID_ARG, "flow_guided must be 0");
+  if (opts && opts->reserved1 != 0) return fail(MEM_ERR_INVALID_ARG, "reserved1 must be 0");
+  const int strat_k = opts ? opts->strat_points : 0;
+  if (strat_k == 1 || strat_k < 0 || strat_k > 64)
+    return fail(MEM_ERR_INVALID_ARG, "strat_points must be 0 or in [2, 64]");
+  if (strat_k && opts->target_rel_err > 0.0)
+    return fail(MEM_ERR_INVALID_ARG, "stratified sampling needs the fixed-budget mode");
   if (opts && opts->target_rel_err > 0.0) {
     // adaptive budget: the batched schedule with this one event set
     const mem_events* evs[1] = {ev};
@@ -443,7 +469,21 @@ mem_status mem_integrate(const mem_events* ev, const mem_process* proc, const me
   const int64_t n_items = ev->n * np;
   const uint32_t n_main = (uint32_t)(n_points - (uint64_t)iters * na);
   const uint32_t cp = chunk_points(kind);
-  const uint32_t cpi = (n_main + cp - 1) / cp;
+  uint32_t cpi = (n_main + cp - 1) / cp;
+  uint32_t ns = 0, n_cubes = 0, cubes_pt = 0;
+  uint64_t n_per_item = n_points;
+  if (strat_k) {
+    ns = strat_side(n_main, d, strat_k);
+    if (ns == 0) return fail(MEM_ERR_INVALID_ARG, "stratified phase has fewer points than strat_points");
+    uint64_t m = 1;
+    for (int j = 0; j < d; ++j) m *= ns;
+    n_cubes = (uint32_t)m;
+    const uint32_t ppt = cp / THREADS;
+    cubes_pt = ppt / (uint32_t)strat_k > 0 ? ppt / (uint32_t)strat_k : 1;
+    const uint32_t cpc = cubes_pt * THREADS;
+    cpi = (n_cubes + cpc - 1) / cpc;
+    n_per_item = (uint64_t)iters * na + (uint64_t)strat_k * m;
+  }
 
   IntegrateArgs a;
   a.recs = ev->d_recs;
@@ -459,6 +499,10 @@ mem_status mem_integrate(const mem_events* ev, const mem_process* proc, const me
   a.idx0 = (uint32_t)((uint64_t)iters * na);
   a.n_main = n_main;
   a.chunks_per_item = cpi;
+  a.strat_k = (uint32_t)strat_k;
+  a.strat_ns = ns;
+  a.strat_cubes = n_cubes;
+  a.cubes_per_thread = cubes_pt;
   a.phase_events = opts ? reinterpret_cast<cudaEvent_t*>(opts->phase_events) : nullptr;
 
   const bool dev_out = is_device_ptr(prob);
@@ -502,8 +546,8 @@ mem_status mem_integrate(const mem_events* ev, const mem_process* proc, const me
   if (e == cudaSuccess) e = launch_integrate(kind, a, st);
   if (e == cudaSuccess && a.phase_events) e = cudaEventRecord(a.phase_events[2], st);
   if (e == cudaSuccess)
-    e = launch_final(a.slots, ev->n, np, cpi, n_main, n_points, proc->pc.prefactor, o_prob, o_err,
-                     o_used, o_st, st);
+    e = launch_final(a.slots, ev->n, np, cpi, n_main, n_per_item, n_cubes, proc->pc.prefactor,
+                     o_prob, o_err, o_used, o_st, st);
   if (e == cudaSuccess && a.phase_events) e = cudaEventRecord(a.phase_events[3], st);
   if (e == cudaSuccess && !dev_out) {
     e = cudaMemcpyAsync(prob, o_prob, ev->n * sizeof(double), cudaMemcpyDeviceToHost, st);

@@ -186,6 +186,8 @@ extern "C" mem_status mem_integrate_batch(int32_t n_groups, const mem_events* co
     return bfail(MEM_ERR_INVALID_ARG, "invalid argument");
   if (!(opts->target_rel_err > 0.0)) return bfail(MEM_ERR_INVALID_ARG, "target_rel_err must be > 0");
   if (opts->flow_guided != 0) return bfail(MEM_ERR_INVALID_ARG, "flow_guided must be 0");
+  if (opts->strat_points != 0 || opts->reserved1 != 0)
+    return bfail(MEM_ERR_INVALID_ARG, "strat_points must be 0 with adaptive budgets");
   const uint64_t cap_ev = opts->max_points ? opts->max_points : (uint64_t)1 << 24;
   const double alpha = opts->alpha > 0 ? opts->alpha : 1.5;
   if (opts->grid_in) return bfail(MEM_ERR_INVALID_ARG, "grid_in is not supported with adaptive budgets");

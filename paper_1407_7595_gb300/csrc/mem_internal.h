@@ -64,6 +64,10 @@ struct IntegrateArgs {
   uint32_t idx0;            // first point index of the frozen-grid phase
   uint32_t n_main;          // frozen-grid points per item
   uint32_t chunks_per_item;
+  uint32_t strat_k = 0;     // stratified frozen-grid phase: points per hypercube (0 = plain)
+  uint32_t strat_ns = 0;    // hypercubes per dimension
+  uint32_t strat_cubes = 0; // hypercubes per item (strat_ns^D)
+  uint32_t cubes_per_thread = 0;
   GridBin* grid32;          // device n_items x D x NG
   void* caches;             // device n_items x sizeof(Phys::Cache): per-item constants
   Slot* slots;              // device n_items x chunks_per_item
@@ -122,7 +126,11 @@ cudaError_t launch_batch_w_grid(const BatchArgs&, cudaStream_t);
 cudaError_t launch_batch_tt_grid(const BatchArgs&, cudaStream_t);
 
 cudaError_t launch_final(const Slot* slots, int64_t n_events, int nperm, uint32_t cpi,
-                         uint32_t n_main, uint64_t n_per_item, double prefactor, double* prob,
-                         double* err, uint64_t* n_used, int32_t* status, cudaStream_t st);
+                         uint32_t n_main, uint64_t n_per_item, uint32_t n_cubes,
+                         double prefactor, double* prob, double* err, uint64_t* n_used,
+                         int32_t* status, cudaStream_t st);
+// Hypercubes per dimension of the stratified phase: the largest s >= 1 with
+// k s^d <= n (0 if n < k).
+uint32_t strat_side(uint64_t n, int d, int k);
 
 }  // namespace mem

@@ -367,12 +367,115 @@ k_main(const float* __restrict__ recs, ProcConst P, TFConst T, int64_t n_items,
   }
 }
 
+// Stratified frozen-grid sampling (Sec. 4: the VEGAS integrator's stratified
+// sampling): the map's input cube is divided into M = ns^D equal hypercubes with
+// k points each; hypercube c has the base-ns digits of c as coordinates
+// (dimension 0 least significant) and its points the Philox indices
+// idx0 + c k + i. Thread t of CTA (item, chunk) takes hypercubes
+// chunk CPC + j THREADS + t, j < cubes_per_thread (CPC = THREADS cubes_per_thread),
+// and accumulates the per-cube mean into a1 and the per-cube sample variance / k
+// into a2 (Welford within the hypercube); non-finite weights count as 0 and are
+// reported.
+template <class PH, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
+k_main_strat(const float* __restrict__ recs, ProcConst P, TFConst T, int64_t n_items,
+             uint32_t chunks_per_item, const __grid_constant__ PhiloxKey key,
+             uint64_t event_id_base, uint32_t idx0, uint32_t ns, uint32_t n_cubes, uint32_t k,
+             uint32_t cubes_per_thread, const GridBin* __restrict__ grid32,
+             const typename PH::Cache* __restrict__ caches, Slot* __restrict__ slots) {
+  constexpr int D = PH::D;
+  __shared__ MainSmem<PH> S;
+  const int64_t item = blockIdx.x / chunks_per_item;
+  const uint32_t chunk = blockIdx.x % chunks_per_item;
+  if (item >= n_items) return;
+  const int64_t ev = item / PH::NPERM;
+  const int perm = (int)(item % PH::NPERM);
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(caches + item);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&S.cache);
+    for (int t = threadIdx.x; t < (int)(sizeof(typename PH::Cache) / 4); t += blockDim.x)
+      dst[t] = src[t];
+  }
+  const GridBin* gsrc = grid32 + item * (D * NG);
+  for (int t = threadIdx.x; t < D * NG; t += blockDim.x) S.gb[t] = gsrc[t];
+  __syncthreads();
+  const uint32_t eid = (uint32_t)(event_id_base + (uint64_t)ev);
+  Kahan32 a1, a2;
+  uint32_t nbad = 0;
+  if (S.cache.ok) {
+    const float inv_ns = 1.f / (float)ns;
+    const float below_one = 0x1.fffffep-1f;
+    const uint32_t cube0 = chunk * (THREADS * cubes_per_thread);
+    const float inv_kk = 1.f / ((float)(k - 1) * (float)k);
+#pragma unroll 1
+    for (uint32_t j = 0; j < cubes_per_thread; ++j) {
+      const uint32_t c = cube0 + j * THREADS + threadIdx.x;
+      if (c >= n_cubes) break;
+      float cell[D];
+      uint32_t r = c;
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        const uint32_t t = r / ns;
+        cell[q] = (float)(r - t * ns);
+        r = t;
+      }
+      float mean = 0.f, m2 = 0.f;
+#pragma unroll 1
+      for (uint32_t i = 0; i < k; ++i) {
+        float u[D], x[D], xc[D];
+        int bin[D];
+        point_uniforms<D>(key, eid, (uint32_t)perm, idx0 + c * k + i, u);
+#pragma unroll
+        for (int q = 0; q < D; ++q) u[q] = fminf((cell[q] + u[q]) * inv_ns, below_one);
+        const float J = vegas_map<D>(S.gb, u, x, xc, bin);
+        float w = PH::eval(S.cache, P, x, xc) * J;
+        if (!isfinite(w)) {
+          ++nbad;
+          w = 0.f;
+        }
+        const float delta = w - mean;
+        mean += delta / (float)(i + 1);
+        m2 = fmaf(delta, w - mean, m2);
+      }
+      a1.add(mean);
+      a2.add(m2 * inv_kk);
+    }
+  }
+  const DD v1 = warp_reduce_kahan(a1), v2 = warp_reduce_kahan(a2);
+  for (int o = 16; o > 0; o >>= 1) nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    S.red[0][warp] = v1;
+    S.red[1][warp] = v2;
+    S.bad[warp] = nbad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    DD s1 = S.red[0][0], s2 = S.red[1][0];
+    uint32_t b = S.bad[0];
+    for (int w = 1; w < WARPS; ++w) {
+      s1 = two_sum_merge(s1, S.red[0][w]);
+      s2 = two_sum_merge(s2, S.red[1][w]);
+      b += S.bad[w];
+    }
+    Slot sl;
+    sl.s1 = s1.hi;
+    sl.c1 = s1.lo;
+    sl.s2 = s2.hi;
+    sl.c2 = s2.lo;
+    sl.n_bad = b | (S.cache.ok ? 0u : 0x80000000u);
+    sl.pad = 0;
+    slots[blockIdx.x] = sl;
+  }
+}
+
 // Per event: fixed-order FP64 reduction of the item slots, MC mean and error
 // per item, average over permutations, FP64 prefactor.
 __global__ void k_final(const Slot* __restrict__ slots, int64_t n_events, int nperm,
                         uint32_t chunks_per_item, uint32_t n_main, uint64_t n_per_item,
-                        double prefactor, double* __restrict__ prob, double* __restrict__ err,
-                        uint64_t* __restrict__ n_used, int32_t* __restrict__ status);
+                        uint32_t n_cubes, double prefactor, double* __restrict__ prob,
+                        double* __restrict__ err, uint64_t* __restrict__ n_used,
+                        int32_t* __restrict__ status);
 
 // Integrand at consecutive points of one item (parity tests): one thread per point.
 template <class PH>

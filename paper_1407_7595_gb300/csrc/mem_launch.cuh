@@ -27,6 +27,13 @@ cudaError_t run_integrate(const IntegrateArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   if (a.phase_events) cudaEventRecord(a.phase_events[1], st);
   const uint64_t blocks = (uint64_t)a.n_items * a.chunks_per_item;
+  if (a.strat_k) {
+    k_main_strat<PH, MINB_MAIN><<<(unsigned)blocks, THREADS, 0, st>>>(
+        a.recs, a.P, a.T, a.n_items, a.chunks_per_item, philox_key(a.seed), a.event_id_base,
+        a.idx0, a.strat_ns, a.strat_cubes, a.strat_k, a.cubes_per_thread, a.grid32,
+        reinterpret_cast<const typename PH::Cache*>(a.caches), a.slots);
+    return cudaGetLastError();
+  }
   k_main<PH, PPT, MINB_MAIN><<<(unsigned)blocks, THREADS, 0, st>>>(
       a.recs, a.P, a.T, a.n_items, a.chunks_per_item, philox_key(a.seed), a.event_id_base, a.idx0, a.n_main,
       a.grid32, reinterpret_cast<const typename PH::Cache*>(a.caches), a.slots);

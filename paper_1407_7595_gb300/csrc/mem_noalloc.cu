@@ -143,7 +143,7 @@ extern "C" mem_status mem_integrate_noalloc(const mem_process_desc* desc, const 
   cudaStream_t st = (cudaStream_t)stream;
   e = launch_integrate(kind, a, st);
   if (e == cudaSuccess)
-    e = launch_final(a.slots, n_events, np, cpi, n_main, n_points, a.P.prefactor, prob, err,
+    e = launch_final(a.slots, n_events, np, cpi, n_main, n_points, 0, a.P.prefactor, prob, err,
                      nullptr, ev_status, st);
   if (e != cudaSuccess) return cuda_bad(e, "mem_integrate_noalloc");
   return MEM_OK;
