@@ -271,3 +271,19 @@ void ora_parton_batch(const ora_process* P, const float* recs, int64_t n, int n_
   free(th);
   free(jobs);
 }
+
+/* Event discriminant (Sec. 3, the equation after the PDF paragraph): D = log10 of the
+ * ratio of the signal and background probability densities, with the error of
+ * independent estimates propagated to first order:
+ *   sigma_D = sqrt((sigma_S / p_S)^2 + (sigma_B / p_B)^2) / ln(10).
+ * Returns 0, or 1 (D and its error set to NaN) unless both densities are > 0. */
+int ora_discriminant(double p_s, double e_s, double p_b, double e_b, double* D, double* err) {
+  if (!(p_s > 0.0 && p_b > 0.0)) {
+    *D = NAN;
+    *err = NAN;
+    return 1;
+  }
+  *D = log10(p_s / p_b);
+  *err = sqrt((e_s / p_s) * (e_s / p_s) + (e_b / p_b) * (e_b / p_b)) / log(10.0);
+  return 0;
+}

@@ -158,6 +158,10 @@ typedef struct {
   int32_t pad;
 } ora_opts;
 
+/* Event discriminant D = log10(p_S / p_B) and its first-order error from the
+ * errors of the two estimates; returns 1 (NaN outputs) unless both p > 0. */
+int ora_discriminant(double p_s, double e_s, double p_b, double e_b, double* D, double* err);
+
 /* Hypercubes per dimension of the stratified phase: the largest n_s >= 1 with
  * k n_s^d <= n (0 if n < k). */
 uint64_t ora_strat_side(uint64_t n, int d, int k);

@@ -94,6 +94,7 @@ def load():
     lib.ora_msq_w.argtypes = [P, C.c_int, _dp, _dp, _dp, _dp]
     lib.ora_msq_w.restype = C.c_double
     lib.ora_integrand_roots.argtypes = [P, T, fp, C.c_int, _dp, _dp]
+    lib.ora_discriminant.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, _dp, _dp]
     lib.ora_strat_side.argtypes = [C.c_uint64, C.c_int, C.c_int]
     lib.ora_strat_side.restype = C.c_uint64
     lib.ora_pdf_q.argtypes = [P, C.c_int, C.c_double, C.c_double]
@@ -313,6 +314,13 @@ def eval_points(P, T, rec, event_id, perm, seed, point0, n, grid=None):
     load().ora_eval_points(C.byref(P), C.byref(T), rp, event_id, perm, seed, point0, n, gp,
                            w.ctypes.data_as(_dp))
     return w
+
+
+def discriminant(p_s, e_s, p_b, e_b):
+    """(D, sigma_D, status) of one event."""
+    D, e = C.c_double(), C.c_double()
+    rc = load().ora_discriminant(p_s, e_s, p_b, e_b, C.byref(D), C.byref(e))
+    return D.value, e.value, rc
 
 
 def strat_side(n, d, k):
