@@ -239,6 +239,20 @@ mem_status mem_autotune(const mem_events* events, const mem_process* process,
 mem_status mem_parton_weights(const mem_events* events, const mem_process* process, double* prob,
                               double* w_assign, int32_t* ev_status, void* stream);
 
+/* Event discriminant (Sec. 3): D = log10(p_S / p_B) for each of n events, from
+ * the probability densities of the same events under a signal and a background
+ * hypothesis (e.g. two mem_integrate results), with the first-order error of
+ * independent estimates sigma_D = sqrt((err_S/p_S)^2 + (err_B/p_B)^2) / ln 10.
+ * Inputs prob_s, err_s, prob_b, err_b and outputs D, err_D (optional),
+ * status (optional: MEM_OK, or MEM_ERR_INVALID_ARG where a density is not
+ * > 0, with NaN outputs): n doubles (int32 for status) each, all host or all
+ * device memory. Asynchronous on `stream` with device arrays.
+ * Errors: MEM_ERR_INVALID_ARG (n < 1, NULL inputs or D, mixed memory kinds),
+ * MEM_ERR_OOM, MEM_ERR_CUDA. */
+mem_status mem_discriminant(int64_t n, const double* prob_s, const double* err_s,
+                            const double* prob_b, const double* err_b, double* D, double* err_D,
+                            int32_t* status, void* stream);
+
 /* Working memory of mem_integrate_noalloc, fixed at build time (32 MiB per GPU). */
 #define MEM_NOALLOC_SCRATCH_BYTES (32u << 20)
 

@@ -98,6 +98,7 @@ SIGNATURES = [
     ("mem_parton_weights", C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("mem_process_set_pdf_grid", C.c_int, [_vp, _vp, C.c_int32, C.c_int32, C.c_double,
                                            C.c_double, C.c_double, C.c_double]),
+    ("mem_discriminant", C.c_int, [C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("mem_destroy", None, [_vp]),
     ("mem_last_error", C.c_char_p, []),
     ("mem_eval_points", C.c_int, [_vp, _vp, C.POINTER(mem_tf_desc), C.c_int64, C.c_int32,
@@ -261,6 +262,12 @@ def mem_parton_weights(events, proc, prob, w_assign=None, ev_status=None, stream
     per-event status (int32); all host or all device tensors."""
     _check(lib().mem_parton_weights(events, proc, _ptr(prob), _ptr(w_assign), _ptr(ev_status),
                                     stream))
+
+
+def mem_discriminant(prob_s, err_s, prob_b, err_b, D, err_D=None, status=None, stream=None):
+    """D = log10(p_S / p_B) and its error per event; arrays all host or all device."""
+    _check(lib().mem_discriminant(len(D), _ptr(prob_s), _ptr(err_s), _ptr(prob_b), _ptr(err_b),
+                                  _ptr(D), _ptr(err_D), _ptr(status), stream))
 
 
 def mem_integrate_noalloc(desc, tf, records, n_points, seed, event_id_base, prob, err,

@@ -1,6 +1,7 @@
 // C ABI of libmem.so (declared in include/mem.h): validation, process
 // constants, device memory, launches and result transfer.
 #include <cuda_runtime.h>
+#include <math_constants.h>
 
 #include <cmath>
 #include <cstdio>
@@ -142,6 +143,21 @@ cudaError_t launch_final(const Slot* slots, int64_t n_events, int nperm, uint32_
   k_final<<<blocks, 128, 0, st>>>(slots, n_events, nperm, cpi, n_main, n_per_item, n_cubes,
                                   prefactor, prob, err, n_used, status);
   return cudaGetLastError();
+}
+
+// D = log10(p_S / p_B), sigma_D = sqrt((e_S/p_S)^2 + (e_B/p_B)^2) / ln 10 per event.
+__global__ void k_discriminant(int64_t n, const double* __restrict__ ps, const double* __restrict__ es,
+                               const double* __restrict__ pb, const double* __restrict__ eb,
+                               double* __restrict__ D, double* __restrict__ eD,
+                               int32_t* __restrict__ status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double a = ps[i], b = pb[i];
+  const bool ok = a > 0.0 && b > 0.0;
+  const double ra = es[i] / a, rb = eb[i] / b;
+  D[i] = ok ? log10(a / b) : CUDART_NAN;
+  if (eD) eD[i] = ok ? sqrt(ra * ra + rb * rb) / 2.302585092994045684 : CUDART_NAN;
+  if (status) status[i] = ok ? MEM_OK : MEM_ERR_INVALID_ARG;
 }
 
 __global__ void k_philox(const __grid_constant__ PhiloxKey key, uint32_t eid, uint32_t perm,
@@ -602,6 +618,51 @@ mem_status mem_eval_points(const mem_events* ev, const mem_process* proc, const 
   if (e == cudaSuccess) e = e2;
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "mem_eval_points");
+  return MEM_OK;
+}
+
+mem_status mem_discriminant(int64_t n, const double* prob_s, const double* err_s,
+                            const double* prob_b, const double* err_b, double* D, double* err_D,
+                            int32_t* status, void* stream) {
+  if (n < 1 || !prob_s || !err_s || !prob_b || !err_b || !D)
+    return fail(MEM_ERR_INVALID_ARG, "invalid argument");
+  const bool dev = is_device_ptr(D);
+  const void* all[] = {prob_s, err_s, prob_b, err_b, err_D, status};
+  for (const void* p : all)
+    if (p && is_device_ptr(p) != dev)
+      return fail(MEM_ERR_INVALID_ARG, "arrays must all be host or all be device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t b8 = (size_t)n * sizeof(double), b4 = (size_t)n * sizeof(int32_t);
+  const double *ps = prob_s, *es = err_s, *pb = prob_b, *eb = err_b;
+  double *o = D, *oe = err_D;
+  int32_t* os = status;
+  unsigned char* ws = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!dev) {
+    MEM_CK(cudaMallocAsync((void**)&ws, 6 * ((b8 + 255) & ~(size_t)255) + b4, st));
+    auto part = [&](int k) { return reinterpret_cast<double*>(ws + k * ((b8 + 255) & ~(size_t)255)); };
+    double* in[4] = {part(0), part(1), part(2), part(3)};
+    const double* src[4] = {prob_s, err_s, prob_b, err_b};
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+      e = cudaMemcpyAsync(in[k], src[k], b8, cudaMemcpyHostToDevice, st);
+    ps = in[0], es = in[1], pb = in[2], eb = in[3];
+    o = part(4);
+    oe = err_D ? part(5) : nullptr;
+    os = status ? reinterpret_cast<int32_t*>(ws + 6 * ((b8 + 255) & ~(size_t)255)) : nullptr;
+  }
+  if (e == cudaSuccess) {
+    k_discriminant<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, ps, es, pb, eb, o, oe, os);
+    e = cudaGetLastError();
+  }
+  if (!dev) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(D, o, b8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && err_D) e = cudaMemcpyAsync(err_D, oe, b8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && status) e = cudaMemcpyAsync(status, os, b4, cudaMemcpyDeviceToHost, st);
+    cudaError_t e2 = cudaFreeAsync(ws, st);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "mem_discriminant");
   return MEM_OK;
 }
 
