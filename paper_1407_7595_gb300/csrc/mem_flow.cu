@@ -33,6 +33,12 @@ __global__ void k_flow_bf16(const FlowW* __restrict__ W, FlowB* __restrict__ B) 
     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
     const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
     B->W1t[k][o][i] = q <= 1 ? hi : (q == 2 ? lo : __float2bfloat16_rn(0.f));
+    if (i < 16) B->W1u[k][umma_kmajor(o, i, 16)] = B->W1t[k][o][i];
+  }
+  // the output layer as the tcgen05 operand (N 16: outputs 8-15 zero)
+  for (int t = threadIdx.x; t < 16 * FH; t += blockDim.x) {
+    const int n = t / FH, i = t % FH;
+    B->W3u[k][umma_kmajor(n, i, FH)] = __float2bfloat16_rn(n < 8 ? W->W3[k][i][n] : 0.f);
   }
   // the hidden layer as the tcgen05 operand, bias folded into k 128 (high) and 129 (low)
   for (int t = threadIdx.x; t < FH * FKH; t += blockDim.x) {

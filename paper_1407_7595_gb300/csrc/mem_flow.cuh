@@ -15,6 +15,7 @@
 // kernels evaluate the first layer (K = |A| <= 4) in FP32; inference runs it as a
 // K = 16 product of a two-part BF16 split of z_A and of W1a (~16 bits kept).
 #pragma once
+#include "mem_fastmath.cuh"
 #include <cuda_bf16.h>
 
 #include "mem_common.cuh"
@@ -54,11 +55,16 @@ struct FlowW {
 // swizzle; see umma_kmajor) with its bias folded in: k 0-127 = W2[k][n],
 // k 128 = b2 high part, k 129 = b2 low part (BF16 split, ~16 bits), k 130-143
 // = 0; the activation operand carries 1, 1, 0 ... in those columns.
+// W1u and W3u are the first and output layers as tcgen05 B operands (same
+// layout): W1u N 128 x K 16 in the split form of W1t; W3u N 16 x K 128, rows
+// n < 8 = W3[k][.][n], rows 8-15 zero.
 struct FlowB {
   __nv_bfloat16 W2t[FK][FH][FLD];
   __nv_bfloat16 W3t[FK][8][FLD];
   __nv_bfloat16 W1t[FK][FH][FW1];
   __nv_bfloat16 W2u[FK][FH * FKH];
+  __nv_bfloat16 W1u[FK][FH * 16];
+  __nv_bfloat16 W3u[FK][16 * FH];
 };
 
 // Element index of (row m, column k) of a K-column tile in the tcgen05
@@ -248,7 +254,7 @@ __device__ __forceinline__ void flow_update_row(float* zr, const float (&v)[8], 
   float ls = 0.f;
 #pragma unroll
   for (int j = 0; j < NB; ++j) {
-    const float s = F_SMAX * tanhf(v[j] * (1.f / F_SMAX));
+    const float s = F_SMAX * tanh_coupling(v[j] * (1.f / F_SMAX));
     const int idx = flow_b(k, j);
     zr[idx] = fmaf(zr[idx], __expf(s), v[NB + j]);
     ls += s;

@@ -8,11 +8,13 @@
 // whose per-point weight is unbiased for the integral whatever the flow's
 // parameters, because |dy/du| is the exact Jacobian of the map that was applied.
 //
-// The coupling MLPs run on the fifth-generation tensor cores: per 128-point tile
-// and layer, one thread issues tcgen05.mma (BF16 operands in shared memory,
-// FP32 accumulators in tensor memory) for the first (K 16), hidden (K 128) and
-// output (N 16) layers; the warps read the accumulators back (tcgen05.ld),
-// add the bias, apply ReLU and repack BF16 operands for the next product.
+// The coupling MLPs run on the tensor cores: per 128-point tile and layer, one
+// thread issues tcgen05.mma (BF16 operands in shared memory, FP32 accumulators
+// in tensor memory, biases folded into the products) for the first (K 16) and
+// hidden (K 144) layers; the warps read the accumulators back (tcgen05.ld),
+// apply ReLU and repack BF16 operands for the next product. The output layer
+// (N 8) runs per warp on mma.sync, where its small N costs less than a
+// tensor-memory round trip.
 #pragma once
 #include "mem_batch.cuh"
 #include "mem_flow.cuh"
@@ -23,7 +25,9 @@ namespace mem {
 
 constexpr int FCH = 768;         // points per pass of a sampling CTA (z state in shared memory)
 constexpr int FROWS = 128;       // rows per tensor-core tile (M of the MMA)
-constexpr uint32_t F_TMEM_COLS = 128;  // hidden-layer accumulator (128 x 128 FP32)
+// tensor memory of a CTA: 128 x 128 FP32, the first-layer accumulator and then
+// the hidden layer's
+constexpr uint32_t F_TMEM_COLS = 128;
 constexpr uint32_t F_WAIT_LIMIT = 1u << 20;  // polls of one MMA-completion wait
 constexpr int FTS = 128;         // training samples per item
 
@@ -134,15 +138,16 @@ __global__ void k_flow_normalise(int64_t n_items, int nperm, int per_event,
   for (int t = threadIdx.x; t < FTS; t += blockDim.x) ws[item * FTS + t] *= scale;
 }
 
-// Shared memory of a sampling CTA (about 112 KB: two CTAs per SM; tensor
-// memory 128 columns each).
+// Shared memory of a sampling CTA (about 114 KB: two CTAs per SM; tensor
+// memory 128 columns each). The tcgen05 operands use the K-major layout of
+// umma_kmajor.
 template <class PH>
 struct __align__(1024) FlowSampSmem {
-  __nv_bfloat16 W2u[FH * FKH];    // hidden layer with its bias, tcgen05 B operand
+  __nv_bfloat16 W2u[FH * FKH];    // hidden layer with its bias (B, N 128 x K 144)
   __nv_bfloat16 Act[FROWS * FKH]; // hidden-layer input (+ constant columns), then output-layer input
-  __nv_bfloat16 W1t[FH][FW1];     // first layer, mma.sync B fragments (split form)
+  __nv_bfloat16 A1[FROWS * 16];   // first-layer input: [z_A hi | z_A lo | z_A hi | 1 1 0 0] per row
+  __nv_bfloat16 W1u[FH * 16];     // first layer (B, N 128 x K 16, split form, item bias in K 12-13)
   __nv_bfloat16 W3t[8][FLD];      // output layer, mma.sync B fragments
-  float cb1[FH];                  // c W1c + b1 for the CTA's item
   float b3[16];
   float zs[FCH * 8];              // per point: z[0..6], running log-Jacobian
   typename PH::Cache cache;
@@ -202,38 +207,54 @@ __device__ inline void flow_tc_end(FlowSampSmem<PH>& S, uint32_t tmem) {
 }
 
 // Layer k's operands into shared memory (B operands copied as laid out in
-// global memory) and the per-item bias c W1c + b1.
+// global memory), with the per-item bias c W1c + b1 folded into K 12-13 of the
+// first layer's operand (the input carries 1, 1 there).
 template <class PH>
 __device__ inline void flow_tc_load_layer(FlowSampSmem<PH>& S, const FlowW* __restrict__ W,
                                           const FlowB* __restrict__ Bw, int k) {
   const uint4* s2 = reinterpret_cast<const uint4*>(&Bw->W2u[k][0]);
   uint4* d2 = reinterpret_cast<uint4*>(S.W2u);
   for (int t = threadIdx.x; t < FH * FKH / 8; t += blockDim.x) d2[t] = s2[t];
-  const uint4* s1 = reinterpret_cast<const uint4*>(&Bw->W1t[k][0][0]);
-  uint4* d1 = reinterpret_cast<uint4*>(&S.W1t[0][0]);
-  for (int t = threadIdx.x; t < (int)(sizeof(S.W1t) / 16); t += blockDim.x) d1[t] = s1[t];
+  const uint4* s1 = reinterpret_cast<const uint4*>(&Bw->W1u[k][0]);
+  uint4* d1 = reinterpret_cast<uint4*>(S.W1u);
+  for (int t = threadIdx.x; t < (int)(sizeof(S.W1u) / 16); t += blockDim.x) d1[t] = s1[t];
   const uint4* s3 = reinterpret_cast<const uint4*>(&Bw->W3t[k][0][0]);
   uint4* d3 = reinterpret_cast<uint4*>(&S.W3t[0][0]);
   for (int t = threadIdx.x; t < (int)(sizeof(S.W3t) / 16); t += blockDim.x) d3[t] = s3[t];
-  for (int n = threadIdx.x; n < FH; n += blockDim.x) {
-    float v = W->b1[k][n];
+  float cb[(FH + THREADS - 1) / THREADS];
 #pragma unroll
-    for (int q = 0; q < FC; ++q) v = fmaf(S.c[q], W->W1c[k][q][n], v);
-    S.cb1[n] = v;
+  for (int i = 0; i < (FH + THREADS - 1) / THREADS; ++i) {
+    const int n = threadIdx.x + i * THREADS;
+    if (n < FH) {
+      float v = W->b1[k][n];
+#pragma unroll
+      for (int q = 0; q < FC; ++q) v = fmaf(S.c[q], W->W1c[k][q][n], v);
+      cb[i] = v;
+    }
+  }
+  __syncthreads();   // W1u copied: its K 12-13 now take the item's bias c W1c + b1 (split)
+#pragma unroll
+  for (int i = 0; i < (FH + THREADS - 1) / THREADS; ++i) {
+    const int n = threadIdx.x + i * THREADS;
+    if (n < FH) {
+      const float hi = bf16_hi(cb[i]);
+      S.W1u[umma_kmajor(n, 12, 16)] = __float2bfloat16_rn(hi);
+      S.W1u[umma_kmajor(n, 13, 16)] = __float2bfloat16_rn(cb[i] - hi);
+    }
   }
   if (threadIdx.x < 16) S.b3[threadIdx.x] = threadIdx.x < 8 ? W->b3[k][threadIdx.x] : 0.f;
 }
 
-// Accumulator columns col0 .. col0 + 63 of this warp's 32 rows (the bias is
-// already in the product) -> ReLU + BF16 in one conversion -> the output
-// layer's operand in Act.
+// Accumulator columns 64 (warp / 4) .. + 63 of this warp's 32 rows (tensor-memory
+// lanes 32 (warp % 4) ..) -> ReLU + BF16 -> the same columns and rows of Act, the
+// operand of the next product (the biases are folded into the products).
 template <class PH>
-__device__ inline void flow_tc_hidden_epilogue(FlowSampSmem<PH>& S, uint32_t tmem) {
+__device__ inline void flow_tc_epilogue(FlowSampSmem<PH>& S, uint32_t taddr) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = warp & 3, row = 32 * q + lane;
   const int cbase = 64 * (warp >> 2);
   float v[64];
-  tmem_ld64(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)cbase, v);
+  tmem_ld64(taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)cbase, v);
 #pragma unroll
   for (int cc = 0; cc < 8; ++cc) {
     const int col0 = cbase + 8 * cc;
@@ -245,46 +266,50 @@ __device__ inline void flow_tc_hidden_epilogue(FlowSampSmem<PH>& S, uint32_t tme
   }
 }
 
-// One warp, first layer of coupling layer k for the 16 tile rows rl .. rl + 15
-// (z rows at zr, stride 8): h1 = ReLU(z_A W1a + c W1c + b1) as mma.sync products
-// of the two-part BF16 split of z_A, written as BF16 into the UMMA operand Act.
+// Threads 0-127, row = thread: the first layer's input row of coupling layer k,
+// z_A (at zr, stride 8) in the two-part BF16 split [hi | lo | hi | 1 1 0 0] that
+// the split weights [W1a hi | W1a hi | W1a lo | bias hi, bias lo, 0 0] turn into
+// z W1a + c W1c + b1 to ~16 bits.
 template <class PH>
-__device__ inline void flow_first_layer(FlowSampSmem<PH>& S, int k, int rl, const float* zr) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int na = flow_na(k), j0 = (2 * t) & 3;
-  float zv[2][2];
+__device__ inline void flow_tc_first_operand(FlowSampSmem<PH>& S, int k, int row, const float* zr) {
+  const int na = flow_na(k);
+  float zh[4], zl[4];
 #pragma unroll
-  for (int h = 0; h < 2; ++h)
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int j = j0 + q;
-      zv[h][q] = j < na ? zr[(g + 8 * h) * 8 + flow_a(k, j)] : 0.f;
-    }
-  uint32_t a1[4];
-  if (t < 2) {
-    a1[0] = pack_bf16(zv[0][0], zv[0][1]);
-    a1[1] = pack_bf16(zv[1][0], zv[1][1]);
-    a1[2] = a1[0];
-    a1[3] = a1[1];
-  } else {
-    a1[0] = pack_bf16(zv[0][0] - bf16_hi(zv[0][0]), zv[0][1] - bf16_hi(zv[0][1]));
-    a1[1] = pack_bf16(zv[1][0] - bf16_hi(zv[1][0]), zv[1][1] - bf16_hi(zv[1][1]));
-    a1[2] = 0u;
-    a1[3] = 0u;
+  for (int j = 0; j < 4; ++j) {
+    const float z = j < na ? zr[flow_a(k, j)] : 0.f;
+    zh[j] = bf16_hi(z);
+    zl[j] = z - zh[j];
   }
-#pragma unroll
-  for (int j = 0; j < FH / 8; ++j) {
-    const int n0 = 8 * j;
-    const float c0 = S.cb1[n0 + 2 * t], c1 = S.cb1[n0 + 2 * t + 1];
-    float acc[4] = {c0, c1, c0, c1};
-    const __nv_bfloat16* brow = &S.W1t[n0 + g][0];
-    mma_bf16(acc, a1, *reinterpret_cast<const uint32_t*>(brow + 2 * t),
-             *reinterpret_cast<const uint32_t*>(brow + 2 * t + 8));
-    *reinterpret_cast<uint32_t*>(&S.Act[umma_kmajor(rl + g, n0 + 2 * t, FKH)]) =
-        pack_bf16_relu(acc[0], acc[1]);
-    *reinterpret_cast<uint32_t*>(&S.Act[umma_kmajor(rl + g + 8, n0 + 2 * t, FKH)]) =
-        pack_bf16_relu(acc[2], acc[3]);
+  const uint32_t h01 = pack_bf16(zh[0], zh[1]), h23 = pack_bf16(zh[2], zh[3]);
+  *reinterpret_cast<uint4*>(&S.A1[umma_kmajor(row, 0, 16)]) =
+      make_uint4(h01, h23, pack_bf16(zl[0], zl[1]), pack_bf16(zl[2], zl[3]));
+  *reinterpret_cast<uint4*>(&S.A1[umma_kmajor(row, 8, 16)]) =
+      make_uint4(h01, h23, pack_bf16(1.f, 1.f), 0u);
+}
+
+// One tcgen05 product D[tmem] = A B^T over n_k K-steps of 16, both operands
+// K-major in shared memory (row strides sbo_a, sbo_b bytes), issued by thread 0,
+// which waits for its completion; every thread then passes a barrier. False if
+// the wait gave up (S.abort is then set for the CTA).
+__device__ __forceinline__ bool flow_tc_mma(uint32_t d_tmem, uint32_t a_addr, uint32_t sbo_a,
+                                            uint32_t b_addr, uint32_t sbo_b, int n_k,
+                                            uint32_t idesc, uint32_t mbar, uint32_t& phase,
+                                            int* abort) {
+  fence_async_smem();   // generic-proxy operand writes -> the tensor core
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc_fence_after();
+    for (int s = 0; s < n_k; ++s)
+      umma_bf16(d_tmem, umma_desc(a_addr + 256u * (uint32_t)s, 128, sbo_a),
+                umma_desc(b_addr + 256u * (uint32_t)s, 128, sbo_b), idesc, s > 0 ? 1u : 0u);
+    umma_commit(mbar);
+    if (!mbar_wait(mbar, phase, F_WAIT_LIMIT)) *abort = 1;
   }
+  phase ^= 1u;
+  __syncthreads();   // the issuing thread saw the product complete
+  tc_fence_after();
+  return *abort == 0;
 }
 
 __device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], uint32_t saddr) {
@@ -302,17 +327,20 @@ __device__ inline void flow_output_layer(FlowSampSmem<PH>& S, int k, int rl, flo
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const uint32_t base = smem_u32(S.Act);
   const int lrow = rl + (lane & 7) + ((lane >> 3) & 1) * 8, lcol = (lane >> 4) * 8;
-  float o[4] = {0.f, 0.f, 0.f, 0.f};
+  // two independent accumulation chains (even and odd K steps) halve the
+  // dependent mma.sync latency
+  float o[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  const __nv_bfloat16* brow = &S.W3t[g][0];
 #pragma unroll
   for (int kk = 0; kk < FH / 16; ++kk) {
     uint32_t a[4];
     ldmatrix_x4(a, base + 2u * (uint32_t)umma_kmajor(lrow, 16 * kk + lcol, FKH));
-    const __nv_bfloat16* brow = &S.W3t[g][0];
-    mma_bf16(o, a, *reinterpret_cast<const uint32_t*>(brow + 16 * kk + 2 * t),
+    mma_bf16(o[kk & 1], a, *reinterpret_cast<const uint32_t*>(brow + 16 * kk + 2 * t),
              *reinterpret_cast<const uint32_t*>(brow + 16 * kk + 2 * t + 8));
   }
   const float bo0 = S.b3[2 * t], bo1 = S.b3[2 * t + 1];
-  const float v0 = o[0] + bo0, v1 = o[1] + bo1, v2 = o[2] + bo0, v3 = o[3] + bo1;
+  const float v0 = o[0][0] + o[1][0] + bo0, v1 = o[0][1] + o[1][1] + bo1;
+  const float v2 = o[0][2] + o[1][2] + bo0, v3 = o[0][3] + o[1][3] + bo1;
   float v[8];
 #pragma unroll
   for (int src = 0; src < 4; ++src) {
@@ -332,10 +360,12 @@ __device__ inline void flow_output_layer(FlowSampSmem<PH>& S, int k, int rl, flo
 // One pass of a CTA over points q0 .. q0 + nrow of an item (nrow a multiple of
 // FROWS, at most FCH; rows at or past p1 are computed but not used): base draw,
 // the coupling layers, then out(r, y, yc, log|dy/du|) per used row, threads
-// striding over rows. Per 128-row tile and layer, the 128 x 128 hidden product
-// runs on tcgen05 (one MMA round trip); the first (K 16) and output (N 8)
-// products run per warp on mma.sync around it. False if an MMA-completion wait
-// gave up (the CTA then stops issuing work).
+// striding over rows. Per 128-row tile and layer, two tcgen05 products: the
+// first layer (K 16: split BF16 input and the item bias) and the hidden layer
+// (K 144, bias folded in), each followed by a tensor-memory epilogue (ReLU, BF16
+// repack into Act); then the output layer (N 8) per warp on mma.sync from Act and
+// the affine update of the z rows. False if an MMA-completion wait gave up (the
+// CTA then stops issuing work).
 template <class PH, class Out>
 __device__ inline bool flow_pass(FlowSampSmem<PH>& S, uint32_t tmem, uint32_t& phase,
                                  const FlowW* __restrict__ W, const FlowB* __restrict__ Bw,
@@ -362,8 +392,9 @@ __device__ inline bool flow_pass(FlowSampSmem<PH>& S, uint32_t tmem, uint32_t& p
     }
     S.zs[r * 8 + 7] = lj;
   }
+  const uint32_t act = smem_u32(S.Act), a1 = smem_u32(S.A1), w1 = smem_u32(S.W1u);
+  const uint32_t w2 = smem_u32(S.W2u), mbar = smem_u32(&S.mbar);
   const int warp = threadIdx.x >> 5;
-  const uint32_t a_addr = smem_u32(S.Act), w2 = smem_u32(S.W2u), mbar = smem_u32(&S.mbar);
   for (int k = 0; k < FK; ++k) {
     // the previous layer's products are complete and its z updates visible
     tc_fence_before();
@@ -371,28 +402,19 @@ __device__ inline bool flow_pass(FlowSampSmem<PH>& S, uint32_t tmem, uint32_t& p
     if (S.abort) return false;
     flow_tc_load_layer(S, W, Bw, k);
     for (uint32_t t0 = 0; t0 < nrow; t0 += FROWS) {
-      // first layer: warp w produces rows 16 w .. 16 w + 15 of the hidden input
-      __syncthreads();   // Act is free: the previous tile's output layer has read it
-      flow_first_layer(S, k, 16 * warp, &S.zs[(t0 + 16 * warp) * 8]);
-      fence_async_smem();
+      __syncthreads();   // z rows of the previous tile updated, A1 and Act free
+      if (threadIdx.x < FROWS) flow_tc_first_operand(S, k, threadIdx.x, &S.zs[(t0 + threadIdx.x) * 8]);
+      // first layer (item bias folded into K 12-13), ReLU -> Act
+      if (!flow_tc_mma(tmem, a1, 16 * 16, w1, 16 * 16, 1, ID_H, mbar, phase, &S.abort))
+        return false;
+      flow_tc_epilogue(S, tmem);
+      // hidden layer (bias folded into K 128-129), ReLU -> Act
+      if (!flow_tc_mma(tmem, act, 16 * FKH, w2, 16 * FKH, FKH / 16, ID_H, mbar, phase, &S.abort))
+        return false;
+      flow_tc_epilogue(S, tmem);
       tc_fence_before();
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        tc_fence_after();
-#pragma unroll
-        for (uint32_t s = 0; s < FKH / 16; ++s)
-          umma_bf16(tmem, umma_desc(a_addr + 256 * s, 128, 16 * FKH),
-                    umma_desc(w2 + 256 * s, 128, 16 * FKH), ID_H, s > 0 ? 1u : 0u);
-        umma_commit(mbar);
-        if (!mbar_wait(mbar, phase, F_WAIT_LIMIT)) S.abort = 1;
-      }
-      phase ^= 1u;
-      __syncthreads();   // the issuing thread saw the product complete
-      tc_fence_after();
-      if (S.abort) return false;
-      flow_tc_hidden_epilogue(S, tmem);   // h2 -> Act (the product has read Act)
-      tc_fence_before();
-      __syncthreads();
+      __syncthreads();   // Act holds the whole tile's hidden output
+      // output layer per warp on mma.sync, then the affine update of its 16 rows
       flow_output_layer(S, k, 16 * warp, &S.zs[(t0 + 16 * warp) * 8]);
     }
   }

@@ -2,7 +2,9 @@
 (csrc/mem_fastmath.cuh) against float64 numpy, compiled as host code with nvcc:
 atan2(y, x) for y > 0 over all quadrant cases and 24 decades of |x|/y, and
 sin(a) on [0, pi] including arguments near 0 and pi. Bound: 4 ulp of FP32
-relative error (the integrand's per-point tolerance is 1e-5)."""
+relative error (the integrand's per-point tolerance is 1e-5). The coupling
+tanh (host form: expf where the device uses __expf, whose error on
+[-1e4, 0] is a few ulp more) within 2e-6 relative over 1e-8 < |x| < 50."""
 import os
 import shutil
 import subprocess
@@ -20,8 +22,9 @@ int main(int argc, char** argv) {
   FILE* g = fopen(argv[2], "wb");
   float v[2];
   while (fread(v, sizeof(float), 2, f) == 2) {
-    const float out[2] = {mem::atan2_ypos(v[0], v[1]), mem::sin_0pi(v[1])};
-    fwrite(out, sizeof(float), 2, g);
+    const float out[3] = {mem::atan2_ypos(v[0], v[1]), mem::sin_0pi(v[1]),
+                          mem::tanh_coupling(v[0])};
+    fwrite(out, sizeof(float), 3, g);
   }
   fclose(f);
   fclose(g);
@@ -49,7 +52,7 @@ def run(prog, y, x):
     inp = np.stack([y, x], 1).astype(np.float32)
     (d / "in.bin").write_bytes(inp.tobytes())
     subprocess.run([str(exe), str(d / "in.bin"), str(d / "out.bin")], check=True)
-    out = np.frombuffer((d / "out.bin").read_bytes(), dtype=np.float32).reshape(-1, 2)
+    out = np.frombuffer((d / "out.bin").read_bytes(), dtype=np.float32).reshape(-1, 3)
     return inp, out
 
 
@@ -78,3 +81,13 @@ def test_sin_zero_to_pi(prog):
     # near pi the argument itself carries one FP32 rounding of pi - a
     tol = 4 * 2.0 ** -24 + np.where(aa[ok] > 3.0, 2.0 ** -24 * np.pi / ref[ok], 0.0)
     assert np.all(rel <= tol), rel.max()
+
+
+def test_tanh_coupling(prog):
+    rng = np.random.default_rng(7)
+    n = 200000
+    x = np.sign(rng.uniform(-1, 1, n)) * 10.0 ** rng.uniform(-8, np.log10(50.0), n)
+    inp, out = run(prog, x, np.ones(n))
+    xx = inp[:, 0].astype(np.float64)
+    rel = np.abs(out[:, 2] / np.tanh(xx) - 1)
+    assert rel.max() < 2e-6, (rel.max(), xx[np.argmax(rel)])
