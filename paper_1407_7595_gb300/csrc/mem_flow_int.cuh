@@ -212,15 +212,16 @@ __device__ inline void flow_tc_end(FlowSampSmem<PH>& S, uint32_t tmem) {
 template <class PH>
 __device__ inline void flow_tc_load_layer(FlowSampSmem<PH>& S, const FlowW* __restrict__ W,
                                           const FlowB* __restrict__ Bw, int k) {
+  // asynchronous 16-byte copies (all in flight at once), completed below
   const uint4* s2 = reinterpret_cast<const uint4*>(&Bw->W2u[k][0]);
   uint4* d2 = reinterpret_cast<uint4*>(S.W2u);
-  for (int t = threadIdx.x; t < FH * FKH / 8; t += blockDim.x) d2[t] = s2[t];
+  for (int t = threadIdx.x; t < FH * FKH / 8; t += blockDim.x) cp_async16(&d2[t], &s2[t]);
   const uint4* s1 = reinterpret_cast<const uint4*>(&Bw->W1u[k][0]);
   uint4* d1 = reinterpret_cast<uint4*>(S.W1u);
-  for (int t = threadIdx.x; t < (int)(sizeof(S.W1u) / 16); t += blockDim.x) d1[t] = s1[t];
+  for (int t = threadIdx.x; t < (int)(sizeof(S.W1u) / 16); t += blockDim.x) cp_async16(&d1[t], &s1[t]);
   const uint4* s3 = reinterpret_cast<const uint4*>(&Bw->W3t[k][0][0]);
   uint4* d3 = reinterpret_cast<uint4*>(&S.W3t[0][0]);
-  for (int t = threadIdx.x; t < (int)(sizeof(S.W3t) / 16); t += blockDim.x) d3[t] = s3[t];
+  for (int t = threadIdx.x; t < (int)(sizeof(S.W3t) / 16); t += blockDim.x) cp_async16(&d3[t], &s3[t]);
   float cb[(FH + THREADS - 1) / THREADS];
 #pragma unroll
   for (int i = 0; i < (FH + THREADS - 1) / THREADS; ++i) {
@@ -232,6 +233,7 @@ __device__ inline void flow_tc_load_layer(FlowSampSmem<PH>& S, const FlowW* __re
       cb[i] = v;
     }
   }
+  cp_async_wait_all();
   __syncthreads();   // W1u copied: its K 12-13 now take the item's bias c W1c + b1 (split)
 #pragma unroll
   for (int i = 0; i < (FH + THREADS - 1) / THREADS; ++i) {
@@ -401,13 +403,18 @@ __device__ inline bool flow_pass(FlowSampSmem<PH>& S, uint32_t tmem, uint32_t& p
     __syncthreads();
     if (S.abort) return false;
     flow_tc_load_layer(S, W, Bw, k);
+    if (threadIdx.x < FROWS) flow_tc_first_operand(S, k, threadIdx.x, &S.zs[threadIdx.x * 8]);
     for (uint32_t t0 = 0; t0 < nrow; t0 += FROWS) {
-      __syncthreads();   // z rows of the previous tile updated, A1 and Act free
-      if (threadIdx.x < FROWS) flow_tc_first_operand(S, k, threadIdx.x, &S.zs[(t0 + threadIdx.x) * 8]);
-      // first layer (item bias folded into K 12-13), ReLU -> Act
+      // first layer (item bias folded into K 12-13), ReLU -> Act. The barrier in
+      // flow_tc_mma also orders the previous tile's output layer (reads of Act)
+      // before this tile's epilogue writes Act.
       if (!flow_tc_mma(tmem, a1, 16 * 16, w1, 16 * 16, 1, ID_H, mbar, phase, &S.abort))
         return false;
       flow_tc_epilogue(S, tmem);
+      // A1 is free (the product above is complete): the next tile's input, whose
+      // z_A rows the current tile's update does not touch
+      if (t0 + FROWS < nrow && threadIdx.x < FROWS)
+        flow_tc_first_operand(S, k, threadIdx.x, &S.zs[(t0 + FROWS + threadIdx.x) * 8]);
       // hidden layer (bias folded into K 128-129), ReLU -> Act
       if (!flow_tc_mma(tmem, act, 16 * FKH, w2, 16 * FKH, FKH / 16, ID_H, mbar, phase, &S.abort))
         return false;

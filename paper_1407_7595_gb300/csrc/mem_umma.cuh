@@ -149,6 +149,16 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16-byte global -> shared copy in flight (both addresses 16-byte aligned); the
+// thread's copies complete at cp_async_wait_all.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem_dst)), "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Ordering of tensor-core operations around thread barriers, and of generic
 // shared-memory writes before the tensor core (async proxy) reads them.
 __device__ __forceinline__ void tc_fence_before() {
