@@ -47,6 +47,11 @@ FLOPS_PER_EVAL = {synth.PROC_DY: 161.6, synth.PROC_W: 406.0, synth.PROC_TTBAR: 3
 # cheaper than the library functions and the per-flavour evaluation.
 FLOPS_EXECUTED_PER_EVAL = {synth.PROC_DY: 157.0, synth.PROC_W: 345.7, synth.PROC_TTBAR: 2842.3}
 FP32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 FP32 lanes
+# DRAM bytes (read + write) per launch unit from one ncu capture of the current
+# kernels: k_main reads each item's grid and constants once (other CTAs of the item
+# hit L2), so its traffic grows with the items; k_parton_tt reads each record once.
+DRAM_BYTES_PER_ITEM_MAIN = {synth.PROC_W: 9008.0}
+DRAM_BYTES_PER_PARTON_EVENT = 128.2
 
 # FP32 flops of the parton-level kernel per event (both b-quark assignments; FADD,
 # FMUL = 1, FFMA = 2), counted with ncu instruction counters and held fixed.
@@ -408,9 +413,12 @@ def run_ours(args):
         fpe = FLOPS_PER_EVAL.get(kind)
         t_main = statistics.mean(main_ms) * 1e-3
         achieved = fpe * n_ev * n_perm * n_main / t_main / 1e12 if fpe else None
+        dpi = DRAM_BYTES_PER_ITEM_MAIN.get(kind)
         roof = {"bound": "alu", "kernel": "k_main (frozen-grid sampling)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None,
+                "traffic": (dpi * n_ev * n_perm
+                            if dpi and not args.pdf_grid and not args.strat else None),
                 "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                f"{max_mhz:.0f} MHz max SM clock",
                 "flops_per_eval": fpe,
@@ -857,7 +865,8 @@ def run_parton(args):
                "status_ok": ok,
                "roofline": {"bound": "alu", "kernel": "k_parton_tt", "achieved": achieved,
                             "peak": peak, "unit": "TFLOP/s",
-                            "frac": achieved / peak if achieved else None, "traffic": None,
+                            "frac": achieved / peak if achieved else None,
+                            "traffic": None if args.pdf_grid else DRAM_BYTES_PER_PARTON_EVENT * n_ev,
                             "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 "
                                            f"lanes x 2 x {max_mhz:.0f} MHz max SM clock",
                             "flops_per_event": fpe, "kernel_ms": t_k * 1e3},

@@ -268,12 +268,14 @@ __device__ inline void flow_tc_epilogue(FlowSampSmem<PH>& S, uint32_t taddr) {
   }
 }
 
-// Threads 0-127, row = thread: the first layer's input row of coupling layer k,
+// Thread pair (row, half) with row = thread % 128: K 0-7 (half 0) or K 8-15
+// (half 1) of the first layer's input row of coupling layer k,
 // z_A (at zr, stride 8) in the two-part BF16 split [hi | lo | hi | 1 1 0 0] that
 // the split weights [W1a hi | W1a hi | W1a lo | bias hi, bias lo, 0 0] turn into
 // z W1a + c W1c + b1 to ~16 bits.
 template <class PH>
-__device__ inline void flow_tc_first_operand(FlowSampSmem<PH>& S, int k, int row, const float* zr) {
+__device__ inline void flow_tc_first_operand(FlowSampSmem<PH>& S, int k, int row, int half,
+                                             const float* zr) {
   const int na = flow_na(k);
   float zh[4], zl[4];
 #pragma unroll
@@ -283,10 +285,12 @@ __device__ inline void flow_tc_first_operand(FlowSampSmem<PH>& S, int k, int row
     zl[j] = z - zh[j];
   }
   const uint32_t h01 = pack_bf16(zh[0], zh[1]), h23 = pack_bf16(zh[2], zh[3]);
-  *reinterpret_cast<uint4*>(&S.A1[umma_kmajor(row, 0, 16)]) =
-      make_uint4(h01, h23, pack_bf16(zl[0], zl[1]), pack_bf16(zl[2], zl[3]));
-  *reinterpret_cast<uint4*>(&S.A1[umma_kmajor(row, 8, 16)]) =
-      make_uint4(h01, h23, pack_bf16(1.f, 1.f), 0u);
+  if (half == 0)
+    *reinterpret_cast<uint4*>(&S.A1[umma_kmajor(row, 0, 16)]) =
+        make_uint4(h01, h23, pack_bf16(zl[0], zl[1]), pack_bf16(zl[2], zl[3]));
+  else
+    *reinterpret_cast<uint4*>(&S.A1[umma_kmajor(row, 8, 16)]) =
+        make_uint4(h01, h23, pack_bf16(1.f, 1.f), 0u);
 }
 
 // One tcgen05 product D[tmem] = A B^T over n_k K-steps of 16, both operands
@@ -375,6 +379,7 @@ __device__ inline bool flow_pass(FlowSampSmem<PH>& S, uint32_t tmem, uint32_t& p
                                  uint32_t q0, uint32_t nrow, uint32_t p1, Out& out) {
   constexpr int D = PH::D;
   static_assert(D == FD, "the flow is built for the 7-dimensional ttbar integral");
+  static_assert(THREADS == 2 * FROWS, "two threads build each row of the first-layer input");
   constexpr uint32_t ID_H = umma_idesc_bf16(FROWS, FH);
   for (uint32_t r = threadIdx.x; r < nrow; r += THREADS) {
     const uint32_t p = q0 + r;
@@ -403,7 +408,8 @@ __device__ inline bool flow_pass(FlowSampSmem<PH>& S, uint32_t tmem, uint32_t& p
     __syncthreads();
     if (S.abort) return false;
     flow_tc_load_layer(S, W, Bw, k);
-    if (threadIdx.x < FROWS) flow_tc_first_operand(S, k, threadIdx.x, &S.zs[threadIdx.x * 8]);
+    const int frow = threadIdx.x & (FROWS - 1), fhalf = threadIdx.x / FROWS;
+    flow_tc_first_operand(S, k, frow, fhalf, &S.zs[frow * 8]);
     for (uint32_t t0 = 0; t0 < nrow; t0 += FROWS) {
       // first layer (item bias folded into K 12-13), ReLU -> Act. The barrier in
       // flow_tc_mma also orders the previous tile's output layer (reads of Act)
@@ -413,8 +419,8 @@ __device__ inline bool flow_pass(FlowSampSmem<PH>& S, uint32_t tmem, uint32_t& p
       flow_tc_epilogue(S, tmem);
       // A1 is free (the product above is complete): the next tile's input, whose
       // z_A rows the current tile's update does not touch
-      if (t0 + FROWS < nrow && threadIdx.x < FROWS)
-        flow_tc_first_operand(S, k, threadIdx.x, &S.zs[(t0 + FROWS + threadIdx.x) * 8]);
+      if (t0 + FROWS < nrow)
+        flow_tc_first_operand(S, k, frow, fhalf, &S.zs[(t0 + FROWS + frow) * 8]);
       // hidden layer (bias folded into K 128-129), ReLU -> Act
       if (!flow_tc_mma(tmem, act, 16 * FKH, w2, 16 * FKH, FKH / 16, ID_H, mbar, phase, &S.abort))
         return false;
