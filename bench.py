@@ -595,7 +595,8 @@ def flow_ab_leg(abi, torch, sp, n_train=4096, n_eval=4096, batch=304, steps=2000
         return float((r[1][3] == 0).double().mean().item()) / r[0]
 
     target = dict(target_rel_err=0.01, max_points=1 << 24)
-    v_set = ((3, 4096, 1 << 14), (5, 8192, 1 << 14), (2, 8192, 1 << 14), (3, 2048, 1 << 13))
+    v_set = ((3, 4096, 1 << 14), (5, 8192, 1 << 14), (2, 8192, 1 << 14), (3, 2048, 1 << 13),
+             (2, 4096, 1 << 14), (4, 4096, 1 << 14), (3, 4096, 1 << 13))
     f_set = ((1, 2048, 1 << 14), (2, 4096, 1 << 14), (1, 1024, 12288), (2, 2048, 12288),
              (1, 4096, 1 << 14), (2, 2048, 1 << 14), (3, 2048, 1 << 14))
     if arm == "vegas":
