@@ -12,6 +12,7 @@
 #include "../../include/mem.h"
 #include "mem_internal.h"
 #include "mem_kernels.cuh"
+#include "mem_launch_config.h"
 
 namespace {
 
@@ -59,8 +60,8 @@ uint32_t strat_side(uint64_t n, int d, int k) {
 
 int dims_of(int kind) { return kind == PROC_DY ? 2 : kind == PROC_W ? 4 : kind == PROC_TTBAR ? 7 : -1; }
 int nperm_of(int kind) { return kind == PROC_TTBAR ? 24 : (kind == PROC_DY || kind == PROC_W) ? 1 : -1; }
-uint32_t chunk_points(int kind) {
-  return THREADS * (kind == PROC_DY ? 16u : kind == PROC_W ? 32u : 8u);
+uint32_t chunk_points(int kind) {  // points of one frozen-grid CTA: THREADS x points per thread
+  return THREADS * (uint32_t)(kind == PROC_DY ? PPT_DY : kind == PROC_W ? PPT_W : PPT_TT);
 }
 
 cudaError_t launch_integrate(int kind, const IntegrateArgs& a, cudaStream_t st) {

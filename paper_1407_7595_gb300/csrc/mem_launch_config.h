@@ -4,11 +4,11 @@
 
 namespace mem {
 
-constexpr int PPT_DY = 16;
-constexpr int PPT_W = 32;
+constexpr int PPT_DY = 16;       // frozen-grid points per thread (Drell-Yan): 4,096 per CTA
+constexpr int PPT_W = 64;        // frozen-grid points per thread (W): 16,384 per CTA
 constexpr int MINB_W = 5;        // adaptation and round kernels: 5 CTAs of 256 threads per SM (<= 51 registers)
 constexpr int MINB_W_MAIN = 6;   // frozen-grid kernel: 6 CTAs per SM (<= 42 registers, 4 bytes of spill)
-constexpr int PPT_TT = 8;
+constexpr int PPT_TT = 16;       // frozen-grid points per thread (ttbar): 4,096 per CTA
 constexpr int MINB_TT = 2;       // adaptation and round kernels: <= 128 registers, no spills
 constexpr int MINB_TT_MAIN = 3;  // frozen-grid kernel: <= 80 registers (20 bytes of spill), 24 warps/SM
 
