@@ -15,6 +15,7 @@
 // normalised propagators) are applied in FP64.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <string>
@@ -207,16 +208,20 @@ extern "C" mem_status mem_parton_weights(const mem_events* events, const mem_pro
   const double mgt = (double)P.mtgt, mgw = (double)P.mwgw;
   const double pref = std::pow(tp, 4.0) * (2.0 / s) * std::pow(1.0 / (2.0 * std::pow(tp, 3.0)), 6.0) /
                       (mgt * mgt * mgt * mgt) / (mgw * mgw * mgw * mgw);
-  static int blocks_per_sm = 0, sms = 0;
-  if (!blocks_per_sm) {
-    int dev_id = 0;
-    cudaGetDevice(&dev_id);
+  // resident CTAs of the current device, cached per device (writers store equal values)
+  static std::atomic<int> occ_cache[64];
+  int dev_id = 0;
+  cudaGetDevice(&dev_id);
+  int full_ctas = dev_id < 64 ? occ_cache[dev_id].load(std::memory_order_relaxed) : 0;
+  if (full_ctas == 0) {
+    int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_parton_tt, PARTON_THREADS, 0);
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_parton_tt, PARTON_THREADS, 0);
+    full_ctas = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    if (dev_id < 64) occ_cache[dev_id].store(full_ctas, std::memory_order_relaxed);
   }
   const int64_t need = (n + PARTON_THREADS - 1) / PARTON_THREADS;
-  const int64_t full = (int64_t)blocks_per_sm * sms;
+  const int64_t full = full_ctas;
   const unsigned grid = (unsigned)(need < full ? need : full);
   double* d_prob = prob;
   double* d_w = w_assign;
