@@ -178,8 +178,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def cpu_model():
+    """The host CPU's model name (best effort)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
 def cpu_baseline(kind, seed):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload, all host cores."""
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: all host
+    cores (the paper's CPU (MP) column) and one core (its CPU column)."""
     from oracle import oracle as O
     # (events, evaluations per item): about 10 s of work on 16 Grace cores
     n_ev, n_pts = {synth.PROC_W: (64, 1 << 16), synth.PROC_DY: (16, 1 << 15),
@@ -192,9 +206,17 @@ def cpu_baseline(kind, seed):
     t = time.perf_counter()
     O.integrate(P, T, recs, seed=1, n_points=n_pts, n_threads=cores)
     dt = time.perf_counter() - t
+    # one core on a sixteenth of the events (at least one)
+    n1 = max(1, n_ev // 16)
+    t = time.perf_counter()
+    O.integrate(P, T, recs[:n1], seed=1, n_points=n_pts, n_threads=1)
+    dt1 = time.perf_counter() - t
     return {"value": n_ev * n_perm * n_pts / dt, "unit": "integrand evals/s", "cores": cores,
-            "kind": "oracle", "sample": f"{n_ev} events x {n_perm} permutations x {n_pts} "
-                                       f"evaluations (same generator and VEGAS plan), {dt:.1f} s"}
+            "kind": "oracle", "cpu": cpu_model(),
+            "single_core_value": n1 * n_perm * n_pts / dt1,
+            "sample": f"{n_ev} events x {n_perm} permutations x {n_pts} evaluations (same "
+                      f"generator and VEGAS plan), {dt:.1f} s on {cores} cores; {n1} of the "
+                      f"events on 1 core, {dt1:.1f} s"}
 
 
 def reference_to_target(args, O):
