@@ -236,13 +236,10 @@ mem_status mem_flow_map(const mem_flow* f, const float* cond, const float* u, in
 
 namespace {
 
+// set on every call: the attribute belongs to the current device's context
 cudaError_t train_smem_attr() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_flow_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(FlowTrainSmem));
-  if (e == cudaSuccess) done = true;
-  return e;
+  return cudaFuncSetAttribute(k_flow_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(FlowTrainSmem));
 }
 
 }  // namespace

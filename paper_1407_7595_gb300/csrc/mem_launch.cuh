@@ -11,13 +11,10 @@ namespace mem {
 template <class PH, int PPT, int MINB, int MINB_MAIN = MINB>
 cudaError_t run_integrate(const IntegrateArgs& a, cudaStream_t st) {
   const size_t smem = sizeof(AdaptSmem<PH>);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_adapt<PH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  // set on every call: the attribute belongs to the current device's context
+  cudaError_t ea = cudaFuncSetAttribute(k_adapt<PH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem);
+  if (ea != cudaSuccess) return ea;
   if (a.phase_events) cudaEventRecord(a.phase_events[0], st);
   // with n_iters == 0 the starting grid is frozen as given
   k_adapt<PH, MINB><<<(unsigned)a.n_items, THREADS, smem, st>>>(
