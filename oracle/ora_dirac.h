@@ -1,4 +1,5 @@
-/* Oracle-internal Dirac algebra in the Dirac representation:
+/* Oracle-internal Dirac algebra (test infrastructure; see oracle.h) in the Dirac
+ * representation:
  *   gamma^0 = diag(1, -1) in 2x2 blocks, gamma^k = [[0, s_k], [-s_k, 0]],
  *   gamma^5 = [[0, 1], [1, 0]], P_L = (1 - gamma^5)/2, P_R = (1 + gamma^5)/2.
  * Plain 4x4 complex matrices and 4-component spinors. Test oracle only. */

@@ -1,4 +1,5 @@
-/* Philox4x32-10 counter-based generator, written from its published
+/* Philox4x32-10 counter-based generator of the oracle (test infrastructure; see
+ * oracle.h), written from its published
  * definition (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as
  * 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplications with the
  * round constants 0xD2511F53 and 0xCD9E8D57, the key bumped by the Weyl
