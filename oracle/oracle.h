@@ -158,6 +158,15 @@ typedef struct {
   int32_t pad;
 } ora_opts;
 
+/* Dilepton ttbar: the neutrino and antineutrino momenta (E, px, py, pz) for given
+ * b, bbar, l+, l- momenta (massless), missing pT and the virtualities q2_W+, q2_W-,
+ * q2_t, q2_tbar (Sec. 3, Eq. "dilepsolv"); up to 4 solutions in nu_out, nub_out
+ * (4 x 4 doubles each) with jac_out[i] = 1 / |det d(q2_W+, q2_t, q2_W-, q2_tbar) /
+ * d(nu_x, nu_y, nu_z, nubar_z)|. Returns the number of solutions. */
+int ora_dilep_nu(const double* pb, const double* pbb, const double* plp, const double* plm,
+                 double metx, double mety, double q2wp, double q2wm, double q2t, double q2tb,
+                 double* nu_out, double* nub_out, double* jac_out);
+
 /* Event discriminant D = log10(p_S / p_B) and its first-order error from the
  * errors of the two estimates; returns 1 (NaN outputs) unless both p > 0. */
 int ora_discriminant(double p_s, double e_s, double p_b, double e_b, double* D, double* err);

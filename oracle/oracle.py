@@ -18,7 +18,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liboracle.so")
 SOURCES = ["ora_philox.c", "ora_dirac.c", "ora_matrix.c", "ora_process.c", "ora_vegas.c",
-           "ora_integrate.c"]
+           "ora_integrate.c", "ora_dilep.c"]
 NG = 128
 REC = 32
 
@@ -95,6 +95,7 @@ def load():
     lib.ora_msq_w.restype = C.c_double
     lib.ora_integrand_roots.argtypes = [P, T, fp, C.c_int, _dp, _dp]
     lib.ora_discriminant.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, _dp, _dp]
+    lib.ora_dilep_nu.argtypes = [_dp, _dp, _dp, _dp] + [C.c_double] * 6 + [_dp, _dp, _dp]
     lib.ora_strat_side.argtypes = [C.c_uint64, C.c_int, C.c_int]
     lib.ora_strat_side.restype = C.c_uint64
     lib.ora_pdf_q.argtypes = [P, C.c_int, C.c_double, C.c_double]
@@ -314,6 +315,19 @@ def eval_points(P, T, rec, event_id, perm, seed, point0, n, grid=None):
     load().ora_eval_points(C.byref(P), C.byref(T), rp, event_id, perm, seed, point0, n, gp,
                            w.ctypes.data_as(_dp))
     return w
+
+
+def dilep_nu(pb, pbb, plp, plm, met, q2wp, q2wm, q2t, q2tb):
+    """Neutrino solutions of the dilepton ttbar constraints: list of (nu, nubar, jac)
+    with nu, nubar = (E, px, py, pz)."""
+    args = [_d(v) for v in (pb, pbb, plp, plm)]
+    nu = np.zeros(16)
+    nb = np.zeros(16)
+    jac = np.zeros(4)
+    n = load().ora_dilep_nu(*[a[1] for a in args], float(met[0]), float(met[1]), q2wp, q2wm,
+                            q2t, q2tb, nu.ctypes.data_as(_dp), nb.ctypes.data_as(_dp),
+                            jac.ctypes.data_as(_dp))
+    return [(nu[4 * i:4 * i + 4].copy(), nb[4 * i:4 * i + 4].copy(), jac[i]) for i in range(n)]
 
 
 def discriminant(p_s, e_s, p_b, e_b):

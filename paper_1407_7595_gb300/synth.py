@@ -379,6 +379,83 @@ def gen_ttbar_parton(n, seed):
     return out
 
 
+PROC_TTBAR_DILEP = 3
+
+
+def gen_ttbar_dilep(n, seed, tf=None, truth=False):
+    """Dilepton ttbar events, t -> b l+ nu, tbar -> bbar mu- nubar (the final state of
+    the paper's hadron-level analysis without the Higgs, Sec. 3-4): the production
+    and decay chain of gen_ttbar; leptons exact within |eta| <= 2.5; the two b
+    jets within |eta| <= 2.5 and E >= 20 GeV, smeared by the double Gaussian and
+    stored by decreasing measured energy; MET = nu_T + nubar_T + N(0, 15^2).
+    Record: objects 0 l+ (e+), 1 mu-, 2 and 3 the b jets; [24], [25] MET;
+    [26] = 4; [27] = 3; [28] = 0 if object 2 is the b quark, else 1.
+    With truth=True also returns the (n, 6, 4) parton momenta (E, px, py, pz) of
+    b, bbar, l+, mu-, nu, nubar."""
+    tf = tf or DEFAULT_TF[PROC_TTBAR]
+    P = DEFAULT_PROCESS
+    rng = np.random.Generator(np.random.Philox(seed))
+    out = np.zeros((n, RECORD_FLOATS), dtype=np.float32)
+    tr = np.zeros((n, 6, 4))
+    have = 0
+    while have < n:
+        m = max(1024, 2 * (n - have))
+        mtt = rng.uniform(350.0, 1000.0, m)
+        mt1 = _bw_mass_v(rng, P["mt"], P["wt"], 15.0, m)
+        mt2 = _bw_mass_v(rng, P["mt"], P["wt"], 15.0, m)
+        mw1 = _bw_mass_v(rng, P["mw"], P["ww"], 15.0, m)
+        mw2 = _bw_mass_v(rng, P["mw"], P["ww"], 15.0, m)
+        y = rng.uniform(-1.5, 1.5, m)
+        ok = mt1 + mt2 < mtt
+        mtt = np.where(ok, mtt, mt1 + mt2 + 1.0)
+        sysp = np.stack([mtt * np.cosh(y), 0 * y, 0 * y, mtt * np.sinh(y)], axis=1)
+        t, tb = _two_body_v(rng, mtt, mt1, mt2)
+        t, tb = _boost_v(t, sysp), _boost_v(tb, sysp)
+        b, wp = _two_body_v(rng, mt1, 0.0, mw1)
+        b, wp = _boost_v(b, t), _boost_v(wp, t)
+        lp, nu = _two_body_v(rng, mw1, 0.0, 0.0)
+        lp, nu = _boost_v(lp, wp), _boost_v(nu, wp)
+        bb, wm = _two_body_v(rng, mt2, 0.0, mw2)
+        bb, wm = _boost_v(bb, tb), _boost_v(wm, tb)
+        lm, nub = _two_body_v(rng, mw2, 0.0, 0.0)
+        lm, nub = _boost_v(lm, wm), _boost_v(nub, wm)
+        for q in (lp, lm, b, bb):
+            ok &= np.abs(_eta_phi_v(q)[0]) <= 2.5
+        def smear(q):
+            rel = np.where(rng.uniform(size=m) < tf["jet_tail_w"], tf["jet_tail"], tf["jet_core"])
+            return q[:, 0] * (1.0 + rel * rng.standard_normal(m))
+        Eb, Ebb = smear(b), smear(bb)
+        ok &= (Eb >= 20.0) & (Ebb >= 20.0)
+        swap = Ebb > Eb
+        idx = np.nonzero(ok)[0][: n - have]
+        r = out[have: have + len(idx)]
+        for slot, (q, kind) in enumerate(((lp, KIND_E_PLUS), (lm, KIND_MU_MINUS))):
+            eta, phi, _ = _eta_phi_v(q[idx])
+            r[:, 4 * slot] = q[idx, 0]
+            r[:, 4 * slot + 1] = eta
+            r[:, 4 * slot + 2] = phi
+            r[:, 4 * slot + 3] = kind
+        first = np.where(swap[:, None], bb, b)[idx]
+        second = np.where(swap[:, None], b, bb)[idx]
+        E1 = np.where(swap, Ebb, Eb)[idx]
+        E2 = np.where(swap, Eb, Ebb)[idx]
+        for slot, q, E in ((2, first, E1), (3, second, E2)):
+            eta, phi, _ = _eta_phi_v(q)
+            r[:, 4 * slot] = E
+            r[:, 4 * slot + 1] = eta
+            r[:, 4 * slot + 2] = phi
+            r[:, 4 * slot + 3] = KIND_JET
+        r[:, 24] = (nu[idx, 1] + nub[idx, 1]) + tf["met_sigma"] * rng.standard_normal(len(idx))
+        r[:, 25] = (nu[idx, 2] + nub[idx, 2]) + tf["met_sigma"] * rng.standard_normal(len(idx))
+        r[:, 26] = 4
+        r[:, 27] = PROC_TTBAR_DILEP
+        r[:, 28] = swap[idx].astype(np.float32)
+        for k, q in enumerate((b, bb, lp, lm, nu, nub)):
+            tr[have: have + len(idx), k] = q[idx]
+        have += len(idx)
+    return (out, tr) if truth else out
+
+
 GENERATORS = {PROC_DY: gen_dy, PROC_W: gen_w, PROC_TTBAR: gen_ttbar}
 
 
