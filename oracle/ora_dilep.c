@@ -16,7 +16,9 @@
  *    p_x (roots by the Durand-Kerner iteration in complex FP64, real ones polished
  *    by Newton steps on the two conics), p_y from the linear combination of the
  *    conics without the p_y^2 term; solutions with positive neutrino energies are
- *    kept.
+ *    kept and refined by Newton steps on the four virtualities themselves with
+ *    exactly massless neutrinos (the conic coefficients lose digits to
+ *    cancellation; the direct residual does not).
  * Each solution carries 1 / |det d(q2_W+, q2_t, q2_W-, q2_tbar) / d(nu_x, nu_y,
  * nu_z, nubar_z)|, the Jacobian of trading the neutrino momenta (with the MET
  * constraint applied) for the four virtualities.
@@ -135,6 +137,76 @@ static void polish(const conic_t* a, const conic_t* b, double* x, double* y) {
   }
 }
 
+static double m2sum(const double* a, const double* b, const double* c) {
+  double t[4];
+  for (int k = 0; k < 4; ++k) t[k] = a[k] + b[k] + (c ? c[k] : 0.0);
+  return t[0] * t[0] - t[1] * t[1] - t[2] * t[2] - t[3] * t[3];
+}
+
+/* The four virtualities (W+, t, W-, tbar) of on-shell neutrinos with free
+ * components f = (nu_x, nu_y, nu_z, nubar_z), nubar_T = MET - nu_T, and their
+ * derivatives M = d(q2) / d(f) (scaled units). */
+static void forward(const double* b, const double* bb, const double* lp, const double* lm,
+                    double mx, double my, const double* f, double* q, double M[4][4], double* nu,
+                    double* nub) {
+  nu[1] = f[0];
+  nu[2] = f[1];
+  nu[3] = f[2];
+  nu[0] = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+  nub[1] = mx - f[0];
+  nub[2] = my - f[1];
+  nub[3] = f[3];
+  nub[0] = sqrt(nub[1] * nub[1] + nub[2] * nub[2] + nub[3] * nub[3]);
+  q[0] = m2sum(lp, nu, NULL);
+  q[1] = m2sum(b, lp, nu);
+  q[2] = m2sum(lm, nub, NULL);
+  q[3] = m2sum(bb, lm, nub);
+  /* d(P + nu)^2 / d nu_k = 2 (P_0 nu_k / E - P_k) for massless nu */
+  for (int k = 0; k < 3; ++k) {
+    M[0][k] = 2.0 * (lp[0] * nu[1 + k] / nu[0] - lp[1 + k]);
+    M[1][k] = 2.0 * ((b[0] + lp[0]) * nu[1 + k] / nu[0] - (b[1 + k] + lp[1 + k]));
+  }
+  M[0][3] = M[1][3] = 0.0;
+  /* nubar_x = mx - nu_x, nubar_y = my - nu_y: d/dnu_x, d/dnu_y carry a minus sign */
+  for (int k = 0; k < 2; ++k) {
+    M[2][k] = -2.0 * (lm[0] * nub[1 + k] / nub[0] - lm[1 + k]);
+    M[3][k] = -2.0 * ((bb[0] + lm[0]) * nub[1 + k] / nub[0] - (bb[1 + k] + lm[1 + k]));
+  }
+  M[2][2] = M[3][2] = 0.0;
+  M[2][3] = 2.0 * (lm[0] * nub[3] / nub[0] - lm[3]);
+  M[3][3] = 2.0 * ((bb[0] + lm[0]) * nub[3] / nub[0] - (bb[3] + lm[3]));
+}
+
+/* Solves M d = r (4x4, partial pivoting); returns 0 when singular. */
+static int solve4(double m[4][4], double* r) {
+  double a[4][5];
+  for (int i = 0; i < 4; ++i) {
+    for (int k = 0; k < 4; ++k) a[i][k] = m[i][k];
+    a[i][4] = r[i];
+  }
+  for (int c = 0; c < 4; ++c) {
+    int p = c;
+    for (int i = c + 1; i < 4; ++i)
+      if (fabs(a[i][c]) > fabs(a[p][c])) p = i;
+    if (a[p][c] == 0.0) return 0;
+    for (int k = 0; k < 5; ++k) {
+      const double t = a[c][k];
+      a[c][k] = a[p][k];
+      a[p][k] = t;
+    }
+    for (int i = c + 1; i < 4; ++i) {
+      const double f = a[i][c] / a[c][c];
+      for (int k = c; k < 5; ++k) a[i][k] -= f * a[c][k];
+    }
+  }
+  for (int c = 3; c >= 0; --c) {
+    double v = a[c][4];
+    for (int k = c + 1; k < 4; ++k) v -= a[c][k] * r[k];
+    r[c] = v / a[c][c];
+  }
+  return 1;
+}
+
 static double det4(double m[4][4]) {
   double a[4][4];
   memcpy(a, m, sizeof(a));
@@ -237,34 +309,28 @@ int ora_dilep_nu(const double* pb, const double* pbb, const double* plp, const d
     if (!(E > 0.0 && Eb > 0.0)) continue;
     sols[n][0] = x;
     sols[n][1] = y;
-    /* Jacobian d(q2_W+, q2_t, q2_W-, q2_tbar) / d(x, y, z, zbar), GeV units */
-    double M[4][4];
-    const double nv[3] = {x, y, zz}, nb[3] = {X, Y, zb};
-    for (int k = 0; k < 3; ++k) {
-      M[0][k] = 2.0 * (lp[0] * nv[k] / E - lp[1 + k]) * S;
-      M[1][k] = 2.0 * ((b[0] + lp[0]) * nv[k] / E - (b[1 + k] + lp[1 + k])) * S;
+    /* Newton steps on the original four equations with exactly massless neutrinos:
+     * the conic coefficients carry cancellations that the direct residual has not */
+    double f[4] = {x, y, zz, zb}, q[4], M[4][4], nv[4], nb[4];
+    const double tq[4] = {q2wp / S2, q2t / S2, q2wm / S2, q2tb / S2};
+    for (int it = 0; it < 3; ++it) {
+      forward(b, bb, lp, lm, mx, my, f, q, M, nv, nb);
+      double r[4];
+      for (int k = 0; k < 4; ++k) r[k] = q[k] - tq[k];
+      if (!solve4(M, r)) break;
+      for (int k = 0; k < 4; ++k) f[k] -= r[k];
     }
-    M[0][3] = M[1][3] = 0.0;
-    /* nubar_x = mx - x, nubar_y = my - y: d/dx, d/dy carry a minus sign */
-    for (int k = 0; k < 2; ++k) {
-      M[2][k] = -2.0 * (lm[0] * nb[k] / Eb - lm[1 + k]) * S;
-      M[3][k] = -2.0 * ((bb[0] + lm[0]) * nb[k] / Eb - (bb[1 + k] + lm[1 + k])) * S;
-    }
-    M[2][2] = M[3][2] = 0.0;
-    M[2][3] = 2.0 * (lm[0] * nb[2] / Eb - lm[3]) * S;
-    M[3][3] = 2.0 * ((bb[0] + lm[0]) * nb[2] / Eb - (bb[3] + lm[3])) * S;
-    const double det = det4(M);
+    forward(b, bb, lp, lm, mx, my, f, q, M, nv, nb);
+    /* Jacobian d(q2_W+, q2_t, q2_W-, q2_tbar) / d(nu_x, nu_y, nu_z, nubar_z), GeV units */
+    /* q2 in units of S^2 and momenta in units of S: each entry scales by S */
+    const double det = det4(M) * S2 * S2;
     if (det == 0.0) continue;
     double* no = nu_out + 4 * n;
     double* nbo = nub_out + 4 * n;
-    no[0] = E * S;
-    no[1] = x * S;
-    no[2] = y * S;
-    no[3] = zz * S;
-    nbo[0] = Eb * S;
-    nbo[1] = X * S;
-    nbo[2] = Y * S;
-    nbo[3] = zb * S;
+    for (int k = 0; k < 4; ++k) {
+      no[k] = nv[k] * S;
+      nbo[k] = nb[k] * S;
+    }
     jac_out[n] = 1.0 / fabs(det);
     ++n;
   }

@@ -20,8 +20,8 @@
 #include "oracle.h"
 #include "ora_dirac.h"
 
-int ora_dims(int kind) { return kind == 0 ? 2 : kind == 1 ? 4 : 7; }
-int ora_nperm(int kind) { return kind == 2 ? 24 : 1; }
+int ora_dims(int kind) { return kind == 0 ? 2 : kind == 1 ? 4 : kind == 2 ? 7 : 6; }
+int ora_nperm(int kind) { return kind == 2 ? 24 : kind == 3 ? 2 : 1; }
 
 double ora_pdf(const ora_process* P, int type, double x) {
   if (!(x > 0.0 && x < 1.0)) return 0.0;
@@ -316,13 +316,72 @@ static int states_tt(const ora_process* P, const ora_tf* T, const float* rec, in
   return n;
 }
 
+/* Dilepton ttbar (the final state of Sec. 3-4 without the Higgs): t -> b l+ nu,
+ * tbar -> bbar mu- nubar; leptons measured exactly (delta TFs), b-jet energies
+ * with the double-Gaussian TF. Variables: x0 -> E_b and x1 -> E_bbar (log-uniform
+ * over their jet windows), x2 -> q2_W+ and x3 -> q2_W- (Breit-Wigner maps over
+ * [0, s]), x4 -> q2_t over [q2_W+ + (b + l+)^2, s] and x5 -> q2_tbar over
+ * [q2_W- + (bbar + mu-)^2, s] (Breit-Wigner; the lower ends are where 2 b.nu = 0).
+ * The missing pT at each point is the visible imbalance -(l+ + mu- + b + bbar)_T
+ * (Sec. 4, hadron level), so the final state has zero total pT; the neutrinos
+ * follow from Eq. "dilepsolv" (ora_dilep_nu), one state per solution, each with
+ * its Jacobian. perm 0: object 2 is the b jet, object 3 the bbar; perm 1 the reverse. */
+static int states_ttdl(const ora_process* P, const ora_tf* T, const float* rec, int perm,
+                       const double* x, state_t* st) {
+  obj_t lp = get_obj(rec, 0), lm = get_obj(rec, 1);
+  obj_t jb = get_obj(rec, perm == 0 ? 2 : 3), jbb = get_obj(rec, perm == 0 ? 3 : 2);
+  const double s = P->sqrt_s * P->sqrt_s;
+  double lo, hi;
+  jet_window(P, T, jb.E, &lo, &hi);
+  double L = log(hi / lo);
+  const double Eb = lo * exp(x[0] * L), J0 = Eb * L;
+  jet_window(P, T, jbb.E, &lo, &hi);
+  L = log(hi / lo);
+  const double Ebb = lo * exp(x[1] * L), J1 = Ebb * L;
+  rv4 pb = massless(Eb, jb.n), pbb = massless(Ebb, jbb.n);
+  rv4 plp = massless(lp.E, lp.n), plm = massless(lm.E, lm.n);
+  double j2, j3, j4, j5;
+  const double q2wp = bw_map(0.0, s, P->mw, P->ww, x[2], &j2);
+  const double q2wm = bw_map(0.0, s, P->mw, P->ww, x[3], &j3);
+  const double lo_t = q2wp + 2.0 * rv_dot(pb, plp), lo_tb = q2wm + 2.0 * rv_dot(pbb, plm);
+  if (!(lo_t < s && lo_tb < s)) return 0;
+  const double q2t = bw_map(lo_t, s, P->mt, P->wt, x[4], &j4);
+  const double q2tb = bw_map(lo_tb, s, P->mt, P->wt, x[5], &j5);
+  const double metx = -(plp.v[1] + plm.v[1] + pb.v[1] + pbb.v[1]);
+  const double mety = -(plp.v[2] + plm.v[2] + pb.v[2] + pbb.v[2]);
+  double nu[4 * ORA_MAXSOL], nub[4 * ORA_MAXSOL], jnu[ORA_MAXSOL];
+  const int n = ora_dilep_nu(pb.v, pbb.v, plp.v, plm.v, metx, mety, q2wp, q2wm, q2t, q2tb, nu,
+                             nub, jnu);
+  for (int r = 0; r < n; ++r) {
+    state_t* S = &st[r];
+    S->nfs = 6;
+    S->lab[0] = pb;
+    S->lab[1] = plp;
+    S->lab[2] = rv(nu[4 * r], nu[4 * r + 1], nu[4 * r + 2], nu[4 * r + 3]);
+    S->lab[3] = pbb;
+    S->lab[4] = plm;
+    S->lab[5] = rv(nub[4 * r], nub[4 * r + 1], nub[4 * r + 2], nub[4 * r + 3]);
+    S->jac = J0 * J1 * j2 * j3 * j4 * j5 * jnu[r];
+    S->meas = 1.0;
+    for (int i = 0; i < 6; ++i) S->meas *= inv_ps(S->lab[i].v[0]);
+    S->meas *= Eb * Eb * jb.sin_theta * Ebb * Ebb * jbb.sin_theta;
+    S->tf = dgauss(T, jb.E, Eb) * dgauss(T, jbb.E, Ebb);
+    S->aux[0] = q2wp;
+    S->aux[1] = q2wm;
+    S->aux[2] = q2t;
+    S->aux[3] = q2tb;
+  }
+  return n;
+}
+
 static int build_states(const ora_process* P, const ora_tf* T, const float* rec, int perm,
                         const double* x, state_t* st) {
-  memset(st, 0, 2 * sizeof(state_t));
+  memset(st, 0, ORA_MAXSOL * sizeof(state_t));
   switch (P->kind) {
     case 0: return states_dy(P, T, rec, x, st);
     case 1: return states_w(P, T, rec, x, st);
     case 2: return states_tt(P, T, rec, perm, x, st);
+    case 3: return states_ttdl(P, T, rec, perm, x, st);
   }
   return 0;
 }
@@ -359,7 +418,7 @@ static double flavour_sum(const ora_process* P, const rv4* b, rv4 k1, rv4 k2, do
     int charge = rec[3] == 4.0f ? +1 : -1;
     sum += fq1 * fqb2 * ora_msq_w(P, charge, k1.v, k2.v, b[0].v, b[1].v);
     sum += fqb1 * fq2 * ora_msq_w(P, charge, k2.v, k1.v, b[0].v, b[1].v);
-  } else {
+  } else {   /* ttbar (kind 2) and dilepton ttbar (kind 3) */
     sum += fg1 * fg2 *
            ora_msq_ttbar(P, 0, k1.v, k2.v, b[0].v, b[1].v, b[2].v, b[3].v, b[4].v, b[5].v);
     for (int fl = 0; fl < 2; ++fl) { /* u ubar and d dbar */
@@ -369,6 +428,8 @@ static double flavour_sum(const ora_process* P, const rv4* b, rv4 k1, rv4 k2, do
              ora_msq_ttbar(P, 1, k2.v, k1.v, b[0].v, b[1].v, b[2].v, b[3].v, b[4].v, b[5].v);
     }
   }
+  /* W- -> mu- nubar is one channel where W- -> q qbar' counts 3 colours x 2 generations */
+  if (P->kind == 3) sum /= 6.0;
   return sum;
 }
 
@@ -393,9 +454,19 @@ static double state_weight(const ora_process* P, const state_t* S, const float* 
   return msq * flux * pow(TWO_PI, 4) * (2.0 / s) * S->meas * S->tf * S->jac;
 }
 
+/* PDF-weighted, flavour-summed |M|^2 at given parton-frame momenta (fs: the six
+ * final-state momenta in the process's lab order, k12: q1 then q2). */
+double ora_flavour_msq(const ora_process* P, const double* fs, const double* k12, double x1,
+                       double x2, const float* rec) {
+  rv4 b[6];
+  for (int i = 0; i < 6; ++i) b[i] = rv(fs[4 * i], fs[4 * i + 1], fs[4 * i + 2], fs[4 * i + 3]);
+  rv4 k1 = rv(k12[0], k12[1], k12[2], k12[3]), k2 = rv(k12[4], k12[5], k12[6], k12[7]);
+  return flavour_sum(P, b, k1, k2, x1, x2, rec);
+}
+
 double ora_integrand(const ora_process* P, const ora_tf* T, const float* rec, int perm,
                      const double* x) {
-  state_t st[2];
+  state_t st[ORA_MAXSOL];
   int n = build_states(P, T, rec, perm, x, st);
   double total = 0.0;
   for (int r = 0; r < n; ++r) total += state_weight(P, &st[r], rec, NULL);
@@ -404,7 +475,7 @@ double ora_integrand(const ora_process* P, const ora_tf* T, const float* rec, in
 
 int ora_integrand_roots(const ora_process* P, const ora_tf* T, const float* rec, int perm,
                         const double* x, double* w_root) {
-  state_t st[2];
+  state_t st[ORA_MAXSOL];
   int n = build_states(P, T, rec, perm, x, st);
   for (int r = 0; r < n; ++r) w_root[r] = state_weight(P, &st[r], rec, NULL);
   return n;
@@ -436,7 +507,7 @@ double ora_parton_ttbar(const ora_process* P, const float* rec, int bperm, doubl
 int ora_kinematics(const ora_process* P, const ora_tf* T, const float* rec, int perm,
                    const double* x, int root, double* fs, double* fs_lab, double* k12,
                    double* aux) {
-  state_t st[2];
+  state_t st[ORA_MAXSOL];
   int n = build_states(P, T, rec, perm, x, st);
   if (root >= n) return n;
   rv4 b[6], k1, k2;

@@ -64,6 +64,7 @@ typedef struct {
 #define ORA_NG 128      /* VEGAS bins per dimension */
 #define ORA_MAXD 8
 #define ORA_REC 32
+#define ORA_MAXSOL 4    /* kinematic solutions per point (dilepton ttbar: up to 4) */
 
 int ora_dims(int kind);
 int ora_nperm(int kind);
@@ -99,6 +100,8 @@ void ora_parton_batch(const ora_process* P, const float* recs, int64_t n, int n_
 
 /* The integrand's contribution of each kinematic root (neutrino p_z solution) at
  * point x; returns the number of roots (0..2). Their sum is ora_integrand. */
+double ora_flavour_msq(const ora_process* P, const double* fs, const double* k12, double x1,
+                       double x2, const float* rec);
 int ora_integrand_roots(const ora_process* P, const ora_tf* T, const float* rec, int perm,
                         const double* x, double* w_root);
 int ora_kinematics(const ora_process* P, const ora_tf* T, const float* rec, int perm,

@@ -94,6 +94,8 @@ def load():
     lib.ora_msq_w.argtypes = [P, C.c_int, _dp, _dp, _dp, _dp]
     lib.ora_msq_w.restype = C.c_double
     lib.ora_integrand_roots.argtypes = [P, T, fp, C.c_int, _dp, _dp]
+    lib.ora_flavour_msq.argtypes = [P, _dp, _dp, C.c_double, C.c_double, fp]
+    lib.ora_flavour_msq.restype = C.c_double
     lib.ora_discriminant.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, _dp, _dp]
     lib.ora_dilep_nu.argtypes = [_dp, _dp, _dp, _dp] + [C.c_double] * 6 + [_dp, _dp, _dp]
     lib.ora_strat_side.argtypes = [C.c_uint64, C.c_int, C.c_int]
@@ -214,9 +216,18 @@ def integrand_roots(P, T, rec, perm, x):
     """Per-root contributions of the integrand at x (a list of 0-2 floats)."""
     rec, rp = _rec_ptr(rec)
     x, xp = _d(x)
-    w = np.zeros(2)
+    w = np.zeros(4)
     n = load().ora_integrand_roots(C.byref(P), C.byref(T), rp, perm, xp, w.ctypes.data_as(_dp))
     return list(w[:n])
+
+
+def flavour_msq(P, fs, k12, x1, x2, rec):
+    """PDF-weighted, flavour-summed |M|^2 at the parton-frame momenta fs (6, 4) and
+    k12 (2, 4), with the record supplying the lepton charge where it matters."""
+    rec, rp = _rec_ptr(rec)
+    fs, fp_ = _d(np.asarray(fs).reshape(-1))
+    k12, kp = _d(np.asarray(k12).reshape(-1))
+    return load().ora_flavour_msq(C.byref(P), fp_, kp, x1, x2, rp)
 
 
 def pdf_q(P, t, x, Q):
