@@ -51,6 +51,11 @@ FP32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 FP32 lanes
 # kernels: k_main reads each item's grid and constants once (other CTAs of the item
 # hit L2), so its traffic grows with the items; k_parton_tt reads each record once.
 DRAM_BYTES_PER_ITEM_MAIN = {synth.PROC_W: 9008.0}
+# Dilepton ttbar: the neutrino solution runs in FP64, whose GB300 rate (nominal
+# 1.25 TFLOP/s) bounds the kernel; FP64 flops (DADD, DMUL = 1; DFMA = 2) per
+# evaluation from ncu instruction counters.
+FP64_FLOPS_PER_EVAL = {}
+FP64_PEAK_TFLOPS = 1.25
 DRAM_BYTES_PER_PARTON_EVENT = 128.2
 
 # FP32 flops of the parton-level kernel per event (both b-quark assignments; FADD,
@@ -68,6 +73,9 @@ WORKLOAD_NAMES = {
     "dy": "Drell-Yan Z/photon->mu mu, 2-dim integral, 64 events x 2^16 evaluations/event",
     "ttbar": "semileptonic ttbar (gg + qqbar, spin-correlated helicity amplitudes), 7-dim "
              "integral x 24 jet permutations, 4096 events x 2^22 evaluations/event",
+    "ttdl": "dilepton ttbar (b l+ nu bbar mu- nubar; both neutrinos from the four "
+            "virtualities, up to 4 solutions, FP64 solve), 6-dim integral x 2 b-jet "
+            "assignments, 1024 events x 2^18 evaluations/event",
 }
 
 
@@ -77,7 +85,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["w", "dy", "ttbar", "mix", "flow", "parton"],
+    ap.add_argument("--workload", choices=["w", "dy", "ttbar", "mix", "flow", "parton", "ttdl"],
                     default="w")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the events-to-1%% leg")
     ap.add_argument("--strat", type=int, default=0,
@@ -197,7 +205,7 @@ def cpu_baseline(kind, seed):
     from oracle import oracle as O
     # (events, evaluations per item): about 10 s of work on 16 Grace cores
     n_ev, n_pts = {synth.PROC_W: (64, 1 << 16), synth.PROC_DY: (16, 1 << 15),
-                   synth.PROC_TTBAR: (2, 1 << 10)}[kind]
+                   synth.PROC_TTBAR: (2, 1 << 10), synth.PROC_TTBAR_DILEP: (16, 1 << 12)}[kind]
     n_perm = synth.NPERM[kind]
     recs = synth.gen_events(kind, n_ev, seed)
     P = O.process(kind, synth.DEFAULT_PROCESS)
@@ -436,13 +444,21 @@ def run_ours(args):
         t_main = statistics.mean(main_ms) * 1e-3
         achieved = fpe * n_ev * n_perm * n_main / t_main / 1e12 if fpe else None
         dpi = DRAM_BYTES_PER_ITEM_MAIN.get(kind)
+        if kind == synth.PROC_TTBAR_DILEP:
+            fpe = None
+            f64 = FP64_FLOPS_PER_EVAL.get(kind)
+            peak = FP64_PEAK_TFLOPS
+            achieved = f64 * n_ev * n_perm * n_main / t_main / 1e12 if f64 else None
         roof = {"bound": "alu", "kernel": "k_main (frozen-grid sampling)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None,
                 "traffic": (dpi * n_ev * n_perm
                             if dpi and not args.pdf_grid and not args.strat else None),
-                "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
-                               f"{max_mhz:.0f} MHz max SM clock",
+                "peak_source": (f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                f"{max_mhz:.0f} MHz max SM clock"
+                                if kind != synth.PROC_TTBAR_DILEP else
+                                "nominal GB300 FP64 rate (the FP64 neutrino solution bounds "
+                                "this kernel)"),
                 "flops_per_eval": fpe,
                 "flops_executed_per_eval": FLOPS_EXECUTED_PER_EVAL.get(kind),
                 "frac_executed": (FLOPS_EXECUTED_PER_EVAL[kind] * n_ev * n_perm * n_main / t_main / 1e12

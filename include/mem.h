@@ -47,7 +47,14 @@ typedef enum {
 enum {
   MEM_PROC_DY = 0,    /* q qbar -> photon/Z -> mu- mu+ ; 2 integration dims, 1 permutation */
   MEM_PROC_W = 1,     /* u dbar -> W+ -> e+ nu (or W-) ; 4 dims, 1 permutation */
-  MEM_PROC_TTBAR = 2  /* gg, q qbar -> t tbar -> b l+ nu bbar d ubar ; 7 dims, 24 jet permutations */
+  MEM_PROC_TTBAR = 2, /* gg, q qbar -> t tbar -> b l+ nu bbar d ubar ; 7 dims, 24 jet permutations */
+  MEM_PROC_TTBAR_DILEP = 3 /* gg, q qbar -> t tbar -> b l+ nu bbar mu- nubar (Sec. 3-4, Eq.
+                            * "dilepsolv": both neutrinos from the four virtualities and the
+                            * visible pT imbalance, up to 4 solutions per point); 6 dims, 2 b-jet
+                            * assignments. Records: objects 0 l+ (kind 4), 1 mu- (kind 1), 2 and 3
+                            * the b jets (kind 5); leptons and jet directions exact, jet energies
+                            * with the double Gaussian. mem_integrate, mem_integrate_noalloc and
+                            * mem_eval_points only (batched and learned-sampler calls reject it). */
 };
 
 typedef struct mem_process mem_process; /* opaque, library-owned */

@@ -58,10 +58,17 @@ uint32_t strat_side(uint64_t n, int d, int k) {
   }
 }
 
-int dims_of(int kind) { return kind == PROC_DY ? 2 : kind == PROC_W ? 4 : kind == PROC_TTBAR ? 7 : -1; }
-int nperm_of(int kind) { return kind == PROC_TTBAR ? 24 : (kind == PROC_DY || kind == PROC_W) ? 1 : -1; }
+int dims_of(int kind) {
+  return kind == PROC_DY ? 2 : kind == PROC_W ? 4 : kind == PROC_TTBAR ? 7 : kind == PROC_TTDL ? 6 : -1;
+}
+int nperm_of(int kind) {
+  return kind == PROC_TTBAR ? 24 : kind == PROC_TTDL ? 2 : (kind == PROC_DY || kind == PROC_W) ? 1 : -1;
+}
 uint32_t chunk_points(int kind) {  // points of one frozen-grid CTA: THREADS x points per thread
-  return THREADS * (uint32_t)(kind == PROC_DY ? PPT_DY : kind == PROC_W ? PPT_W : PPT_TT);
+  return THREADS * (uint32_t)(kind == PROC_DY ? PPT_DY
+                              : kind == PROC_W ? PPT_W
+                              : kind == PROC_TTDL ? PPT_DL
+                                                  : PPT_TT);
 }
 
 cudaError_t launch_integrate(int kind, const IntegrateArgs& a, cudaStream_t st) {
@@ -69,12 +76,16 @@ cudaError_t launch_integrate(int kind, const IntegrateArgs& a, cudaStream_t st) 
     case PROC_DY: return launch_integrate_dy(a, st);
     case PROC_W: return launch_integrate_w(a, st);
     case PROC_TTBAR: return launch_integrate_tt(a, st);
+    case PROC_TTDL: return launch_integrate_ttdl(a, st);
   }
   return cudaErrorInvalidValue;
 }
 
 size_t cache_size(int kind) {
-  return kind == PROC_DY ? cache_size_dy() : kind == PROC_W ? cache_size_w() : cache_size_tt();
+  return kind == PROC_DY ? cache_size_dy()
+         : kind == PROC_W ? cache_size_w()
+         : kind == PROC_TTDL ? cache_size_ttdl()
+                             : cache_size_tt();
 }
 
 cudaError_t launch_eval(int kind, const EvalArgs& a, cudaStream_t st) {
@@ -82,6 +93,7 @@ cudaError_t launch_eval(int kind, const EvalArgs& a, cudaStream_t st) {
     case PROC_DY: return launch_eval_dy(a, st);
     case PROC_W: return launch_eval_w(a, st);
     case PROC_TTBAR: return launch_eval_tt(a, st);
+    case PROC_TTDL: return launch_eval_ttdl(a, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -282,11 +294,13 @@ namespace {
 
 mem_status check_tf(const mem_tf_desc* tf, int kind) {
   if (!tf) return fail(MEM_ERR_INVALID_ARG, "tf is NULL");
-  if (kind != PROC_TTBAR && !(tf->lep_rel > 0 && tf->window_k > 0 && tf->lep_rel * tf->window_k < 1))
+  // ttbar processes: leptons measured exactly; dilepton ttbar: MET is the visible imbalance
+  if ((kind == PROC_DY || kind == PROC_W) &&
+      !(tf->lep_rel > 0 && tf->window_k > 0 && tf->lep_rel * tf->window_k < 1))
     return fail(MEM_ERR_INVALID_ARG, "lepton TF needs lep_rel > 0, window_k > 0, lep_rel*window_k < 1");
-  if (kind != PROC_DY && !(tf->met_sigma > 0 && tf->met_box_k > 0))
+  if ((kind == PROC_W || kind == PROC_TTBAR) && !(tf->met_sigma > 0 && tf->met_box_k > 0))
     return fail(MEM_ERR_INVALID_ARG, "MET TF needs met_sigma > 0 and met_box_k > 0");
-  if (kind == PROC_TTBAR &&
+  if ((kind == PROC_TTBAR || kind == PROC_TTDL) &&
       !(tf->jet_core > 0 && tf->jet_tail > 0 && tf->jet_tail_w >= 0 && tf->jet_tail_w <= 1 &&
         tf->jet_lo_div > 1 && tf->jet_hi_mul > 1))
     return fail(MEM_ERR_INVALID_ARG, "invalid jet TF parameters");

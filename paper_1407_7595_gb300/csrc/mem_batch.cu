@@ -211,6 +211,9 @@ extern "C" mem_status mem_integrate_batch(int32_t n_groups, const mem_events* co
     if (ev->kind != pr->desc.kind)
       return bfail(MEM_ERR_INVALID_ARG, "group " + std::to_string(g) + ": process kind mismatch");
     const int kind = pr->desc.kind, d = dims_of(kind), np = nperm_of(kind);
+    if (kind == PROC_TTDL)
+      return bfail(MEM_ERR_INVALID_ARG, "group " + std::to_string(g) +
+                                            ": dilepton ttbar is integrated by mem_integrate only");
     const mem_tf_desc& T = *tfs[g];
     if (kind != PROC_TTBAR && !(T.lep_rel > 0 && T.window_k > 0 && T.lep_rel * T.window_k < 1))
       return bfail(MEM_ERR_INVALID_ARG, "lepton TF parameters invalid");

@@ -12,4 +12,8 @@ constexpr int PPT_TT = 16;       // frozen-grid points per thread (ttbar): 4,096
 constexpr int MINB_TT = 2;       // adaptation and round kernels: <= 128 registers, no spills
 constexpr int MINB_TT_MAIN = 3;  // frozen-grid kernel: <= 80 registers (20 bytes of spill), 24 warps/SM
 
+constexpr int PPT_DL = 16;       // frozen-grid points per thread (dilepton ttbar): 4,096 per CTA
+constexpr int MINB_DL = 1;       // adaptation kernel: one CTA of 256 threads per SM
+constexpr int MINB_DL_MAIN = 2;  // frozen-grid kernel: <= 128 registers
+
 }  // namespace mem

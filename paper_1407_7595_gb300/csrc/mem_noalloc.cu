@@ -74,10 +74,15 @@ extern "C" mem_status mem_integrate_noalloc(const mem_process_desc* desc, const 
   for (int t = 0; t < 3; ++t)
     if (!(desc->pdf_A[t] > 0.0) || !std::isfinite(desc->pdf_a[t]) || !(desc->pdf_b[t] >= 0.0))
       return bad("PDF parameters need A > 0, finite a, b >= 0");
-  if (kind != PROC_TTBAR && !(tf->lep_rel > 0 && tf->window_k > 0 && tf->lep_rel * tf->window_k < 1))
+  if ((kind == PROC_DY || kind == PROC_W) &&
+      !(tf->lep_rel > 0 && tf->window_k > 0 && tf->lep_rel * tf->window_k < 1))
     return bad("lepton TF needs lep_rel > 0, window_k > 0, lep_rel*window_k < 1");
-  if (kind != PROC_DY && !(tf->met_sigma > 0 && tf->met_box_k > 0))
+  if ((kind == PROC_W || kind == PROC_TTBAR) && !(tf->met_sigma > 0 && tf->met_box_k > 0))
     return bad("MET TF needs met_sigma > 0 and met_box_k > 0");
+  if ((kind == PROC_TTBAR || kind == PROC_TTDL) &&
+      !(tf->jet_core > 0 && tf->jet_tail > 0 && tf->jet_tail_w >= 0 && tf->jet_tail_w <= 1 &&
+        tf->jet_lo_div > 1 && tf->jet_hi_mul > 1))
+    return bad("invalid jet TF parameters");
   if (n_events < 1 || n_events > ((int64_t)1 << 31)) return bad("n_events out of range");
   if (n_points > ((uint64_t)1 << 32)) return bad("n_points above 2^32 per item");
   // default plan of mem_integrate: 5 adaptation iterations of min(2^14, n/8) points

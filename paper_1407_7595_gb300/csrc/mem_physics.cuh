@@ -13,7 +13,7 @@
 
 namespace mem {
 
-enum { PROC_DY = 0, PROC_W = 1, PROC_TTBAR = 2 };
+enum { PROC_DY = 0, PROC_W = 1, PROC_TTBAR = 2, PROC_TTDL = 3 };
 
 // ttbar weights are carried in FP32 multiplied by 2^40 (an exact power of two,
 // divided out of the FP64 prefactor) so that products of small factors in

@@ -205,7 +205,8 @@ struct TTCache {
   int ok;
 };
 
-__device__ __forceinline__ float dgauss_g(const TTCache& c, float Em, float E) {
+template <class CC>   // any cache with the double-Gaussian constants below
+__device__ __forceinline__ float dgauss_g(const CC& c, float Em, float E) {
   // sum_k (w_k / c_k) exp(-z_k^2/2), z_k = (Em/E - 1)/c_k
   const float r = fmaf(Em, 1.f / E, -1.f);
   const float z1 = r * c.inv_core, z2 = r * c.inv_tail;

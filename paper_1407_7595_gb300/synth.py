@@ -70,8 +70,12 @@ DEFAULT_TF = {
                  "met_sigma": 15.0, "met_box_k": 4.0},
 }
 
-DIMS = {PROC_DY: 2, PROC_W: 4, PROC_TTBAR: 7}
-NPERM = {PROC_DY: 1, PROC_W: 1, PROC_TTBAR: 24}
+PROC_TTBAR_DILEP = 3
+# dilepton ttbar: leptons measured exactly, b jets as in semileptonic ttbar
+DEFAULT_TF[PROC_TTBAR_DILEP] = dict(DEFAULT_TF[PROC_TTBAR])
+
+DIMS = {PROC_DY: 2, PROC_W: 4, PROC_TTBAR: 7, PROC_TTBAR_DILEP: 6}
+NPERM = {PROC_DY: 1, PROC_W: 1, PROC_TTBAR: 24, PROC_TTBAR_DILEP: 2}
 
 # The five workloads: (process, events, points per event, base seed).
 SEED_BASE = 0x4D454D00
@@ -83,6 +87,8 @@ WORKLOADS = {
     "flow": dict(proc=PROC_TTBAR, n_events=4096, n_points=1 << 22, seed=SEED_BASE + 4),
     # parton-level ttbar (Sec. 4): no integration, one weight per b-quark assignment
     "parton": dict(proc=PROC_TTBAR, n_events=1 << 20, n_points=0, seed=SEED_BASE + 5),
+    # dilepton ttbar (Sec. 3-4 hadron level without the Higgs): 6 dims x 2 b assignments
+    "ttdl": dict(proc=3, n_events=1024, n_points=1 << 18, seed=SEED_BASE + 6),
 }
 
 
@@ -379,9 +385,6 @@ def gen_ttbar_parton(n, seed):
     return out
 
 
-PROC_TTBAR_DILEP = 3
-
-
 def gen_ttbar_dilep(n, seed, tf=None, truth=False):
     """Dilepton ttbar events, t -> b l+ nu, tbar -> bbar mu- nubar (the final state of
     the paper's hadron-level analysis without the Higgs, Sec. 3-4): the production
@@ -456,7 +459,8 @@ def gen_ttbar_dilep(n, seed, tf=None, truth=False):
     return (out, tr) if truth else out
 
 
-GENERATORS = {PROC_DY: gen_dy, PROC_W: gen_w, PROC_TTBAR: gen_ttbar}
+GENERATORS = {PROC_DY: gen_dy, PROC_W: gen_w, PROC_TTBAR: gen_ttbar,
+              PROC_TTBAR_DILEP: gen_ttbar_dilep}
 
 
 def gen_events(proc, n, seed):
