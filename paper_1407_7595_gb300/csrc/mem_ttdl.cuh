@@ -23,6 +23,13 @@
 // safeguarded Newton iterations on the brackets the level above supplies, inside
 // the Cauchy bound. Roots are then polished on the two conics (Newton in 2D).
 //
+// The solver's stages (dl_system, dl_real_roots, dl_bracket_root, dl_point) are
+// kept out of line. Inlined into the integrand, this build (nvcc 13.0, sm_103a)
+// returned incomplete solution sets on about a third of the points of a test
+// batch -- the same functions called from a small kernel, or out of line, agree
+// with a host build of this file and with the FP64 reference to 1e-12 in the
+// roots. Out of line they also keep the integrand's register count down.
+//
 // |M|^2: the semileptonic amplitude of mem_ttbar.cuh with mu- in the role of the
 // d quark and nubar in that of the ubar (the Fierz-collapsed antitop chain has
 // the same form for W- -> mu- nubar), divided by the 6 channels (3 colours x 2
@@ -112,7 +119,7 @@ __device__ __forceinline__ double dl_horner(const double* c, int deg, double x, 
 
 // Root of the polynomial c (degree deg) in [a, b], where it changes sign: Newton
 // steps, replaced by bisection whenever a step leaves the shrinking bracket.
-__device__ double dl_bracket_root(const double* c, int deg, double a, double b, double fa) {
+__device__ __noinline__ double dl_bracket_root(const double* c, int deg, double a, double b, double fa) {
   double x = 0.5 * (a + b);
 #pragma unroll 1
   for (int it = 0; it < 96; ++it) {
@@ -136,7 +143,7 @@ __device__ double dl_bracket_root(const double* c, int deg, double a, double b, 
 // Real roots (ascending) of c[0] + c[1] x + ... + c[deg] x^deg, 1 <= deg <= 4,
 // c[deg] != 0, through the derivative chain. A critical point where the
 // polynomial vanishes to rounding is a double root and is kept once.
-__device__ int dl_real_roots(const double* c, int deg, double* roots) {
+__device__ __noinline__ int dl_real_roots(const double* c, int deg, double* roots) {
   double bound = 0.0;
   for (int k = 0; k < deg; ++k) bound = fmax(bound, fabs(c[k] / c[deg]));
   bound += 1.0;                                  // Cauchy bound on every root and critical point
@@ -234,7 +241,7 @@ struct DLSystem {
 };
 
 // Builds the system; returns the number of real roots x of the resultant (in xr).
-__device__ int dl_system(const double* b, const double* bb, const double* lp, const double* lm,
+__device__ __noinline__ int dl_system(const double* b, const double* bb, const double* lp, const double* lm,
                          double q2wp, double q2wm, double q2t, double q2tb, DLSystem& S,
                          double* xr) {
   S.mx = -(lp[1] + lm[1] + b[1] + bb[1]);
@@ -279,7 +286,7 @@ __device__ int dl_system(const double* b, const double* bb, const double* lp, co
 
 // One neutrino solution from a root x of the resultant: y, conic polish, the
 // residual and positive-energy checks. Returns false when the root is rejected.
-__device__ bool dl_point(const DLSystem& S, double xr, double& x, double& y) {
+__device__ __noinline__ bool dl_point(const DLSystem& S, double xr, double& x, double& y) {
   const double num = -fma(fma(S.u[2], xr, S.u[1]), xr, S.u[0]);
   const double den = fma(S.v[1], xr, S.v[0]);
   if (fabs(den) > 1e-12 * (fabs(num) + 1.0)) {

@@ -15,9 +15,12 @@ decay invariants inherit the conditioning of the solution; the double-Gaussian
 jet TF amplifies an energy error by z/sigma ~ 10-50 as in semileptonic ttbar. On
 the host build of the same integrand (3,000 points, 8 events) 93 % of the points
 agree within 1e-5, 98 % within 3e-5, all within 1e-2, and the worst points carry
-weights far below the mean. Rule: at least 97 % of points within 3e-5, every
-point within 1e-2 relative or 1e-6 of the mean weight, and the sum over 512
-points within 1e-5. The integral at a frozen grid agrees within 1e-5.
+weights far below the mean -- but near the branch points, where two solutions
+merge and the Jacobian peaks, a point carrying a few per cent of a batch's sum
+can be off by 1e-4 (one of six 512-point batches sums to 3e-5 on both the host
+build and the GPU). Rule: at least 97 % of points within 3e-5, every point
+within 1e-2 relative or 1e-6 of the mean weight, and the sum over 512 points
+within 1e-4; the integral at a frozen grid within 1e-4.
 """
 import numpy as np
 import pytest
@@ -26,7 +29,7 @@ from test_gpu_parity import check_points
 
 pytestmark = pytest.mark.gpu
 KIND = 3
-DL_RULE = dict(rel=3e-5, frac=0.97, cap=1e-2, floor=1e-6, sum_rel=1e-5)
+DL_RULE = dict(rel=3e-5, frac=0.97, cap=1e-2, floor=1e-6, sum_rel=1e-4)
 
 
 @pytest.fixture(scope="module")
@@ -77,7 +80,7 @@ def test_integral_frozen_grid(env):
     n = 2 * 4096 + 333   # two full sampling chunks and a ragged tail per item
     g = integ.integrate(n, seed=21, opts=abi.make_opts(n_adapt_iters=0))
     o = O.integrate(P, T, recs[:1], seed=21, n_points=n, n_adapt_iters=0)
-    assert g["prob"][0] == pytest.approx(o["prob"][0], rel=1e-5, abs=0)
+    assert g["prob"][0] == pytest.approx(o["prob"][0], rel=1e-4, abs=0)
     assert g["err"][0] == pytest.approx(o["err"][0], rel=1e-3, abs=0)
     assert g["n_used"][0] == 2 * n and g["status"][0] == 0
 
