@@ -117,9 +117,14 @@ __device__ __forceinline__ double dl_horner(const double* c, int deg, double x, 
   return p;
 }
 
-// Root of the polynomial c (degree deg) in [a, b], where it changes sign: Newton
-// steps, replaced by bisection whenever a step leaves the shrinking bracket.
-__device__ __noinline__ double dl_bracket_root(const double* c, int deg, double a, double b, double fa) {
+// Root of the polynomial c (degree deg) in [a, b], where it changes sign, to
+// |step| <= tol (1 + |x|): Newton steps, replaced by bisection whenever a step
+// leaves the shrinking bracket. The step divides by an FP32 reciprocal of the
+// derivative (FP64 division costs several FP64 instructions on this part): the
+// iteration then contracts by ~1e-7 per step near the root instead of
+// quadratically, which from a Newton-accurate iterate is the same one step.
+__device__ __noinline__ double dl_bracket_root(const double* c, int deg, double a, double b,
+                                               double fa, double tol) {
   double x = 0.5 * (a + b);
 #pragma unroll 1
   for (int it = 0; it < 96; ++it) {
@@ -132,9 +137,13 @@ __device__ __noinline__ double dl_bracket_root(const double* c, int deg, double 
     } else {
       b = x;
     }
-    double xn = x - f / dp;
-    if (!(xn > a && xn < b)) xn = 0.5 * (a + b);
-    if (fabs(xn - x) <= 1e-15 * (1.0 + fabs(x))) return xn;
+    const float dpf = fabsf((float)dp);
+    double xn = 0.5 * (a + b);   // bisection unless the Newton step stays in the bracket
+    if (dpf > 1e-30f && dpf < 1e30f) {
+      const double t = x - f * (double)(1.f / (float)dp);
+      if (t > a && t < b) xn = t;
+    }
+    if (fabs(xn - x) <= tol * (1.0 + fabs(x))) return xn;
     x = xn;
   }
   return x;
@@ -145,7 +154,8 @@ __device__ __noinline__ double dl_bracket_root(const double* c, int deg, double 
 // polynomial vanishes to rounding is a double root and is kept once.
 __device__ __noinline__ int dl_real_roots(const double* c, int deg, double* roots) {
   double bound = 0.0;
-  for (int k = 0; k < deg; ++k) bound = fmax(bound, fabs(c[k] / c[deg]));
+  const double ilead = 1.0 / c[deg];
+  for (int k = 0; k < deg; ++k) bound = fmax(bound, fabs(c[k] * ilead));
   bound += 1.0;                                  // Cauchy bound on every root and critical point
   double crit[4];                                // roots of the level above
   int ncrit = 0;
@@ -161,6 +171,29 @@ __device__ __noinline__ int dl_real_roots(const double* c, int deg, double* root
     }
     double out[4];
     int n = 0;
+    if (m > 0 && dm <= 2) {
+      // critical points of a linear or quadratic level in closed form (stable
+      // quadratic formula); they lie inside the bound (Gauss-Lucas)
+      if (dm == 1) {
+        out[n++] = -d[0] / d[1];
+      } else {
+        const double disc = d[1] * d[1] - 4.0 * d[2] * d[0];
+        if (disc >= 0.0) {
+          const double q = -0.5 * (d[1] + copysign(sqrt(disc), d[1]));
+          double r1 = q / d[2], r2 = q != 0.0 ? d[0] / q : r1;
+          if (r1 > r2) {
+            const double t = r1;
+            r1 = r2;
+            r2 = t;
+          }
+          out[n++] = r1;
+          if (r2 > r1) out[n++] = r2;
+        }
+      }
+      ncrit = n;
+      for (int k = 0; k < n; ++k) crit[k] = out[k];
+      continue;
+    }
     double a = -bound, dpa;
     double fa = dl_horner(d, dm, a, dpa);
     for (int i = 0; i <= ncrit; ++i) {
@@ -168,7 +201,8 @@ __device__ __noinline__ int dl_real_roots(const double* c, int deg, double* root
       double dpb;
       const double fb = dl_horner(d, dm, b, dpb);
       if (b > a && ((fa < 0.0 && fb > 0.0) || (fa > 0.0 && fb < 0.0))) {
-        out[n++] = dl_bracket_root(d, dm, a, b, fa);
+        // critical points only need to separate the next level's roots
+        out[n++] = dl_bracket_root(d, dm, a, b, fa, m == 0 ? 1e-15 : 1e-12);
       } else if (i < ncrit && (n == 0 || out[n - 1] < b)) {
         // touches zero at the critical point: |p| at the rounding level of its terms
         double mag = 0.0, pw = 1.0;
@@ -195,7 +229,8 @@ __device__ __forceinline__ void dl_polish(const DLConic& p, const DLConic& q, do
     const double gx = fma(2.0 * q.xx, x, fma(q.xy, y, q.x1)), gy = fma(q.xy, x, fma(2.0 * q.yy, y, q.y1));
     const double det = fx * gy - fy * gx;
     if (det == 0.0) return;
-    const double dx = (f * gy - g * fy) / det, dy = (g * fx - f * gx) / det;
+    const double id = 1.0 / det;
+    const double dx = (f * gy - g * fy) * id, dy = (g * fx - f * gx) * id;
     x -= dx;
     y -= dy;
     if (fabs(dx) + fabs(dy) < 1e-14 * (1.0 + fabs(x) + fabs(y))) return;
