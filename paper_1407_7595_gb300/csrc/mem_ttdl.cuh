@@ -11,17 +11,20 @@
 // and that imbalance (Eq. "dilepsolv"): up to four solutions, each weighted by
 // 1 / |det d(q^2_W+, q^2_t, q^2_W-, q^2_tbar) / d(nu_x, nu_y, nu_z, nubar_z)|.
 //
-// Precision: the neutrino solution runs in FP64. Eliminating the neutrino energies
-// and p_z leaves two conics in (nu_x, nu_y) whose resultant is a quartic; its
-// coefficients are products of four conic coefficients and cancel by several
-// orders of magnitude, beyond FP32's seven digits. Everything else (maps, transfer
-// functions, amplitudes, PDFs) is FP32 as in the other processes.
+// Precision: the neutrino solution's algebra runs in FP64. Eliminating the neutrino
+// energies and p_z leaves two conics in (nu_x, nu_y) whose resultant is a quartic;
+// its coefficients are products of four conic coefficients and cancel by several
+// orders of magnitude, beyond FP32's seven digits. The iterative root search runs
+// in FP32 wherever its result is only a bracket or a starting point (FP64 is ~1/64
+// of the FP32 rate on this part). Everything else (maps, transfer functions,
+// amplitudes, PDFs) is FP32 as in the other processes.
 //
 // Real roots of the quartic: every real root of a polynomial lies between two
 // consecutive real roots of its derivative (Rolle), so the roots of the linear,
-// quadratic, cubic and quartic derivative chain are found in turn, each level by
-// safeguarded Newton iterations on the brackets the level above supplies, inside
-// the Cauchy bound. Roots are then polished on the two conics (Newton in 2D).
+// quadratic and cubic derivatives (in FP32: they only separate roots) bracket
+// those of the quartic, whose signs at the bracket ends are taken in FP64; each
+// root is then located in FP32 and finished by FP64 Newton steps. Roots are then
+// polished on the two conics (Newton in 2D, FP64).
 //
 // The solver's stages (dl_system, dl_real_roots, dl_bracket_root, dl_point) are
 // kept out of line. Inlined into the integrand, this build (nvcc 13.0, sm_103a)
@@ -107,8 +110,9 @@ __device__ __forceinline__ DLConic dl_mirror(const DLConic& q, double mx, double
   return r;
 }
 
-__device__ __forceinline__ double dl_horner(const double* c, int deg, double x, double& dp) {
-  double p = c[deg], d = 0.0;
+template <class T>
+__device__ __forceinline__ T dl_horner(const T* c, int deg, T x, T& dp) {
+  T p = c[deg], d = T(0);
   for (int k = deg - 1; k >= 0; --k) {
     d = fma(d, x, p);
     p = fma(p, x, c[k]);
@@ -117,15 +121,35 @@ __device__ __forceinline__ double dl_horner(const double* c, int deg, double x, 
   return p;
 }
 
-// Root of the polynomial c (degree deg) in [a, b], where it changes sign, to
-// |step| <= tol (1 + |x|): Newton steps, replaced by bisection whenever a step
-// leaves the shrinking bracket. The step divides by an FP32 reciprocal of the
-// derivative (FP64 division costs several FP64 instructions on this part): the
-// iteration then contracts by ~1e-7 per step near the root instead of
-// quadratically, which from a Newton-accurate iterate is the same one step.
+// FP32 root of the polynomial c (degree deg) in [a, b], where it changes sign
+// (only the sign of fa is used): Newton steps, replaced by bisection whenever a
+// step leaves the shrinking bracket, to FP32 resolution.
+__device__ __noinline__ float dl_bracket32(const float* c, int deg, float a, float b, float fa) {
+  float x = 0.5f * (a + b);
+#pragma unroll 1
+  for (int it = 0; it < 64; ++it) {
+    float dp;
+    const float f = dl_horner(c, deg, x, dp);
+    if (f == 0.f) return x;
+    if ((f < 0.f) == (fa < 0.f)) a = x;
+    else b = x;
+    float xn = x - f / dp;
+    if (!(xn > a && xn < b)) xn = 0.5f * (a + b);
+    if (fabsf(xn - x) <= 2e-7f * (1.f + fabsf(x))) return xn;
+    x = xn;
+  }
+  return x;
+}
+
+// FP64 root of c in [a, b] (a sign change, fa = c(a)) from the start x0, to
+// |step| <= tol (1 + |x|): Newton steps that divide by an FP32 reciprocal of the
+// derivative (FP64 division costs several FP64 instructions on this part; near
+// the root the iteration then contracts by ~1e-7 per step, which from an
+// FP32-accurate start is the same two steps), bisection whenever a step leaves
+// the shrinking bracket.
 __device__ __noinline__ double dl_bracket_root(const double* c, int deg, double a, double b,
-                                               double fa, double tol) {
-  double x = 0.5 * (a + b);
+                                               double fa, double x0, double tol) {
+  double x = (x0 > a && x0 < b) ? x0 : 0.5 * (a + b);
 #pragma unroll 1
   for (int it = 0; it < 96; ++it) {
     double dp;
@@ -150,74 +174,95 @@ __device__ __noinline__ double dl_bracket_root(const double* c, int deg, double 
 }
 
 // Real roots (ascending) of c[0] + c[1] x + ... + c[deg] x^deg, 1 <= deg <= 4,
-// c[deg] != 0, through the derivative chain. A critical point where the
-// polynomial vanishes to rounding is a double root and is kept once.
+// c[deg] != 0. The critical points -- the real roots of the derivative chain
+// (linear, quadratic in closed form, cubic by bracketed Newton) -- are found in
+// FP32 on the monic polynomial: they only separate the roots. Which intervals
+// between them hold a root is decided by the signs of the FP64 polynomial at
+// their ends (at a critical point the polynomial is flat, so an FP32-accurate
+// location gives the exact sign); each root is located in FP32 and finished by
+// FP64 Newton steps inside its bracket. A critical point where the polynomial
+// vanishes to rounding is a double root and is kept once.
 __device__ __noinline__ int dl_real_roots(const double* c, int deg, double* roots) {
-  double bound = 0.0;
   const double ilead = 1.0 / c[deg];
-  for (int k = 0; k < deg; ++k) bound = fmax(bound, fabs(c[k] * ilead));
-  bound += 1.0;                                  // Cauchy bound on every root and critical point
-  double crit[4];                                // roots of the level above
+  float cf[5];
+  float bound = 0.f;
+  for (int k = 0; k < deg; ++k) {
+    cf[k] = (float)(c[k] * ilead);
+    bound = fmaxf(bound, fabsf(cf[k]));
+  }
+  cf[deg] = 1.f;
+  bound += 1.f;   // Cauchy bound on every root and critical point (Gauss-Lucas)
+  float crit[3];
   int ncrit = 0;
 #pragma unroll 1
-  for (int m = deg - 1; m >= 0; --m) {
-    // level m: the m-th derivative, degree deg - m
+  for (int m = deg - 1; m >= 1; --m) {
+    // level m: the m-th derivative, degree deg - m <= 3
     const int dm = deg - m;
-    double d[5];
+    float d[4];
     for (int k = 0; k <= dm; ++k) {
-      double f = c[k + m];
-      for (int j = k + 1; j <= k + m; ++j) f *= (double)j;   // (k+m)! / k!
+      float f = cf[k + m];
+      for (int j = k + 1; j <= k + m; ++j) f *= (float)j;   // (k+m)! / k!
       d[k] = f;
     }
-    double out[4];
+    float out[3];
     int n = 0;
-    if (m > 0 && dm <= 2) {
-      // critical points of a linear or quadratic level in closed form (stable
-      // quadratic formula); they lie inside the bound (Gauss-Lucas)
-      if (dm == 1) {
-        out[n++] = -d[0] / d[1];
-      } else {
-        const double disc = d[1] * d[1] - 4.0 * d[2] * d[0];
-        if (disc >= 0.0) {
-          const double q = -0.5 * (d[1] + copysign(sqrt(disc), d[1]));
-          double r1 = q / d[2], r2 = q != 0.0 ? d[0] / q : r1;
-          if (r1 > r2) {
-            const double t = r1;
-            r1 = r2;
-            r2 = t;
-          }
-          out[n++] = r1;
-          if (r2 > r1) out[n++] = r2;
+    if (dm == 1) {
+      out[n++] = -d[0] / d[1];
+    } else if (dm == 2) {
+      const float disc = d[1] * d[1] - 4.f * d[2] * d[0];
+      if (disc >= 0.f) {
+        const float q = -0.5f * (d[1] + copysignf(sqrtf(disc), d[1]));
+        float r1 = q / d[2], r2 = q != 0.f ? d[0] / q : r1;
+        if (r1 > r2) {
+          const float t = r1;
+          r1 = r2;
+          r2 = t;
         }
+        out[n++] = r1;
+        if (r2 > r1) out[n++] = r2;
       }
-      ncrit = n;
-      for (int k = 0; k < n; ++k) crit[k] = out[k];
-      continue;
-    }
-    double a = -bound, dpa;
-    double fa = dl_horner(d, dm, a, dpa);
-    for (int i = 0; i <= ncrit; ++i) {
-      const double b = i < ncrit ? fmin(fmax(crit[i], -bound), bound) : bound;
-      double dpb;
-      const double fb = dl_horner(d, dm, b, dpb);
-      if (b > a && ((fa < 0.0 && fb > 0.0) || (fa > 0.0 && fb < 0.0))) {
-        // critical points only need to separate the next level's roots
-        out[n++] = dl_bracket_root(d, dm, a, b, fa, m == 0 ? 1e-15 : 1e-12);
-      } else if (i < ncrit && (n == 0 || out[n - 1] < b)) {
-        // touches zero at the critical point: |p| at the rounding level of its terms
-        double mag = 0.0, pw = 1.0;
-        for (int k = 0; k <= dm; ++k, pw *= fabs(b)) mag += fabs(d[k]) * pw;
-        if (fabs(fb) <= 1e-13 * mag) out[n++] = b;
+    } else {
+      float a = -bound, dpa;
+      float fa = dl_horner(d, dm, a, dpa);
+      for (int i = 0; i <= ncrit; ++i) {
+        const float b = i < ncrit ? fminf(fmaxf(crit[i], -bound), bound) : bound;
+        float dpb;
+        const float fb = dl_horner(d, dm, b, dpb);
+        if (b > a && ((fa < 0.f && fb > 0.f) || (fa > 0.f && fb < 0.f)))
+          out[n++] = dl_bracket32(d, dm, a, b, fa);
+        a = b;
+        fa = fb;
+        if (n >= dm) break;
       }
-      a = b;
-      fa = fb;
-      if (n >= dm) break;
     }
     ncrit = n;
     for (int k = 0; k < n; ++k) crit[k] = out[k];
   }
-  for (int k = 0; k < ncrit; ++k) roots[k] = crit[k];
-  return ncrit;
+  // level 0: FP64 signs at the bracket ends, FP32 location, FP64 finish
+  int n = 0;
+  const double B = (double)bound;
+  double a = -B, dpa;
+  double fa = dl_horner(c, deg, a, dpa);
+  for (int i = 0; i <= ncrit; ++i) {
+    const double b = i < ncrit ? fmin(fmax((double)crit[i], -B), B) : B;
+    double dpb;
+    const double fb = dl_horner(c, deg, b, dpb);
+    if (b > a && ((fa < 0.0 && fb > 0.0) || (fa > 0.0 && fb < 0.0))) {
+      // the monic FP32 copy has the sign of c times that of the leading coefficient
+      const float sa = ((fa < 0.0) != (ilead < 0.0)) ? -1.f : 1.f;
+      const float x0 = dl_bracket32(cf, deg, (float)a, (float)b, sa);
+      roots[n++] = dl_bracket_root(c, deg, a, b, fa, (double)x0, 1e-15);
+    } else if (i < ncrit && (n == 0 || roots[n - 1] < b)) {
+      // touches zero at the critical point: |p| at the rounding level of its terms
+      double mag = 0.0, pw = 1.0;
+      for (int k = 0; k <= deg; ++k, pw *= fabs(b)) mag += fabs(c[k]) * pw;
+      if (fabs(fb) <= 1e-13 * mag) roots[n++] = b;
+    }
+    a = b;
+    fa = fb;
+    if (n >= deg) break;
+  }
+  return n;
 }
 
 // Newton steps in (x, y) on the intersection of two conics.
