@@ -265,10 +265,13 @@ __device__ __noinline__ int dl_real_roots(const double* c, int deg, double* root
   return n;
 }
 
-// Newton steps in (x, y) on the intersection of two conics.
+// Newton steps in (x, y) on the intersection of two conics, to a step of 1e-12
+// relative (far below the FP32 that the solution feeds; the conic coefficients
+// themselves carry more rounding than that, so a tighter target only makes the
+// iteration dither until its cap).
 __device__ __forceinline__ void dl_polish(const DLConic& p, const DLConic& q, double& x, double& y) {
 #pragma unroll 1
-  for (int it = 0; it < 8; ++it) {
+  for (int it = 0; it < 4; ++it) {
     const double f = dl_conic_at(p, x, y), g = dl_conic_at(q, x, y);
     const double fx = fma(2.0 * p.xx, x, fma(p.xy, y, p.x1)), fy = fma(p.xy, x, fma(2.0 * p.yy, y, p.y1));
     const double gx = fma(2.0 * q.xx, x, fma(q.xy, y, q.x1)), gy = fma(q.xy, x, fma(2.0 * q.yy, y, q.y1));
@@ -278,35 +281,8 @@ __device__ __forceinline__ void dl_polish(const DLConic& p, const DLConic& q, do
     const double dx = (f * gy - g * fy) * id, dy = (g * fx - f * gx) * id;
     x -= dx;
     y -= dy;
-    if (fabs(dx) + fabs(dy) < 1e-14 * (1.0 + fabs(x) + fabs(y))) return;
+    if (fabs(dx) + fabs(dy) < 1e-12 * (1.0 + fabs(x) + fabs(y))) return;
   }
-}
-
-// Determinant of a 4x4 matrix by elimination with partial pivoting.
-__device__ __forceinline__ double dl_det4(double (&a)[4][4]) {
-  double det = 1.0;
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    int p = c;
-    for (int r = c + 1; r < 4; ++r)
-      if (fabs(a[r][c]) > fabs(a[p][c])) p = r;
-    if (a[p][c] == 0.0) return 0.0;
-    if (p != c) {
-      for (int k = 0; k < 4; ++k) {
-        const double t = a[c][k];
-        a[c][k] = a[p][k];
-        a[p][k] = t;
-      }
-      det = -det;
-    }
-    det *= a[c][c];
-    const double inv = 1.0 / a[c][c];
-    for (int r = c + 1; r < 4; ++r) {
-      const double f = a[r][c] * inv;
-      for (int k = c + 1; k < 4; ++k) a[r][k] -= f * a[c][k];
-    }
-  }
-  return det;
 }
 
 // The conics and the resultant quartic of one phase-space point. Momenta in
@@ -412,7 +388,20 @@ __device__ __forceinline__ double dl_jacobian(const double* b, const double* bb,
   M[2][2] = M[3][2] = 0.0;
   M[2][3] = 2.0 * (lm[0] * nub[3] * ieb - lm[3]);
   M[3][3] = 2.0 * ((bb[0] + lm[0]) * nub[3] * ieb - (bb[3] + lm[3]));
-  const double det = dl_det4(M);
+  // Laplace expansion along the last two columns: column 2 (nu_z) is nonzero only in
+  // rows 0, 1 and column 3 (nubar_z) only in rows 2, 3, so
+  // det = sum_{r in {0,1}, s in {2,3}} (-1)^(r+s+1) M[r][2] M[s][3] (M[r'][0] M[s'][1] - M[r'][1] M[s'][0])
+  // with r' = 1 - r and s' = 5 - s.
+  double det = 0.0;
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int t = 2; t < 4; ++t) {
+      const int rc = 1 - r, tc = 5 - t;
+      const double minor = M[rc][0] * M[tc][1] - M[rc][1] * M[tc][0];
+      const double term = M[r][2] * M[t][3] * minor;
+      det += ((r + t + 1) & 1) ? -term : term;
+    }
   const double u4 = DL_UNIT * DL_UNIT * DL_UNIT * DL_UNIT;   // each entry is in GeV / DL_UNIT
   return det == 0.0 ? 0.0 : 1.0 / (fabs(det) * u4);
 }
