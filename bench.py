@@ -52,10 +52,10 @@ FP32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 FP32 lanes
 # hit L2), so its traffic grows with the items; k_parton_tt reads each record once.
 DRAM_BYTES_PER_ITEM_MAIN = {synth.PROC_W: 9008.0}
 # Dilepton ttbar: the neutrino solution runs in FP64, whose GB300 rate (nominal
-# 1.25 TFLOP/s) bounds the kernel (FP64 pipe 86 % active); FP64 flops (DADD,
+# 1.25 TFLOP/s) bounds the kernel (FP64 pipe 85 % active); FP64 flops (DADD,
 # DMUL = 1; DFMA = 2) per evaluation from ncu instruction counters of the current
 # frozen-grid kernel.
-FP64_FLOPS_PER_EVAL = {synth.PROC_TTBAR_DILEP: 1881.9}
+FP64_FLOPS_PER_EVAL = {synth.PROC_TTBAR_DILEP: 1002.6}
 FP64_PEAK_TFLOPS = 1.25
 DRAM_BYTES_PER_PARTON_EVENT = 128.2
 
