@@ -53,8 +53,8 @@ enum {
                             * visible pT imbalance, up to 4 solutions per point); 6 dims, 2 b-jet
                             * assignments. Records: objects 0 l+ (kind 4), 1 mu- (kind 1), 2 and 3
                             * the b jets (kind 5); leptons and jet directions exact, jet energies
-                            * with the double Gaussian. mem_integrate, mem_integrate_noalloc and
-                            * mem_eval_points only (batched and learned-sampler calls reject it). */
+                            * with the double Gaussian. Fixed-budget, adaptive-budget and batched
+                            * integration and mem_eval_points; the learned-sampler calls reject it. */
 };
 
 typedef struct mem_process mem_process; /* opaque, library-owned */

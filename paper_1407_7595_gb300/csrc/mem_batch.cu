@@ -211,14 +211,16 @@ extern "C" mem_status mem_integrate_batch(int32_t n_groups, const mem_events* co
     if (ev->kind != pr->desc.kind)
       return bfail(MEM_ERR_INVALID_ARG, "group " + std::to_string(g) + ": process kind mismatch");
     const int kind = pr->desc.kind, d = dims_of(kind), np = nperm_of(kind);
-    if (kind == PROC_TTDL)
-      return bfail(MEM_ERR_INVALID_ARG, "group " + std::to_string(g) +
-                                            ": dilepton ttbar is integrated by mem_integrate only");
     const mem_tf_desc& T = *tfs[g];
-    if (kind != PROC_TTBAR && !(T.lep_rel > 0 && T.window_k > 0 && T.lep_rel * T.window_k < 1))
+    if ((kind == PROC_DY || kind == PROC_W) &&
+        !(T.lep_rel > 0 && T.window_k > 0 && T.lep_rel * T.window_k < 1))
       return bfail(MEM_ERR_INVALID_ARG, "lepton TF parameters invalid");
-    if (kind != PROC_DY && !(T.met_sigma > 0 && T.met_box_k > 0))
+    if ((kind == PROC_W || kind == PROC_TTBAR) && !(T.met_sigma > 0 && T.met_box_k > 0))
       return bfail(MEM_ERR_INVALID_ARG, "MET TF parameters invalid");
+    if ((kind == PROC_TTBAR || kind == PROC_TTDL) &&
+        !(T.jet_core > 0 && T.jet_tail > 0 && T.jet_tail_w >= 0 && T.jet_tail_w <= 1 &&
+          T.jet_lo_div > 1 && T.jet_hi_mul > 1))
+      return bfail(MEM_ERR_INVALID_ARG, "jet TF parameters invalid");
     // this group's schedule: its plan entry where given, else the common options
     const mem_plan* pl = opts->plans ? &opts->plans[g] : nullptr;
     const int iters = pl && pl->n_adapt_iters ? pl->n_adapt_iters : opts->n_adapt_iters;
@@ -325,9 +327,10 @@ extern "C" mem_status mem_integrate_batch(int32_t n_groups, const mem_events* co
       ce = cudaStreamWaitEvent(gs[g], fork, 0);
       if (ce != cudaSuccess) break;
       const int kind = plans[g].b.kind;
-      ce = kind == PROC_DY ? launch_batch_dy(plans[g].b, gs[g])
-                           : kind == PROC_W ? launch_batch_w(plans[g].b, gs[g])
-                                            : launch_batch_tt(plans[g].b, gs[g]);
+      ce = kind == PROC_DY     ? launch_batch_dy(plans[g].b, gs[g])
+           : kind == PROC_W    ? launch_batch_w(plans[g].b, gs[g])
+           : kind == PROC_TTDL ? launch_batch_ttdl(plans[g].b, gs[g])
+                               : launch_batch_tt(plans[g].b, gs[g]);
       if (ce == cudaSuccess) ce = cudaEventRecord(done[g], gs[g]);
       if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cs, done[g], 0);
     }

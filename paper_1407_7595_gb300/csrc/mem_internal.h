@@ -119,6 +119,7 @@ struct BatchArgs;
 cudaError_t launch_batch_dy(const BatchArgs&, cudaStream_t);
 cudaError_t launch_batch_w(const BatchArgs&, cudaStream_t);
 cudaError_t launch_batch_tt(const BatchArgs&, cudaStream_t);
+cudaError_t launch_batch_ttdl(const BatchArgs&, cudaStream_t);
 // The same with tabulated PDFs (P.pdf_grid set): kernels built for that path
 // (mem_launch_grid.cu); the functions above forward to them.
 cudaError_t launch_integrate_dy_grid(const IntegrateArgs&, cudaStream_t);

@@ -14,3 +14,11 @@ cudaError_t launch_eval_ttdl(const EvalArgs& a, cudaStream_t st) { return run_ev
 size_t cache_size_ttdl() { return cache_bytes<PhysTTDL>(); }
 
 }  // namespace mem
+
+#include "mem_batch.cuh"
+
+namespace mem {
+cudaError_t launch_batch_ttdl(const BatchArgs& b, cudaStream_t st) {
+  return run_batch<PhysTTDL, MINB_DL>(b, st);
+}
+}  // namespace mem

@@ -5,7 +5,7 @@ through the C ABI.
 The kernel solves for the neutrinos in FP64 with its own method (real roots of
 the resultant quartic through the derivative chain, safeguarded Newton) and does
 everything else in FP32; the oracle uses the Durand-Kerner iteration and FP64
-throughout.
+throughout. The batched, per-event-stopping entry point is covered too.
 
 Per-point tolerance: the kernel's FP64 solver receives FP32 inputs -- the four
 virtualities from the Breit-Wigner maps and the b-jet energies from the log map,
@@ -96,9 +96,23 @@ def test_adaptive_agrees_within_errors(env):
     assert np.all(g["status"] == 0)
 
 
-def test_rejected_by_batched_mode(env):
+def test_batched_and_adaptive_budget(env):
+    """Per-event stopping at a target relative error: the batched entry point and
+    mem_integrate's adaptive schedule (the same schedule) agree, every event
+    converges, and the estimates agree with a fixed-budget oracle run within the
+    combined MC error."""
     abi, synth, O, recs, integ, P, T = env
-    prob, err = np.zeros(len(recs)), np.zeros(len(recs))
-    opts = abi.make_opts(target_rel_err=0.01, max_points=1 << 20, adapt_points=4096)
-    with pytest.raises(abi.MemError, match="dilepton"):
-        abi.mem_integrate_batch([(integ.events, integ.proc, integ.tf)], 3, opts, prob, err)
+    recs6 = synth.gen_events(KIND, 6, 7200)
+    g = abi.Integrator(KIND, recs6, synth.DEFAULT_PROCESS, synth.DEFAULT_TF[KIND])
+    opts = abi.make_opts(target_rel_err=0.02, max_points=1 << 20, adapt_points=4096)
+    r = g.integrate(0, seed=5, opts=opts)
+    prob, err = np.zeros(6), np.zeros(6)
+    used, st = np.zeros(6, dtype=np.uint64), np.zeros(6, dtype=np.int32)
+    abi.mem_integrate_batch([(g.events, g.proc, g.tf)], 5, opts, prob, err, used, st)
+    g.close()
+    assert np.all(st == 0) and np.all(r["status"] == 0)
+    assert np.all(err <= 0.02 * prob * (1 + 1e-12)) and np.all(r["err"] <= 0.02 * r["prob"] * (1 + 1e-12))
+    assert np.all(np.abs(prob - r["prob"]) <= 3.5 * np.hypot(err, r["err"]))
+    o = O.integrate(P, T, recs6[:2], seed=6, n_points=8192, n_adapt_iters=3, adapt_points=2048)
+    pull = (prob[:2] - o["prob"]) / np.hypot(err[:2], o["err"])
+    assert np.all(np.abs(pull) < 4.0), pull
