@@ -8,6 +8,8 @@
  *   W          u dbar -> W+ -> e+ nu   (d ubar -> W- -> e- nubar)
  *   ttbar      g g / q qbar -> t tbar -> (b l+ nu)(bbar d ubar), resonant t, tbar,
  *              W+, W- propagators with Breit-Wigner widths, full spin correlation.
+ *   ttH        g g / q qbar -> t tbar H (production, on-shell tops; Sec. 3's signal
+ *              process), Higgs-top Yukawa y_t = m_t / v, v = 2 m_W / g_W.
  * Couplings: e^2 = 4 pi alpha, g_W^2 = e^2 / sin^2(theta_W), g_s^2 = 4 pi alpha_s.
  */
 #include <math.h>
@@ -274,4 +276,126 @@ void ora_antitop_decay_probe(const ora_process* P, const double* pbb_, const dou
         }
     out2[s] = acc;
   }
+}
+
+/* ------------------------------------------------------------ ttH */
+/* Fermion propagator (q/ + m) / (q^2 - m^2). */
+static dmat fprop(rv4 q, double m) {
+  return d_scale(d_add(d_slash_r(q), d_scale(d_unit(), m)), 1.0 / (rv_dot(q, q) - m * m));
+}
+
+/* X1 S(q1) X2 S(q2) X3 along the top line read from the top (row) side: each
+ * vertex takes in the momentum in_j, so q1 = pt - in1 and q2 = q1 - in2. */
+static dmat chain3(dmat X1, rv4 in1, dmat X2, rv4 in2, dmat X3, rv4 pt, double m) {
+  rv4 q1 = rv_sub(pt, in1), q2 = rv_sub(q1, in2);
+  return d_mul(d_mul(d_mul(d_mul(X1, fprop(q1, m)), X2), fprop(q2, m)), X3);
+}
+static dmat chain2(dmat X1, rv4 in1, dmat X2, rv4 pt, double m) {
+  return d_mul(d_mul(X1, fprop(rv_sub(pt, in1), m)), X2);
+}
+
+/* Colour-ordered vertices of g(k1, e1) g(k2, e2) -> t(pt) tbar H(pH) between the top
+ * row and the antitop column, Yukawa and g_s factors left out: the two gluons and
+ * the Higgs (unit scalar vertex, momentum -pH entering) in every order on the top
+ * line, and the s-channel gluon V/ / s with the Higgs before or after it.
+ *   G1 = orders with e1 before e2 (from the top side) + S_H    (colour T^a T^b)
+ *   G2 = orders with e2 before e1                    - S_H    (colour T^b T^a) */
+static void tth_gg_vertices(rv4 k1, rv4 k2, rv4 pt, rv4 pH, double m, cv4 e1, cv4 e2, dmat* G1,
+                            dmat* G2) {
+  dmat E1 = d_slash(e1), E2 = d_slash(e2), H = d_unit();
+  rv4 mh = rv_scale(pH, -1.0), K = rv_add(k1, k2);
+  *G1 = d_add(d_add(chain3(E1, k1, E2, k2, H, pt, m), chain3(E1, k1, H, mh, E2, pt, m)),
+              chain3(H, mh, E1, k1, E2, pt, m));
+  *G2 = d_add(d_add(chain3(E2, k2, E1, k1, H, pt, m), chain3(E2, k2, H, mh, E1, pt, m)),
+              chain3(H, mh, E2, k2, E1, pt, m));
+  double shat = rv_dot(K, K);
+  cv4 ck1 = cv_from_rv(k1), ck2 = cv_from_rv(k2);
+  cv4 V = cv_lin(cv_dot(e1, e2), cv_lin(1.0, ck1, -1.0, ck2), 0.0, ck1);
+  V = cv_lin(1.0, V, 2.0 * cv_dot(ck2, e1), e2);
+  V = cv_lin(1.0, V, -2.0 * cv_dot(ck1, e2), e1);
+  dmat VS = d_scale(d_slash(V), 1.0 / shat);
+  dmat SH = d_add(chain2(VS, K, H, pt, m), chain2(H, mh, VS, pt, m));
+  *G1 = d_add(*G1, SH);
+  *G2 = d_add(*G2, d_scale(SH, -1.0));
+}
+
+static double tth_gg_colour_sum(rv4 k1, rv4 k2, rv4 pt, rv4 pH, double m, spin row, spin col) {
+  double s = 0.0;
+  for (int h1 = 0; h1 < 2; ++h1)
+    for (int h2 = 0; h2 < 2; ++h2) {
+      dmat G1, G2;
+      tth_gg_vertices(k1, k2, pt, pH, m, gluon_pol(+1, h1), gluon_pol(-1, h2), &G1, &G2);
+      cplx A1 = d_rc(row, d_mv(G1, col));
+      cplx A2 = d_rc(row, d_mv(G2, col));
+      s += 16.0 / 3.0 * (creal(A1 * conj(A1)) + creal(A2 * conj(A2))) -
+           2.0 * 2.0 / 3.0 * creal(A1 * conj(A2));
+    }
+  return s;
+}
+
+/* q(kq) qbar(kqb) -> g* -> t tbar H: the Higgs before or after the gluon vertex on
+ * the top line (the massless light quarks do not couple to it); colour sum 2. */
+static double tth_qq_colour_sum(rv4 kq, rv4 kqb, rv4 pt, rv4 pH, double m, spin row, spin col) {
+  rv4 K = rv_add(kq, kqb), mh = rv_scale(pH, -1.0);
+  double shat = rv_dot(K, K);
+  double s = 0.0;
+  dmat one = d_unit();
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      cv4 J = d_current(d_bar(d_massless(kqb, b)), one, d_massless(kq, a));
+      dmat JS = d_slash(J);
+      dmat G = d_add(chain2(JS, K, one, pt, m), chain2(one, mh, JS, pt, m));
+      cplx A = d_rc(row, d_mv(G, col)) / shat;
+      s += 2.0 * creal(A * conj(A));
+    }
+  return s;
+}
+
+static double yukawa_top(const ora_process* P) {
+  double gw2 = 4.0 * M_PI * P->alpha / P->sw2;
+  double v = 2.0 * P->mw / sqrt(gw2);
+  return P->mt / v;
+}
+
+double ora_msq_tth_production(const ora_process* P, int channel, const double* k1_,
+                              const double* k2_, const double* pt_, const double* ptb_,
+                              const double* pH_) {
+  rv4 k1 = to_rv(k1_), k2 = to_rv(k2_), pt = to_rv(pt_), ptb = to_rv(ptb_), pH = to_rv(pH_);
+  double m = P->mt;
+  double gs2 = 4.0 * M_PI * P->alpha_s;
+  double y = yukawa_top(P);
+  double sum = 0.0;
+  for (int s = 0; s < 2; ++s)
+    for (int sb = 0; sb < 2; ++sb) {
+      spin row = d_bar(d_massive_u(pt, m, s));
+      spin col = d_massive_v(ptb, m, sb);
+      sum += channel == 0 ? tth_gg_colour_sum(k1, k2, pt, pH, m, row, col)
+                          : tth_qq_colour_sum(k1, k2, pt, pH, m, row, col);
+    }
+  double avg = channel == 0 ? 1.0 / (4.0 * 64.0) : 1.0 / (4.0 * 9.0);
+  return sum * gs2 * gs2 * y * y * avg;
+}
+
+/* Gauge probe of the colour-ordered ttH amplitudes: sum over top spins of
+ * |A(T^aT^b)|^2 + |A(T^bT^a)|^2 with gluon `which` (0 or 1) given its momentum as
+ * polarisation and the other gluon the transverse state hel. */
+double ora_tth_gauge_probe(const ora_process* P, const double* k1_, const double* k2_,
+                           const double* pt_, const double* ptb_, const double* pH_, int which,
+                           int hel) {
+  rv4 k1 = to_rv(k1_), k2 = to_rv(k2_), pt = to_rv(pt_), ptb = to_rv(ptb_), pH = to_rv(pH_);
+  double m = P->mt;
+  double tot = 0.0;
+  for (int s = 0; s < 2; ++s)
+    for (int sb = 0; sb < 2; ++sb) {
+      spin row = d_bar(d_massive_u(pt, m, s));
+      spin col = d_massive_v(ptb, m, sb);
+      cv4 e1 = gluon_pol(+1, hel), e2 = gluon_pol(-1, hel);
+      if (which == 0) e1 = cv_from_rv(k1);
+      else e2 = cv_from_rv(k2);
+      dmat G1, G2;
+      tth_gg_vertices(k1, k2, pt, pH, m, e1, e2, &G1, &G2);
+      cplx A1 = d_rc(row, d_mv(G1, col)), A2 = d_rc(row, d_mv(G2, col));
+      tot += creal(A1 * conj(A1)) + creal(A2 * conj(A2));
+    }
+  return tot;
 }

@@ -100,6 +100,14 @@ void ora_parton_batch(const ora_process* P, const float* recs, int64_t n, int n_
 
 /* The integrand's contribution of each kinematic root (neutrino p_z solution) at
  * point x; returns the number of roots (0..2). Their sum is ora_integrand. */
+/* g g (channel 0) or q qbar (channel 1) -> t tbar H with on-shell tops, summed over
+ * all spins and colours, averaged over the initial ones (Sec. 3's signal process). */
+double ora_msq_tth_production(const ora_process* P, int channel, const double* k1,
+                              const double* k2, const double* pt, const double* ptb,
+                              const double* pH);
+double ora_tth_gauge_probe(const ora_process* P, const double* k1, const double* k2,
+                           const double* pt, const double* ptb, const double* pH, int which,
+                           int hel);
 double ora_flavour_msq(const ora_process* P, const double* fs, const double* k12, double x1,
                        double x2, const float* rec);
 int ora_integrand_roots(const ora_process* P, const ora_tf* T, const float* rec, int perm,

@@ -111,6 +111,10 @@ def load():
     lib.ora_msq_ttbar_production.restype = C.c_double
     lib.ora_ttbar_gauge_probe.argtypes = [P, _dp, _dp, _dp, _dp, C.c_int, C.c_int]
     lib.ora_ttbar_gauge_probe.restype = C.c_double
+    lib.ora_msq_tth_production.argtypes = [P, C.c_int, _dp, _dp, _dp, _dp, _dp]
+    lib.ora_msq_tth_production.restype = C.c_double
+    lib.ora_tth_gauge_probe.argtypes = [P, _dp, _dp, _dp, _dp, _dp, C.c_int, C.c_int]
+    lib.ora_tth_gauge_probe.restype = C.c_double
     lib.ora_top_decay_probe.argtypes = [P, _dp, _dp, _dp, _dp]
     lib.ora_antitop_decay_probe.argtypes = [P, _dp, _dp, _dp, _dp]
     lib.ora_pdf.argtypes = [P, C.c_int, C.c_double]
@@ -268,6 +272,16 @@ def msq_w(P, charge, kq, kqb, pl, pn):
 def msq_ttbar(P, channel, k1, k2, pb, pl, pn, pbb, pd, pu):
     args = [_d(v) for v in (k1, k2, pb, pl, pn, pbb, pd, pu)]
     return load().ora_msq_ttbar(C.byref(P), channel, *[a[1] for a in args])
+
+
+def msq_tth_production(P, channel, k1, k2, pt, ptb, pH):
+    args = [_d(v) for v in (k1, k2, pt, ptb, pH)]
+    return load().ora_msq_tth_production(C.byref(P), channel, *[a[1] for a in args])
+
+
+def tth_gauge_probe(P, k1, k2, pt, ptb, pH, which, hel):
+    args = [_d(v) for v in (k1, k2, pt, ptb, pH)]
+    return load().ora_tth_gauge_probe(C.byref(P), *[a[1] for a in args], which, hel)
 
 
 def msq_ttbar_production(P, channel, k1, k2, pt, ptb):

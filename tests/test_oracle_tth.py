@@ -1,0 +1,146 @@
+"""Pins of the oracle's g g / q qbar -> t tbar H production amplitude (Sec. 3's
+signal process; the Higgs-top Yukawa y_t = m_t / v).
+
+* Gauge invariance: each colour-ordered g g amplitude vanishes when one gluon's
+  polarisation is replaced by its momentum (the other gluon physical).
+* Soft-Higgs limit: as the Higgs momentum goes to zero, |M(ttH)|^2 ->
+  y_t^2 m_t^2 (1/(p_t.p_H) + 1/(p_tbar.p_H))^2 |M(tt)|^2 -- the scalar emission off the
+  two external top lines, whose numerators reduce to 2 m_t (u-bar(p)(p/ + m) =
+  2 m u-bar(p)); the deviation is O(p_H), so it shrinks tenfold when p_H does. This
+  fixes the Higgs vertex, its placement in every diagram and the relative sign of
+  the emissions off the top and the antitop.
+* Bose symmetry (g g: exchanging the gluons) and Lorentz invariance (a boost along
+  and a rotation about the beam axis, which keep the gluon polarisations valid).
+"""
+import math
+
+import numpy as np
+import pytest
+
+
+def dot(a, b):
+    return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3]
+
+
+@pytest.fixture(scope="module")
+def params(synth):
+    return dict(synth.DEFAULT_PROCESS)
+
+
+def _boost(p, beta):
+    """Boost p by velocity beta (3-vector)."""
+    b2 = float(beta @ beta)
+    if b2 == 0.0:
+        return p.copy()
+    g = 1.0 / math.sqrt(1.0 - b2)
+    bp = float(beta @ p[1:])
+    out = np.empty(4)
+    out[0] = g * (p[0] + bp)
+    out[1:] = p[1:] + ((g - 1.0) * bp / b2 + g * p[0]) * beta
+    return out
+
+
+def _two_body(rng, M, m1, m2):
+    """Momenta of a two-body decay at rest, isotropic."""
+    p = math.sqrt((M * M - (m1 + m2) ** 2) * (M * M - (m1 - m2) ** 2)) / (2 * M)
+    c = rng.uniform(-1, 1)
+    s = math.sqrt(1 - c * c)
+    ph = rng.uniform(0, 2 * math.pi)
+    n = np.array([s * math.cos(ph), s * math.sin(ph), c])
+    return (np.array([math.sqrt(p * p + m1 * m1), *(p * n)]),
+            np.array([math.sqrt(p * p + m2 * m2), *(-p * n)]))
+
+
+def _tth_kinematics(rng, rs, m, pH):
+    """Beams along z in the partonic rest frame; the Higgs momentum pH given; the
+    t tbar pair recoils and decays isotropically in its own rest frame."""
+    k1, k2 = np.array([rs / 2, 0, 0, rs / 2]), np.array([rs / 2, 0, 0, -rs / 2])
+    Q = k1 + k2 - pH
+    MQ = math.sqrt(dot(Q, Q))
+    t, tb = _two_body(rng, MQ, m, m)
+    beta = Q[1:] / Q[0]
+    return k1, k2, _boost(t, beta), _boost(tb, beta)
+
+
+def _random_higgs(rng, rs, mh):
+    E = rng.uniform(mh + 5.0, 0.3 * rs)
+    p = math.sqrt(E * E - mh * mh)
+    c = rng.uniform(-1, 1)
+    s = math.sqrt(1 - c * c)
+    ph = rng.uniform(0, 2 * math.pi)
+    return np.array([E, p * s * math.cos(ph), p * s * math.sin(ph), p * c])
+
+
+def test_tth_gauge_invariance(ora, params):
+    P = ora.process(2, params)
+    rng = np.random.default_rng(41)
+    for rs in (600.0, 2000.0):
+        pH = _random_higgs(rng, rs, 125.0)
+        k1, k2, pt, ptb = _tth_kinematics(rng, rs, params["mt"], pH)
+        assert np.allclose(k1 + k2, pt + ptb + pH, rtol=0, atol=1e-10 * rs)
+        ref = ora.msq_tth_production(P, 0, k1, k2, pt, ptb, pH)
+        gs4y2 = (4 * math.pi * params["alpha_s"]) ** 2 * (params["mt"] / (2 * params["mw"] / math.sqrt(4 * math.pi * params["alpha"] / params["sw2"]))) ** 2
+        ref_ordered = ref / gs4y2 * 256      # undo couplings and the 1/(4 x 64) average
+        assert ref > 0
+        for which in (0, 1):
+            for hel in (0, 1):
+                assert ora.tth_gauge_probe(P, k1, k2, pt, ptb, pH, which, hel) < 1e-20 * ref_ordered
+
+
+@pytest.mark.parametrize("channel", [0, 1])
+def test_tth_soft_higgs_limit(ora, params, channel):
+    P = ora.process(2, params)
+    m = params["mt"]
+    y = m / (2 * params["mw"] / math.sqrt(4 * math.pi * params["alpha"] / params["sw2"]))
+    rng = np.random.default_rng(42 + channel)
+    rs = 900.0
+    for _ in range(3):
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        c = rng.uniform(-1, 1)
+        ph = rng.uniform(0, 2 * math.pi)
+        # t tbar at lambda = 0, direction fixed; the same direction in the pair's rest frame
+        dev = []
+        for lam in (1e-3, 1e-4):
+            pH = lam * rs * np.array([1.0, *n])
+            k1, k2 = np.array([rs / 2, 0, 0, rs / 2]), np.array([rs / 2, 0, 0, -rs / 2])
+            Q = k1 + k2 - pH
+            MQ = math.sqrt(dot(Q, Q))
+            p = math.sqrt(MQ * MQ / 4 - m * m)
+            s_ = math.sqrt(1 - c * c)
+            d = np.array([s_ * math.cos(ph), s_ * math.sin(ph), c])
+            beta = Q[1:] / Q[0]
+            pt = _boost(np.array([MQ / 2, *(p * d)]), beta)
+            ptb = _boost(np.array([MQ / 2, *(-p * d)]), beta)
+            p0 = math.sqrt(rs * rs / 4 - m * m)
+            pt0 = np.array([rs / 2, *(p0 * d)])
+            ptb0 = np.array([rs / 2, *(-p0 * d)])
+            tt = ora.msq_ttbar_production(P, channel, k1, k2, pt0, ptb0)
+            eik = y * y * m * m * (1 / dot(pt, pH) + 1 / dot(ptb, pH)) ** 2
+            tth = ora.msq_tth_production(P, channel, k1, k2, pt, ptb, pH)
+            dev.append(tth / (eik * tt) - 1.0)
+        assert abs(dev[0]) < 2e-2
+        assert abs(dev[1]) < 0.2 * abs(dev[0]) + 1e-6   # O(p_H): tenfold smaller
+
+
+def test_tth_bose_and_lorentz(ora, params):
+    P = ora.process(2, params)
+    rng = np.random.default_rng(44)
+    rs = 1200.0
+    for _ in range(3):
+        pH = _random_higgs(rng, rs, 125.0)
+        k1, k2, pt, ptb = _tth_kinematics(rng, rs, params["mt"], pH)
+        for channel in (0, 1):
+            ref = ora.msq_tth_production(P, channel, k1, k2, pt, ptb, pH)
+            if channel == 0:
+                assert ora.msq_tth_production(P, 0, k2, k1, pt, ptb, pH) == pytest.approx(ref, rel=1e-11, abs=0)
+            # boost along z and rotation about z
+            bz = np.array([0.0, 0.0, rng.uniform(-0.7, 0.7)])
+            a = rng.uniform(0, 2 * math.pi)
+            R = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
+
+            def tr(p):
+                q = _boost(p, bz)
+                return np.array([q[0], *(R @ q[1:])])
+            got = ora.msq_tth_production(P, channel, tr(k1), tr(k2), tr(pt), tr(ptb), tr(pH))
+            assert got == pytest.approx(ref, rel=1e-10, abs=0)
