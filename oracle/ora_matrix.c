@@ -399,3 +399,61 @@ double ora_tth_gauge_probe(const ora_process* P, const double* k1_, const double
     }
   return tot;
 }
+
+/* g g / q qbar -> t tbar H -> (b l+ nu)(bbar mu- nubar)(b1 b2): the production
+ * vertices above between the decaying top row and antitop column of ora_msq_ttbar
+ * (here with the W- decaying to mu- nubar), times the Higgs decay
+ * y_b ubar(b1) v(b2) (colour singlet: 3 colour states) and the Higgs propagator
+ * 1 / (q_H^2 - m_H^2 + i m_H G_H), y_b = m_b / v; resonant t, tbar, W+, W-
+ * Breit-Wigner propagators as in ora_msq_ttbar. Colour and spins summed, the
+ * initial ones averaged. */
+double ora_msq_tth(const ora_process* P, int channel, const double* k1_, const double* k2_,
+                   const double* pb_, const double* pl_, const double* pn_, const double* pbb_,
+                   const double* pm_, const double* pnb_, const double* ph1_, const double* ph2_) {
+  rv4 k1 = to_rv(k1_), k2 = to_rv(k2_);
+  rv4 pb = to_rv(pb_), pl = to_rv(pl_), pn = to_rv(pn_);
+  rv4 pbb = to_rv(pbb_), pm = to_rv(pm_), pnb = to_rv(pnb_);
+  rv4 ph1 = to_rv(ph1_), ph2 = to_rv(ph2_);
+  double m = P->mt;
+  rv4 pt = rv_add(pb, rv_add(pl, pn));
+  rv4 ptb = rv_add(pbb, rv_add(pm, pnb));
+  rv4 pH = rv_add(ph1, ph2);
+  rv4 w1 = rv_add(pl, pn), w2 = rv_add(pm, pnb);
+  cplx Dt = rv_dot(pt, pt) - m * m + I * m * P->wt;
+  cplx Dtb = rv_dot(ptb, ptb) - m * m + I * m * P->wt;
+  cplx Dw1 = rv_dot(w1, w1) - P->mw * P->mw + I * P->mw * P->ww;
+  cplx Dw2 = rv_dot(w2, w2) - P->mw * P->mw + I * P->mw * P->ww;
+  cplx Dh = rv_dot(pH, pH) - P->mh * P->mh + I * P->mh * P->wh;
+  double gs2 = 4.0 * M_PI * P->alpha_s;
+  double gw2 = 4.0 * M_PI * P->alpha / P->sw2;
+  double yt = yukawa_top(P), yb = yt * P->mb / P->mt;
+  dmat PL = d_PL();
+  dmat ptm = d_add(d_slash_r(pt), d_scale(d_unit(), m));
+  dmat ptbm = d_add(d_scale(d_slash_r(ptb), -1.0), d_scale(d_unit(), m));
+  double sum = 0.0;
+  for (int sb = 0; sb < 2; ++sb)
+    for (int sn = 0; sn < 2; ++sn)
+      for (int sl = 0; sl < 2; ++sl)
+        for (int sbb = 0; sbb < 2; ++sbb)
+          for (int sm = 0; sm < 2; ++sm)
+            for (int snb = 0; snb < 2; ++snb) {
+              cv4 L = d_current(d_bar(d_massless(pn, sn)), PL, d_massless(pl, sl));
+              cv4 H = d_current(d_bar(d_massless(pm, sm)), PL, d_massless(pnb, snb));
+              spin row = d_vm(d_vm(d_bar(d_massless(pb, sb)), d_mul(d_slash(L), PL)), ptm);
+              spin col = d_mv(ptbm, d_mv(d_mul(d_slash(H), PL), d_massless(pbb, sbb)));
+              sum += channel == 0 ? tth_gg_colour_sum(k1, k2, pt, pH, m, row, col)
+                                  : tth_qq_colour_sum(k1, k2, pt, pH, m, row, col);
+            }
+  /* Higgs decay: sum over the b1, b2 spins of |ubar(b1) v(b2)|^2 */
+  double hdec = 0.0;
+  for (int s1 = 0; s1 < 2; ++s1)
+    for (int s2 = 0; s2 < 2; ++s2) {
+      cplx a = d_rc(d_bar(d_massless(ph1, s1)), d_massless(ph2, s2));
+      hdec += creal(a * conj(a));
+    }
+  double dens = creal(Dt * conj(Dt)) * creal(Dtb * conj(Dtb)) * creal(Dw1 * conj(Dw1)) *
+                creal(Dw2 * conj(Dw2)) * creal(Dh * conj(Dh));
+  double coup = gs2 * gs2 * yt * yt * pow(0.5 * gw2, 4) * yb * yb * 3.0;
+  double avg = channel == 0 ? 1.0 / (4.0 * 64.0) : 1.0 / (4.0 * 9.0);
+  return sum * hdec * coup * avg / dens;
+}

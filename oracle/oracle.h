@@ -47,6 +47,7 @@ typedef struct {
   const double* pdf_grid;
   int32_t grid_nx, grid_nq;
   double grid_lx[2], grid_lq[2];
+  double mh, wh, mb; /* Higgs mass and width, b-quark mass in the b Yukawa (ttH) */
 } ora_process;
 
 typedef struct {
@@ -105,6 +106,11 @@ void ora_parton_batch(const ora_process* P, const float* recs, int64_t n, int n_
 double ora_msq_tth_production(const ora_process* P, int channel, const double* k1,
                               const double* k2, const double* pt, const double* ptb,
                               const double* pH);
+/* The same with the decays t -> b l+ nu, tbar -> bbar mu- nubar, H -> b1 b2 and
+ * Breit-Wigner t, tbar, W+, W-, H propagators. */
+double ora_msq_tth(const ora_process* P, int channel, const double* k1, const double* k2,
+                   const double* pb, const double* pl, const double* pn, const double* pbb,
+                   const double* pm, const double* pnb, const double* ph1, const double* ph2);
 double ora_tth_gauge_probe(const ora_process* P, const double* k1, const double* k2,
                            const double* pt, const double* ptb, const double* pH, int which,
                            int hel);

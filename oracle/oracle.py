@@ -30,7 +30,8 @@ class OraProcess(C.Structure):
                 ("sw2", C.c_double), ("alpha_s", C.c_double), ("pdf_A", C.c_double * 3),
                 ("pdf_a", C.c_double * 3), ("pdf_b", C.c_double * 3),
                 ("pdf_grid", C.POINTER(C.c_double)), ("grid_nx", C.c_int32),
-                ("grid_nq", C.c_int32), ("grid_lx", C.c_double * 2), ("grid_lq", C.c_double * 2)]
+                ("grid_nq", C.c_int32), ("grid_lx", C.c_double * 2), ("grid_lq", C.c_double * 2),
+                ("mh", C.c_double), ("wh", C.c_double), ("mb", C.c_double)]
 
 
 class OraTF(C.Structure):
@@ -114,6 +115,8 @@ def load():
     lib.ora_msq_tth_production.argtypes = [P, C.c_int, _dp, _dp, _dp, _dp, _dp]
     lib.ora_msq_tth_production.restype = C.c_double
     lib.ora_tth_gauge_probe.argtypes = [P, _dp, _dp, _dp, _dp, _dp, C.c_int, C.c_int]
+    lib.ora_msq_tth.argtypes = [P, C.c_int] + [_dp] * 10
+    lib.ora_msq_tth.restype = C.c_double
     lib.ora_tth_gauge_probe.restype = C.c_double
     lib.ora_top_decay_probe.argtypes = [P, _dp, _dp, _dp, _dp]
     lib.ora_antitop_decay_probe.argtypes = [P, _dp, _dp, _dp, _dp]
@@ -150,6 +153,8 @@ def process(kind, params, pdf_grid=None):
         setattr(p, k, float(params[k]))
     for k in ("pdf_A", "pdf_a", "pdf_b"):
         getattr(p, k)[:] = [float(v) for v in params[k]]
+    for k in ("mh", "wh", "mb"):   # Higgs parameters (ttH); absent for the other processes
+        setattr(p, k, float(params.get(k, 0.0)))
     if pdf_grid is not None:
         t = np.ascontiguousarray(pdf_grid["table"], dtype=np.float64)
         assert t.ndim == 3 and t.shape[0] == 3 and t.shape[1] >= 2 and t.shape[2] >= 2
@@ -277,6 +282,11 @@ def msq_ttbar(P, channel, k1, k2, pb, pl, pn, pbb, pd, pu):
 def msq_tth_production(P, channel, k1, k2, pt, ptb, pH):
     args = [_d(v) for v in (k1, k2, pt, ptb, pH)]
     return load().ora_msq_tth_production(C.byref(P), channel, *[a[1] for a in args])
+
+
+def msq_tth(P, channel, k1, k2, pb, pl, pn, pbb, pm, pnb, ph1, ph2):
+    args = [_d(v) for v in (k1, k2, pb, pl, pn, pbb, pm, pnb, ph1, ph2)]
+    return load().ora_msq_tth(C.byref(P), channel, *[a[1] for a in args])
 
 
 def tth_gauge_probe(P, k1, k2, pt, ptb, pH, which, hel):

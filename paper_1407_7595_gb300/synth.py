@@ -55,6 +55,8 @@ DEFAULT_PROCESS = {
     "pdf_A": (1.0, 1.0, 1.0),
     "pdf_a": (-0.5, -0.5, -1.0),
     "pdf_b": (3.0, 5.0, 5.0),
+    # Higgs (ttH, Sec. 3): mass, width and the b-quark mass of the b Yukawa coupling
+    "mh": 125.0, "wh": 0.00407, "mb": 4.7,
 }
 
 # Transfer-function parameters per process.

@@ -144,3 +144,54 @@ def test_tth_bose_and_lorentz(ora, params):
                 return np.array([q[0], *(R @ q[1:])])
             got = ora.msq_tth_production(P, channel, tr(k1), tr(k2), tr(pt), tr(ptb), tr(pH))
             assert got == pytest.approx(ref, rel=1e-10, abs=0)
+
+
+def _decay3(rng, M, m12):
+    """Massless three-body configuration at rest: M -> a + (b c), (b c) of mass m12."""
+    a, w = _two_body(rng, M, 0.0, m12)
+    b, c = _two_body(rng, m12, 0.0, 0.0)
+    beta = w[1:] / w[0]
+    return a, _boost(b, beta), _boost(c, beta)
+
+
+@pytest.mark.parametrize("channel", [0, 1])
+def test_tth_full_chain_factorises(ora, params, channel):
+    """With on-shell tops the full 2 -> 8 |M|^2 (propagator denominators removed),
+    averaged over parity-reflected decays in each top rest frame, equals
+    |M|^2(ttH production, top spins summed) x (g_W^2/2)^4 c_t c_tbar x 3 y_b^2 4 p_b1.p_b2
+    with c_t = 8 (p_t.p_l+)(p_b.p_nu), c_tbar = 8 (p_tbar.p_mu-)(p_bbar.p_nubar): the
+    top decays as in semileptonic ttbar (the reflection removes their spin
+    correlation), the W- decaying to one lepton channel, and the scalar Higgs decay
+    factorising exactly (sum over spins of |ubar(b1) v(b2)|^2 = 4 p_b1.p_b2, 3 colours)."""
+    P = ora.process(2, params)
+    m, mw, ww, wt = params["mt"], params["mw"], params["ww"], params["wt"]
+    mh, wh = params["mh"], params["wh"]
+    gw2 = 4 * math.pi * params["alpha"] / params["sw2"]
+    yb = params["mb"] / (2 * mw / math.sqrt(gw2))
+    rng = np.random.default_rng(46 + channel)
+    for rs in (700.0, 1500.0):
+        pH = _random_higgs(rng, rs, mh + 0.003)
+        k1, k2, pt, ptb = _tth_kinematics(rng, rs, m, pH)
+        h1, h2 = _two_body(rng, math.sqrt(dot(pH, pH)), 0.0, 0.0)
+        bH = pH[1:] / pH[0]
+        h1, h2 = _boost(h1, bH), _boost(h2, bH)
+        b0, l0, n0 = _decay3(rng, m, 79.0)
+        bb0, m0, nb0 = _decay3(rng, m, 82.0)
+        acc = 0.0
+        for par_t in (1, -1):
+            for par_tb in (1, -1):
+                bt, btb = pt[1:] / pt[0], ptb[1:] / ptb[0]
+                pb, pl, pn = (_boost(np.array([v[0], *(par_t * v[1:])]), bt) for v in (b0, l0, n0))
+                pbb, pm, pnb = (_boost(np.array([v[0], *(par_tb * v[1:])]), btb) for v in (bb0, m0, nb0))
+                w1, w2 = pl + pn, pm + pnb
+                qh = h1 + h2
+                dens = (wt * m) ** 4 * \
+                    ((dot(w1, w1) - mw * mw) ** 2 + (mw * ww) ** 2) * \
+                    ((dot(w2, w2) - mw * mw) ** 2 + (mw * ww) ** 2) * \
+                    ((dot(qh, qh) - mh * mh) ** 2 + (mh * wh) ** 2)
+                acc += ora.msq_tth(P, channel, k1, k2, pb, pl, pn, pbb, pm, pnb, h1, h2) * dens
+                ct = 8 * dot(pt, pl) * dot(pb, pn)
+                ctb = 8 * dot(ptb, pm) * dot(pbb, pnb)
+        prod = ora.msq_tth_production(P, channel, k1, k2, pt, ptb, pH)
+        want = prod * (gw2 / 2) ** 4 * ct * ctb * 3 * yb * yb * 4 * dot(h1, h2)
+        assert acc / 4 == pytest.approx(want, rel=1e-9, abs=0)
