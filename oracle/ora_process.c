@@ -20,8 +20,8 @@
 #include "oracle.h"
 #include "ora_dirac.h"
 
-int ora_dims(int kind) { return kind == 0 ? 2 : kind == 1 ? 4 : kind == 2 ? 7 : 6; }
-int ora_nperm(int kind) { return kind == 2 ? 24 : kind == 3 ? 2 : 1; }
+int ora_dims(int kind) { return kind == 0 ? 2 : kind == 1 ? 4 : kind == 2 ? 7 : kind == 3 ? 6 : 8; }
+int ora_nperm(int kind) { return kind == 2 ? 24 : kind == 3 ? 2 : kind == 4 ? 12 : 1; }
 
 double ora_pdf(const ora_process* P, int type, double x) {
   if (!(x > 0.0 && x < 1.0)) return 0.0;
@@ -138,7 +138,7 @@ static int nu_roots(rv4 pl, double nx, double ny, double q2, double* pz, double*
 
 typedef struct {
   int nfs;
-  rv4 lab[6];
+  rv4 lab[8];
   double jac;   /* product of the physics-map Jacobians */
   double meas;  /* prod 1/((2pi)^3 2E) and E^2 sin(theta) measure factors */
   double tf;    /* product of transfer functions */
@@ -374,6 +374,110 @@ static int states_ttdl(const ora_process* P, const ora_tf* T, const float* rec, 
   return n;
 }
 
+/* Dilepton ttH (Sec. 3-4, Eq. "integrand" with Eq. "mhsolve"): t -> b l+ nu,
+ * tbar -> bbar mu- nubar, H -> b1 b2; leptons and jet directions exact, the four
+ * b-jet energies with the double-Gaussian TF. perm (0..11) picks the jets (objects
+ * 2..5) of the b and the bbar -- the (perm / 3)-th jet and the (perm % 3)-th of the
+ * other three -- and gives the remaining two to the Higgs pair in object order (the
+ * two energy solutions below cover both energy orderings of the pair, so the pair is
+ * unordered). Variables: x0..x5 as in dilepton ttbar; x6 -> f = E1 + E2 log-uniform
+ * over [lo1 + lo2, hi1 + hi2] (the sum of the two jet windows); x7 -> m_H^2
+ * (Breit-Wigner map over [0, f^2 (1 - cos theta_12) / 2], the largest invariant mass
+ * two massless partons of energy sum f along these directions reach). Given f and
+ * m_H^2 = 2 E1 E2 (1 - cos theta_12), E1,2 = (f +- sqrt(f^2 - 4 E1 E2)) / 2, both
+ * orderings, each with 1 / |d(f, m_H^2)/d(E1, E2)| = 1 / (2 (1 - cos theta_12) |E1 - E2|);
+ * an energy outside its jet window has no weight. Then the missing pT is the visible
+ * imbalance and the neutrinos follow from Eq. "dilepsolv" as for dilepton ttbar. */
+static void tth_perm(int perm, int* jb, int* jbb, int* j1, int* j2) {
+  int rest[3], n = 0;
+  const int ib = perm / 3;
+  for (int j = 0; j < 4; ++j)
+    if (j != ib) rest[n++] = j;
+  *jb = 2 + ib;
+  *jbb = 2 + rest[perm % 3];
+  int h[2], m = 0;
+  for (int k = 0; k < 3; ++k)
+    if (k != perm % 3) h[m++] = rest[k];
+  *j1 = 2 + h[0];
+  *j2 = 2 + h[1];
+}
+
+static int states_tthdl(const ora_process* P, const ora_tf* T, const float* rec, int perm,
+                        const double* x, state_t* st) {
+  if (perm < 0 || perm > 11) return 0;
+  int ob, obb, o1, o2;
+  tth_perm(perm, &ob, &obb, &o1, &o2);
+  obj_t lp = get_obj(rec, 0), lm = get_obj(rec, 1);
+  obj_t jb = get_obj(rec, ob), jbb = get_obj(rec, obb), h1 = get_obj(rec, o1), h2 = get_obj(rec, o2);
+  const double s = P->sqrt_s * P->sqrt_s;
+  double lo, hi;
+  jet_window(P, T, jb.E, &lo, &hi);
+  double L = log(hi / lo);
+  const double Eb = lo * exp(x[0] * L), J0 = Eb * L;
+  jet_window(P, T, jbb.E, &lo, &hi);
+  L = log(hi / lo);
+  const double Ebb = lo * exp(x[1] * L), J1 = Ebb * L;
+  rv4 pb = massless(Eb, jb.n), pbb = massless(Ebb, jbb.n);
+  rv4 plp = massless(lp.E, lp.n), plm = massless(lm.E, lm.n);
+  double j2, j3, j4, j5;
+  const double q2wp = bw_map(0.0, s, P->mw, P->ww, x[2], &j2);
+  const double q2wm = bw_map(0.0, s, P->mw, P->ww, x[3], &j3);
+  const double lo_t = q2wp + 2.0 * rv_dot(pb, plp), lo_tb = q2wm + 2.0 * rv_dot(pbb, plm);
+  if (!(lo_t < s && lo_tb < s)) return 0;
+  const double q2t = bw_map(lo_t, s, P->mt, P->wt, x[4], &j4);
+  const double q2tb = bw_map(lo_tb, s, P->mt, P->wt, x[5], &j5);
+  /* the Higgs pair */
+  double lo1, hi1, lo2, hi2;
+  jet_window(P, T, h1.E, &lo1, &hi1);
+  jet_window(P, T, h2.E, &lo2, &hi2);
+  const double Lf = log((hi1 + hi2) / (lo1 + lo2));
+  const double f = (lo1 + lo2) * exp(x[6] * Lf), J6 = f * Lf;
+  const double dx = h1.n[0] - h2.n[0], dy = h1.n[1] - h2.n[1], dz = h1.n[2] - h2.n[2];
+  const double omc = 0.5 * (dx * dx + dy * dy + dz * dz); /* 1 - cos theta_12 */
+  if (!(omc > 0.0)) return 0;
+  double J7;
+  const double m2 = bw_map(0.0, 0.5 * f * f * omc, P->mh, P->wh, x[7], &J7);
+  const double disc = f * f - 2.0 * m2 / omc;
+  if (!(disc > 0.0)) return 0;
+  const double sq = sqrt(disc);
+  const double JH = 1.0 / (2.0 * omc * sq);
+  int n = 0;
+  for (int o = 0; o < 2; ++o) {
+    const double E1 = 0.5 * (f + (o == 0 ? sq : -sq)), E2 = f - E1;
+    if (!(E1 >= lo1 && E1 <= hi1 && E2 >= lo2 && E2 <= hi2)) continue;
+    rv4 p1 = massless(E1, h1.n), p2 = massless(E2, h2.n);
+    const double metx = -(plp.v[1] + plm.v[1] + pb.v[1] + pbb.v[1] + p1.v[1] + p2.v[1]);
+    const double mety = -(plp.v[2] + plm.v[2] + pb.v[2] + pbb.v[2] + p1.v[2] + p2.v[2]);
+    double nu[4 * 4], nub[4 * 4], jnu[4];
+    const int nn = ora_dilep_nu(pb.v, pbb.v, plp.v, plm.v, metx, mety, q2wp, q2wm, q2t, q2tb, nu,
+                                nub, jnu);
+    for (int r = 0; r < nn && n < ORA_MAXSOL; ++r) {
+      state_t* S = &st[n++];
+      S->nfs = 8;
+      S->lab[0] = pb;
+      S->lab[1] = plp;
+      S->lab[2] = rv(nu[4 * r], nu[4 * r + 1], nu[4 * r + 2], nu[4 * r + 3]);
+      S->lab[3] = pbb;
+      S->lab[4] = plm;
+      S->lab[5] = rv(nub[4 * r], nub[4 * r + 1], nub[4 * r + 2], nub[4 * r + 3]);
+      S->lab[6] = p1;
+      S->lab[7] = p2;
+      S->jac = J0 * J1 * j2 * j3 * j4 * j5 * J6 * J7 * JH * jnu[r];
+      S->meas = 1.0;
+      for (int i = 0; i < 8; ++i) S->meas *= inv_ps(S->lab[i].v[0]);
+      S->meas *= Eb * Eb * jb.sin_theta * Ebb * Ebb * jbb.sin_theta * E1 * E1 * h1.sin_theta *
+                 E2 * E2 * h2.sin_theta;
+      S->tf = dgauss(T, jb.E, Eb) * dgauss(T, jbb.E, Ebb) * dgauss(T, h1.E, E1) *
+              dgauss(T, h2.E, E2);
+      S->aux[0] = q2wp;
+      S->aux[1] = q2wm;
+      S->aux[2] = q2t;
+      S->aux[3] = q2tb;
+    }
+  }
+  return n;
+}
+
 static int build_states(const ora_process* P, const ora_tf* T, const float* rec, int perm,
                         const double* x, state_t* st) {
   memset(st, 0, ORA_MAXSOL * sizeof(state_t));
@@ -382,6 +486,7 @@ static int build_states(const ora_process* P, const ora_tf* T, const float* rec,
     case 1: return states_w(P, T, rec, x, st);
     case 2: return states_tt(P, T, rec, perm, x, st);
     case 3: return states_ttdl(P, T, rec, perm, x, st);
+    case 4: return states_tthdl(P, T, rec, perm, x, st);
   }
   return 0;
 }
@@ -418,6 +523,18 @@ static double flavour_sum(const ora_process* P, const rv4* b, rv4 k1, rv4 k2, do
     int charge = rec[3] == 4.0f ? +1 : -1;
     sum += fq1 * fqb2 * ora_msq_w(P, charge, k1.v, k2.v, b[0].v, b[1].v);
     sum += fqb1 * fq2 * ora_msq_w(P, charge, k2.v, k1.v, b[0].v, b[1].v);
+  } else if (P->kind == 4) {   /* dilepton ttH */
+    sum += fg1 * fg2 *
+           ora_msq_tth(P, 0, k1.v, k2.v, b[0].v, b[1].v, b[2].v, b[3].v, b[4].v, b[5].v, b[6].v,
+                       b[7].v);
+    for (int fl = 0; fl < 2; ++fl) {
+      sum += fq1 * fqb2 *
+             ora_msq_tth(P, 1, k1.v, k2.v, b[0].v, b[1].v, b[2].v, b[3].v, b[4].v, b[5].v,
+                         b[6].v, b[7].v);
+      sum += fqb1 * fq2 *
+             ora_msq_tth(P, 1, k2.v, k1.v, b[0].v, b[1].v, b[2].v, b[3].v, b[4].v, b[5].v,
+                         b[6].v, b[7].v);
+    }
   } else {   /* ttbar (kind 2) and dilepton ttbar (kind 3) */
     sum += fg1 * fg2 *
            ora_msq_ttbar(P, 0, k1.v, k2.v, b[0].v, b[1].v, b[2].v, b[3].v, b[4].v, b[5].v);
@@ -438,7 +555,7 @@ static double flavour_sum(const ora_process* P, const rv4* b, rv4 k1, rv4 k2, do
  * aux (optional): x1, x2, s-hat, PDF-weighted |M|^2. */
 static double state_weight(const ora_process* P, const state_t* S, const float* rec,
                            double* aux) {
-  rv4 b[6], k1, k2;
+  rv4 b[8], k1, k2;
   double x1, x2;
   to_parton_frame(P, S, b, &k1, &k2, &x1, &x2);
   if (!(x1 > 0.0 && x1 < 1.0 && x2 > 0.0 && x2 < 1.0)) return 0.0;
@@ -458,8 +575,8 @@ static double state_weight(const ora_process* P, const state_t* S, const float* 
  * final-state momenta in the process's lab order, k12: q1 then q2). */
 double ora_flavour_msq(const ora_process* P, const double* fs, const double* k12, double x1,
                        double x2, const float* rec) {
-  rv4 b[6];
-  for (int i = 0; i < 6; ++i) b[i] = rv(fs[4 * i], fs[4 * i + 1], fs[4 * i + 2], fs[4 * i + 3]);
+  rv4 b[8];
+  for (int i = 0; i < 8; ++i) b[i] = rv(fs[4 * i], fs[4 * i + 1], fs[4 * i + 2], fs[4 * i + 3]);
   rv4 k1 = rv(k12[0], k12[1], k12[2], k12[3]), k2 = rv(k12[4], k12[5], k12[6], k12[7]);
   return flavour_sum(P, b, k1, k2, x1, x2, rec);
 }
@@ -510,7 +627,7 @@ int ora_kinematics(const ora_process* P, const ora_tf* T, const float* rec, int 
   state_t st[ORA_MAXSOL];
   int n = build_states(P, T, rec, perm, x, st);
   if (root >= n) return n;
-  rv4 b[6], k1, k2;
+  rv4 b[8], k1, k2;
   double x1, x2;
   to_parton_frame(P, &st[root], b, &k1, &k2, &x1, &x2);
   for (int i = 0; i < st[root].nfs; ++i)

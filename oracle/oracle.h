@@ -32,7 +32,8 @@ extern "C" {
 #endif
 
 typedef struct {
-  int32_t kind; /* 0 Drell-Yan, 1 W -> e nu, 2 semileptonic ttbar */
+  int32_t kind; /* 0 Drell-Yan, 1 W -> e nu, 2 semileptonic ttbar, 3 dilepton ttbar,
+                 * 4 dilepton ttH (H -> b bbar) */
   int32_t pad;
   double sqrt_s;
   double mz, wz, mw, ww, mt, wt;
@@ -65,7 +66,7 @@ typedef struct {
 #define ORA_NG 128      /* VEGAS bins per dimension */
 #define ORA_MAXD 8
 #define ORA_REC 32
-#define ORA_MAXSOL 4    /* kinematic solutions per point (dilepton ttbar: up to 4) */
+#define ORA_MAXSOL 8    /* kinematic solutions per point (dilepton ttH: 2 Higgs-pair x 4 neutrino) */
 
 int ora_dims(int kind);
 int ora_nperm(int kind);

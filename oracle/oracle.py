@@ -210,14 +210,15 @@ def integrand(P, T, rec, perm, x):
 def kinematics(P, T, rec, perm, x, root):
     rec, rp = _rec_ptr(rec)
     x, xp = _d(x)
-    fs = np.zeros(24)
-    lab = np.zeros(24)
+    fs = np.zeros(32)
+    lab = np.zeros(32)
     k12 = np.zeros(8)
     aux = np.zeros(8)
     n = load().ora_kinematics(C.byref(P), C.byref(T), rp, perm, xp, root,
                               fs.ctypes.data_as(_dp), lab.ctypes.data_as(_dp),
                               k12.ctypes.data_as(_dp), aux.ctypes.data_as(_dp))
-    return {"n": n, "fs": fs.reshape(6, 4), "lab": lab.reshape(6, 4), "k12": k12.reshape(2, 4),
+    nfs = 2 if P.kind < 2 else (8 if P.kind == 4 else 6)
+    return {"n": n, "fs": fs.reshape(8, 4)[:nfs], "lab": lab.reshape(8, 4)[:nfs], "k12": k12.reshape(2, 4),
             "aux": aux}
 
 
@@ -225,7 +226,7 @@ def integrand_roots(P, T, rec, perm, x):
     """Per-root contributions of the integrand at x (a list of 0-2 floats)."""
     rec, rp = _rec_ptr(rec)
     x, xp = _d(x)
-    w = np.zeros(4)
+    w = np.zeros(8)
     n = load().ora_integrand_roots(C.byref(P), C.byref(T), rp, perm, xp, w.ctypes.data_as(_dp))
     return list(w[:n])
 
@@ -234,7 +235,9 @@ def flavour_msq(P, fs, k12, x1, x2, rec):
     """PDF-weighted, flavour-summed |M|^2 at the parton-frame momenta fs (6, 4) and
     k12 (2, 4), with the record supplying the lepton charge where it matters."""
     rec, rp = _rec_ptr(rec)
-    fs, fp_ = _d(np.asarray(fs).reshape(-1))
+    f8 = np.zeros((8, 4))
+    f8[:len(fs)] = np.asarray(fs)
+    fs, fp_ = _d(f8.reshape(-1))
     k12, kp = _d(np.asarray(k12).reshape(-1))
     return load().ora_flavour_msq(C.byref(P), fp_, kp, x1, x2, rp)
 

@@ -75,9 +75,10 @@ DEFAULT_TF = {
 PROC_TTBAR_DILEP = 3
 # dilepton ttbar: leptons measured exactly, b jets as in semileptonic ttbar
 DEFAULT_TF[PROC_TTBAR_DILEP] = dict(DEFAULT_TF[PROC_TTBAR])
+DEFAULT_TF[4] = dict(DEFAULT_TF[PROC_TTBAR])   # dilepton ttH
 
-DIMS = {PROC_DY: 2, PROC_W: 4, PROC_TTBAR: 7, PROC_TTBAR_DILEP: 6}
-NPERM = {PROC_DY: 1, PROC_W: 1, PROC_TTBAR: 24, PROC_TTBAR_DILEP: 2}
+DIMS = {PROC_DY: 2, PROC_W: 4, PROC_TTBAR: 7, PROC_TTBAR_DILEP: 6, 4: 8}
+NPERM = {PROC_DY: 1, PROC_W: 1, PROC_TTBAR: 24, PROC_TTBAR_DILEP: 2, 4: 12}
 
 # The five workloads: (process, events, points per event, base seed).
 SEED_BASE = 0x4D454D00
@@ -461,8 +462,101 @@ def gen_ttbar_dilep(n, seed, tf=None, truth=False):
     return (out, tr) if truth else out
 
 
+PROC_TTH_DILEP = 4
+
+
+def tth_perm_index(jb, jbb):
+    """Assignment index (0..11) of the dilepton ttH records: jets jb and jbb (0..3,
+    objects 2..5) are the b and the bbar, the other two the Higgs pair (unordered)."""
+    rest = [j for j in range(4) if j != jb]
+    return 3 * jb + rest.index(jbb)
+
+
+def gen_tth_dilep(n, seed, tf=None, truth=False):
+    """Dilepton ttH events (Sec. 3-4, the signal of the paper's hadron-level
+    analysis): t -> b e+ nu, tbar -> bbar mu- nubar, H -> b bbar. Partonic mass
+    uniform in [m_t1 + m_t2 + m_H + 20 GeV, 1500 GeV], rapidity U[-1, 1]; the t tbar
+    system mass uniform over its allowed range, two-body splittings isotropic; t, W
+    masses from Breit-Wigners truncated at +-15 widths, m_H fixed (its width is
+    4 MeV). Leptons exact within |eta| <= 2.5; the four b jets within |eta| <= 2.5 and
+    E >= 20 GeV after double-Gaussian smearing, stored by decreasing measured energy.
+    Record: objects 0 e+, 1 mu-, 2..5 the b jets; [24], [25] MET = nu_T + nubar_T +
+    N(0, 15^2); [26] = 6; [27] = 4; [28] = tth_perm_index of the true b and bbar jets.
+    With truth=True also returns the (n, 8, 4) parton momenta of b, bbar, e+, mu-, nu,
+    nubar, b(H), bbar(H)."""
+    tf = tf or DEFAULT_TF[PROC_TTBAR]
+    P = DEFAULT_PROCESS
+    mh = P["mh"]
+    rng = np.random.Generator(np.random.Philox(seed))
+    out = np.zeros((n, RECORD_FLOATS), dtype=np.float32)
+    tr = np.zeros((n, 8, 4))
+    have = 0
+    while have < n:
+        m = max(1024, 2 * (n - have))
+        mt1 = _bw_mass_v(rng, P["mt"], P["wt"], 15.0, m)
+        mt2 = _bw_mass_v(rng, P["mt"], P["wt"], 15.0, m)
+        mw1 = _bw_mass_v(rng, P["mw"], P["ww"], 15.0, m)
+        mw2 = _bw_mass_v(rng, P["mw"], P["ww"], 15.0, m)
+        rs = rng.uniform(0.0, 1.0, m) * (1500.0 - (mt1 + mt2 + mh + 20.0)) + mt1 + mt2 + mh + 20.0
+        mtt = rng.uniform(0.0, 1.0, m) * (rs - mh - 1.0 - (mt1 + mt2 + 1.0)) + mt1 + mt2 + 1.0
+        y = rng.uniform(-1.0, 1.0, m)
+        sysp = np.stack([rs * np.cosh(y), 0 * y, 0 * y, rs * np.sinh(y)], axis=1)
+        hq, ttq = _two_body_v(rng, rs, np.full(m, mh), mtt)
+        t, tb = _two_body_v(rng, mtt, mt1, mt2)
+        t, tb = _boost_v(t, ttq), _boost_v(tb, ttq)
+        hq, t, tb = _boost_v(hq, sysp), _boost_v(t, sysp), _boost_v(tb, sysp)
+        b, wp = _two_body_v(rng, mt1, 0.0, mw1)
+        b, wp = _boost_v(b, t), _boost_v(wp, t)
+        lp, nu = _two_body_v(rng, mw1, 0.0, 0.0)
+        lp, nu = _boost_v(lp, wp), _boost_v(nu, wp)
+        bb, wm = _two_body_v(rng, mt2, 0.0, mw2)
+        bb, wm = _boost_v(bb, tb), _boost_v(wm, tb)
+        lm, nub = _two_body_v(rng, mw2, 0.0, 0.0)
+        lm, nub = _boost_v(lm, wm), _boost_v(nub, wm)
+        h1, h2 = _two_body_v(rng, np.full(m, mh), 0.0, 0.0)
+        h1, h2 = _boost_v(h1, hq), _boost_v(h2, hq)
+        ok = np.ones(m, dtype=bool)
+        for q in (lp, lm, b, bb, h1, h2):
+            ok &= np.abs(_eta_phi_v(q)[0]) <= 2.5
+
+        def smear(q):
+            rel = np.where(rng.uniform(size=m) < tf["jet_tail_w"], tf["jet_tail"], tf["jet_core"])
+            return q[:, 0] * (1.0 + rel * rng.standard_normal(m))
+        quarks = (b, bb, h1, h2)
+        Em = np.stack([smear(q) for q in quarks], axis=1)          # (m, 4) measured energies
+        ok &= np.all(Em >= 20.0, axis=1)
+        idx = np.nonzero(ok)[0][: n - have]
+        r = out[have: have + len(idx)]
+        for slot, (q, kind) in enumerate(((lp, KIND_E_PLUS), (lm, KIND_MU_MINUS))):
+            eta, phi, _ = _eta_phi_v(q[idx])
+            r[:, 4 * slot] = q[idx, 0]
+            r[:, 4 * slot + 1] = eta
+            r[:, 4 * slot + 2] = phi
+            r[:, 4 * slot + 3] = kind
+        order = np.argsort(-Em[idx], axis=1)                        # jets by decreasing E
+        for k in range(4):
+            src = order[:, k]
+            Ek = Em[idx, src]
+            qk = np.stack([quarks[j][idx] for j in range(4)], axis=1)[np.arange(len(idx)), src]
+            eta, phi, _ = _eta_phi_v(qk)
+            r[:, 4 * (2 + k)] = Ek
+            r[:, 4 * (2 + k) + 1] = eta
+            r[:, 4 * (2 + k) + 2] = phi
+            r[:, 4 * (2 + k) + 3] = KIND_JET
+        r[:, 24] = (nu[idx, 1] + nub[idx, 1]) + tf["met_sigma"] * rng.standard_normal(len(idx))
+        r[:, 25] = (nu[idx, 2] + nub[idx, 2]) + tf["met_sigma"] * rng.standard_normal(len(idx))
+        r[:, 26] = 6
+        r[:, 27] = PROC_TTH_DILEP
+        slot_of = np.argsort(order, axis=1)                         # quark -> jet slot
+        r[:, 28] = [tth_perm_index(int(a), int(c)) for a, c in zip(slot_of[:, 0], slot_of[:, 1])]
+        for k, q in enumerate((b, bb, lp, lm, nu, nub, h1, h2)):
+            tr[have: have + len(idx), k] = q[idx]
+        have += len(idx)
+    return (out, tr) if truth else out
+
+
 GENERATORS = {PROC_DY: gen_dy, PROC_W: gen_w, PROC_TTBAR: gen_ttbar,
-              PROC_TTBAR_DILEP: gen_ttbar_dilep}
+              PROC_TTBAR_DILEP: gen_ttbar_dilep, PROC_TTH_DILEP: gen_tth_dilep}
 
 
 def gen_events(proc, n, seed):

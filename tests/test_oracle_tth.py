@@ -195,3 +195,149 @@ def test_tth_full_chain_factorises(ora, params, channel):
         prod = ora.msq_tth_production(P, channel, k1, k2, pt, ptb, pH)
         want = prod * (gw2 / 2) ** 4 * ct * ctb * 3 * yb * yb * 4 * dot(h1, h2)
         assert acc / 4 == pytest.approx(want, rel=1e-9, abs=0)
+
+
+# ---------------------------------------------------------------------------
+# The dilepton ttH integrand (process kind 4): Eq. "integrand" with the neutrinos
+# from Eq. "dilepsolv" and the Higgs pair's (f, m_H^2) variables of Eq. "mhsolve".
+# ---------------------------------------------------------------------------
+KIND_TTH = 4
+
+
+def _tth_setup(ora, synth):
+    return (ora.process(KIND_TTH, synth.DEFAULT_PROCESS),
+            ora.tf(synth.DEFAULT_TF[KIND_TTH]))
+
+
+@pytest.fixture(scope="module")
+def tth_events(synth):
+    return synth.gen_tth_dilep(4, 91)
+
+
+def _dir(p):
+    return p[1:] / np.linalg.norm(p[1:])
+
+
+def _obj_dir(rec, o):
+    eta, phi = float(rec[4 * o + 1]), float(rec[4 * o + 2])
+    return np.array([math.cos(phi) / math.cosh(eta), math.sin(phi) / math.cosh(eta), math.tanh(eta)])
+
+
+def _which_object(rec, p):
+    d = _dir(p)
+    best = min(range(2, 6), key=lambda o: np.linalg.norm(_obj_dir(rec, o) - d))
+    assert np.linalg.norm(_obj_dir(rec, best) - d) < 1e-6
+    return best
+
+
+def _states(ora, P, T, rec, perm, x):
+    n = ora.kinematics(P, T, rec, perm, x, 0)["n"]
+    return [ora.kinematics(P, T, rec, perm, x, r) for r in range(n)]
+
+
+def _find_point(ora, P, T, rec, perm, rng, tries=4000):
+    for _ in range(tries):
+        x = rng.uniform(0.02, 0.98, size=8)
+        if ora.kinematics(P, T, rec, perm, x, 0)["n"] > 0:
+            return x
+    return None
+
+
+def test_tth_dims_and_assignments(ora, synth, tth_events):
+    """8 variables and 12 jet assignments: every ordered (b, bbar) pair of the four
+    jets once, the other two jets going to the Higgs pair; the generator's truth
+    index follows the same convention."""
+    P, T = _tth_setup(ora, synth)
+    assert ora.dims(KIND_TTH) == 8 and ora.nperm(KIND_TTH) == 12
+    rng = np.random.default_rng(50)
+    rec = tth_events[0]
+    pairs = set()
+    for perm in range(12):
+        x = _find_point(ora, P, T, rec, perm, rng)
+        assert x is not None
+        lab = _states(ora, P, T, rec, perm, x)[0]["lab"]
+        ob, obb, o1, o2 = (_which_object(rec, lab[i]) for i in (0, 3, 6, 7))
+        assert len({ob, obb, o1, o2}) == 4
+        assert synth.tth_perm_index(ob - 2, obb - 2) == perm
+        pairs.add((ob, obb))
+    assert len(pairs) == 12
+
+
+def test_tth_conservation_and_virtualities(ora, synth, tth_events):
+    P, T = _tth_setup(ora, synth)
+    rng = np.random.default_rng(51)
+    checked = 0
+    for rec in tth_events:
+        for _ in range(150):
+            x = rng.uniform(0.02, 0.98, size=8)
+            perm = int(rng.integers(0, 12))
+            for k in _states(ora, P, T, rec, perm, x):
+                fs, lab, k12, aux = k["fs"], k["lab"], k["k12"], k["aux"]
+                assert fs.shape == (8, 4)
+                tot = fs.sum(axis=0)
+                assert np.allclose(k12[0] + k12[1], tot, rtol=0, atol=1e-12 * tot[0])
+                ltot = lab.sum(axis=0)
+                assert abs(ltot[1]) < 1e-10 * ltot[0] and abs(ltot[2]) < 1e-10 * ltot[0]
+                for p in lab:
+                    assert abs(dot(p, p)) < 1e-10 * p[0] ** 2
+                b, lp, nu, bb, lm, nub, h1, h2 = lab
+                want = (dot(lp + nu, lp + nu), dot(lm + nub, lm + nub),
+                        dot(b + lp + nu, b + lp + nu), dot(bb + lm + nub, bb + lm + nub))
+                for g, w in zip(aux[:4], want):
+                    assert g == pytest.approx(w, rel=1e-9, abs=0)
+                # the Higgs-pair energies lie inside their jet windows
+                tf = synth.DEFAULT_TF[KIND_TTH]
+                for p in (h1, h2):
+                    Em = float(rec[4 * _which_object(rec, p)])
+                    assert Em / tf["jet_lo_div"] * (1 - 1e-12) <= p[0] <= Em * tf["jet_hi_mul"] * (1 + 1e-12)
+                checked += 1
+    assert checked > 40
+
+
+def _phys8(lab):
+    """(E_b, E_bbar, nu_x, nu_y, nu_z, nubar_z, E_b1, E_b2)."""
+    return np.array([lab[0][0], lab[3][0], lab[2][1], lab[2][2], lab[2][3], lab[5][3],
+                     lab[6][0], lab[7][0]])
+
+
+def test_tth_jacobian_is_determinant_of_the_map(ora, synth, tth_events):
+    """Every state's Jacobian equals |det d(E_b, E_bbar, nu_x, nu_y, nu_z, nubar_z, E_b1,
+    E_b2)/dx| by central differences of the map (the state at x +- h is the one
+    nearest in those variables): this fixes the (f, m_H^2) transform and its
+    two-solution Jacobian together with the neutrino part."""
+    P, T = _tth_setup(ora, synth)
+    rng = np.random.default_rng(52)
+    n_ok = 0
+    for rec in tth_events:
+        for _ in range(60):
+            x = rng.uniform(0.05, 0.95, size=8)
+            perm = int(rng.integers(0, 12))
+            for k in _states(ora, P, T, rec, perm, x):
+                f0 = _phys8(k["lab"])
+                M = np.zeros((8, 8))
+                ok = True
+                for j in range(8):
+                    # h = 1e-5: the narrow Higgs Breit-Wigner makes the map steep, so smaller
+                    # steps lose digits to cancellation (truncation at 1e-5 is ~1e-7)
+                    h = 1e-5
+                    cols = []
+                    for sgn in (1, -1):
+                        xs = x.copy()
+                        xs[j] += sgn * h
+                        cand = [_phys8(q["lab"]) for q in _states(ora, P, T, rec, perm, xs)]
+                        if not cand:
+                            ok = False
+                            break
+                        d = sorted((np.max(np.abs(c - f0)), i) for i, c in enumerate(cand))
+                        if len(d) > 1 and d[1][0] < 10 * d[0][0]:
+                            ok = False
+                            break
+                        cols.append(cand[d[0][1]])
+                    if not ok:
+                        break
+                    M[:, j] = (cols[0] - cols[1]) / (2 * h)
+                if not ok:
+                    continue
+                assert abs(np.linalg.det(M)) == pytest.approx(k["aux"][6], rel=2e-5, abs=0)
+                n_ok += 1
+    assert n_ok >= 10
