@@ -48,13 +48,20 @@ enum {
   MEM_PROC_DY = 0,    /* q qbar -> photon/Z -> mu- mu+ ; 2 integration dims, 1 permutation */
   MEM_PROC_W = 1,     /* u dbar -> W+ -> e+ nu (or W-) ; 4 dims, 1 permutation */
   MEM_PROC_TTBAR = 2, /* gg, q qbar -> t tbar -> b l+ nu bbar d ubar ; 7 dims, 24 jet permutations */
-  MEM_PROC_TTBAR_DILEP = 3 /* gg, q qbar -> t tbar -> b l+ nu bbar mu- nubar (Sec. 3-4, Eq.
+  MEM_PROC_TTBAR_DILEP = 3, /* gg, q qbar -> t tbar -> b l+ nu bbar mu- nubar (Sec. 3-4, Eq.
                             * "dilepsolv": both neutrinos from the four virtualities and the
                             * visible pT imbalance, up to 4 solutions per point); 6 dims, 2 b-jet
                             * assignments. Records: objects 0 l+ (kind 4), 1 mu- (kind 1), 2 and 3
                             * the b jets (kind 5); leptons and jet directions exact, jet energies
                             * with the double Gaussian. Fixed-budget, adaptive-budget and batched
                             * integration and mem_eval_points; the learned-sampler calls reject it. */
+  MEM_PROC_TTH_DILEP = 4   /* gg, q qbar -> t tbar H -> (b l+ nu)(bbar mu- nubar)(b bbar) (Sec. 3-4,
+                            * Eq. "integrand" with Eq. "mhsolve"): 8 dims (b, bbar energies, W and
+                            * top virtualities, the Higgs pair's f = E1 + E2 and m_H^2), 12 jet
+                            * assignments. Records: objects 0 l+ (kind 4), 1 mu- (kind 1), 2..5 the
+                            * b jets (kind 5). Needs mh, wh, mb in the process description.
+                            * mem_integrate at a fixed budget (no target_rel_err),
+                            * mem_integrate_noalloc and mem_eval_points. */
 };
 
 typedef struct mem_process mem_process; /* opaque, library-owned */
@@ -69,6 +76,7 @@ typedef struct {
   double mz, wz, mw, ww, mt, wt; /* masses and widths */
   double alpha, sw2, alpha_s;    /* e^2/4pi, sin^2(theta_W), g_s^2/4pi */
   double pdf_A[3], pdf_a[3], pdf_b[3];
+  double mh, wh, mb;  /* Higgs mass and width, b mass in the b Yukawa (MEM_PROC_TTH_DILEP only) */
 } mem_process_desc;
 
 /* Transfer functions T(X|Y) (Sec. 1): delta functions for all directions and

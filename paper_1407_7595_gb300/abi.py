@@ -34,7 +34,8 @@ class mem_process_desc(C.Structure):
                 ("mz", C.c_double), ("wz", C.c_double), ("mw", C.c_double), ("ww", C.c_double),
                 ("mt", C.c_double), ("wt", C.c_double), ("alpha", C.c_double),
                 ("sw2", C.c_double), ("alpha_s", C.c_double), ("pdf_A", C.c_double * 3),
-                ("pdf_a", C.c_double * 3), ("pdf_b", C.c_double * 3)]
+                ("pdf_a", C.c_double * 3), ("pdf_b", C.c_double * 3),
+                ("mh", C.c_double), ("wh", C.c_double), ("mb", C.c_double)]
 
 
 class mem_tf_desc(C.Structure):
@@ -146,6 +147,8 @@ def process_desc(kind, params):
         setattr(d, k, float(params[k]))
     for k in ("pdf_A", "pdf_a", "pdf_b"):
         getattr(d, k)[:] = [float(v) for v in params[k]]
+    for k in ("mh", "wh", "mb"):   # Higgs parameters (ttH only)
+        setattr(d, k, float(params.get(k, 0.0)))
     return d
 
 

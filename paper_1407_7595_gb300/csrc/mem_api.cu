@@ -59,16 +59,18 @@ uint32_t strat_side(uint64_t n, int d, int k) {
 }
 
 int dims_of(int kind) {
-  return kind == PROC_DY ? 2 : kind == PROC_W ? 4 : kind == PROC_TTBAR ? 7 : kind == PROC_TTDL ? 6 : -1;
+  return kind == PROC_DY ? 2 : kind == PROC_W ? 4 : kind == PROC_TTBAR ? 7 : kind == PROC_TTDL ? 6
+       : kind == PROC_TTH ? 8 : -1;
 }
 int nperm_of(int kind) {
-  return kind == PROC_TTBAR ? 24 : kind == PROC_TTDL ? 2 : (kind == PROC_DY || kind == PROC_W) ? 1 : -1;
+  return kind == PROC_TTBAR ? 24 : kind == PROC_TTDL ? 2 : kind == PROC_TTH ? 12
+       : (kind == PROC_DY || kind == PROC_W) ? 1 : -1;
 }
 uint32_t chunk_points(int kind) {  // points of one frozen-grid CTA: THREADS x points per thread
   return THREADS * (uint32_t)(kind == PROC_DY ? PPT_DY
                               : kind == PROC_W ? PPT_W
-                              : kind == PROC_TTDL ? PPT_DL
-                                                  : PPT_TT);
+                              : (kind == PROC_TTDL || kind == PROC_TTH) ? PPT_DL
+                                                                        : PPT_TT);
 }
 
 cudaError_t launch_integrate(int kind, const IntegrateArgs& a, cudaStream_t st) {
@@ -77,6 +79,7 @@ cudaError_t launch_integrate(int kind, const IntegrateArgs& a, cudaStream_t st) 
     case PROC_W: return launch_integrate_w(a, st);
     case PROC_TTBAR: return launch_integrate_tt(a, st);
     case PROC_TTDL: return launch_integrate_ttdl(a, st);
+    case PROC_TTH: return launch_integrate_tth(a, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -85,7 +88,8 @@ size_t cache_size(int kind) {
   return kind == PROC_DY ? cache_size_dy()
          : kind == PROC_W ? cache_size_w()
          : kind == PROC_TTDL ? cache_size_ttdl()
-                             : cache_size_tt();
+         : kind == PROC_TTH ? cache_size_tth()
+                            : cache_size_tt();
 }
 
 cudaError_t launch_eval(int kind, const EvalArgs& a, cudaStream_t st) {
@@ -94,6 +98,7 @@ cudaError_t launch_eval(int kind, const EvalArgs& a, cudaStream_t st) {
     case PROC_W: return launch_eval_w(a, st);
     case PROC_TTBAR: return launch_eval_tt(a, st);
     case PROC_TTDL: return launch_eval_ttdl(a, st);
+    case PROC_TTH: return launch_eval_tth(a, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -247,6 +252,12 @@ ProcConst make_proc_const(const mem_process_desc& d) {
   const double tt = gs2 * gs2 * std::pow(0.5 * g2, 4) * 64.0 * 6.0;
   P.tt_gg = (float)(tt / (4.0 * 64.0));
   P.tt_qq = (float)(tt / (4.0 * 9.0));
+  // ttH: Yukawas y = m / v, v = 2 m_W / g_W; W- -> mu- nubar is 1 of the 6 channels in tt
+  const double vev = 2.0 * d.mw / std::sqrt(g2);
+  const double yt = d.mt / vev, yb = d.mb / vev;
+  P.mh2 = (float)(d.mh * d.mh);
+  P.mhgh = (float)(d.mh * d.wh);
+  P.tth_c = (float)(yt * yt * 3.0 * yb * yb / 6.0);
   for (int t = 0; t < 3; ++t) {
     P.pdfA[t] = (float)d.pdf_A[t];
     P.pdfa[t] = (float)d.pdf_a[t];
@@ -260,6 +271,8 @@ ProcConst make_proc_const(const mem_process_desc& d) {
   const double tp = 2.0 * PI_D;
   if (d.kind == PROC_DY) P.prefactor = (2.0 / s) / (4.0 * tp * tp);
   else if (d.kind == PROC_W) P.prefactor = (2.0 / s) / (8.0 * tp * tp);
+  else if (d.kind == PROC_TTH)   // eight final-state particles
+    P.prefactor = (2.0 / s) * std::pow(tp, 4.0 - 24.0) / 256.0 / TTH_WEIGHT_SCALE / TTH_DEC_SCALE;
   else P.prefactor = (2.0 / s) * std::pow(tp, 4.0 - 18.0) / 64.0 / TT_WEIGHT_SCALE;
   return P;
 }
@@ -300,7 +313,7 @@ mem_status check_tf(const mem_tf_desc* tf, int kind) {
     return fail(MEM_ERR_INVALID_ARG, "lepton TF needs lep_rel > 0, window_k > 0, lep_rel*window_k < 1");
   if ((kind == PROC_W || kind == PROC_TTBAR) && !(tf->met_sigma > 0 && tf->met_box_k > 0))
     return fail(MEM_ERR_INVALID_ARG, "MET TF needs met_sigma > 0 and met_box_k > 0");
-  if ((kind == PROC_TTBAR || kind == PROC_TTDL) &&
+  if ((kind == PROC_TTBAR || kind == PROC_TTDL || kind == PROC_TTH) &&
       !(tf->jet_core > 0 && tf->jet_tail > 0 && tf->jet_tail_w >= 0 && tf->jet_tail_w <= 1 &&
         tf->jet_lo_div > 1 && tf->jet_hi_mul > 1))
     return fail(MEM_ERR_INVALID_ARG, "invalid jet TF parameters");
@@ -348,6 +361,9 @@ mem_status mem_create_process(const mem_process_desc* desc, mem_process** out) {
   for (double x : v)
     if (!(x > 0.0) || !std::isfinite(x)) return fail(MEM_ERR_INVALID_ARG, "masses, widths, couplings and sqrt_s must be positive");
   if (!(desc->sw2 < 1.0)) return fail(MEM_ERR_INVALID_ARG, "sw2 must be < 1");
+  if (desc->kind == PROC_TTH && !(desc->mh > 0.0 && desc->wh > 0.0 && desc->mb > 0.0 &&
+                                  std::isfinite(desc->mh + desc->wh + desc->mb)))
+    return fail(MEM_ERR_INVALID_ARG, "ttH needs mh, wh, mb > 0");
   for (int t = 0; t < 3; ++t)
     if (!(desc->pdf_A[t] > 0.0) || !std::isfinite(desc->pdf_a[t]) || !(desc->pdf_b[t] >= 0.0))
       return fail(MEM_ERR_INVALID_ARG, "PDF parameters need A > 0, finite a, b >= 0");

@@ -99,10 +99,12 @@ cudaError_t launch_integrate_dy(const IntegrateArgs&, cudaStream_t);
 cudaError_t launch_integrate_w(const IntegrateArgs&, cudaStream_t);
 cudaError_t launch_integrate_tt(const IntegrateArgs&, cudaStream_t);
 cudaError_t launch_integrate_ttdl(const IntegrateArgs&, cudaStream_t);
+cudaError_t launch_integrate_tth(const IntegrateArgs&, cudaStream_t);
 cudaError_t launch_eval_dy(const EvalArgs&, cudaStream_t);
 cudaError_t launch_eval_w(const EvalArgs&, cudaStream_t);
 cudaError_t launch_eval_tt(const EvalArgs&, cudaStream_t);
 cudaError_t launch_eval_ttdl(const EvalArgs&, cudaStream_t);
+cudaError_t launch_eval_tth(const EvalArgs&, cudaStream_t);
 
 // constants and error reporting shared with entry points outside mem_api.cu
 ProcConst make_proc_const_from(const void* mem_process_desc_ptr);
@@ -113,6 +115,7 @@ size_t cache_size_dy();
 size_t cache_size_w();
 size_t cache_size_tt();
 size_t cache_size_ttdl();
+size_t cache_size_tth();
 size_t cache_size(int kind);
 
 struct BatchArgs;

@@ -13,12 +13,17 @@
 
 namespace mem {
 
-enum { PROC_DY = 0, PROC_W = 1, PROC_TTBAR = 2, PROC_TTDL = 3 };
+enum { PROC_DY = 0, PROC_W = 1, PROC_TTBAR = 2, PROC_TTDL = 3, PROC_TTH = 4 };
 
 // ttbar weights are carried in FP32 multiplied by 2^40 (an exact power of two,
 // divided out of the FP64 prefactor) so that products of small factors in
 // far-tail points stay in the FP32 normal range.
 constexpr double TT_WEIGHT_SCALE = 1099511627776.0;
+// Dilepton ttH: eight final-state particles and the Higgs Yukawas make the FP32
+// weight smaller still; its per-point constant carries 2^80 and its per-solution
+// decay factor 2^40 (both exact powers of two, divided out of the FP64 prefactor).
+constexpr double TTH_WEIGHT_SCALE = 1208925819614629174706176.0;
+constexpr double TTH_DEC_SCALE = 1099511627776.0;
 
 // Constants of a process, built on the host in FP64 and rounded once.
 struct ProcConst {
@@ -31,6 +36,8 @@ struct ProcConst {
   float dy_same[3], dy_opp[3];
   float w_coup;             // W: g^4 / 12
   float tt_gg, tt_qq;       // ttbar: couplings x colour x averaging factors
+  float mh2, mhgh;          // Higgs mass^2 and mass x width (ttH)
+  float tth_c;              // ttH over ttbar couplings: y_t^2 x 3 y_b^2 / 6
   float pdfA[3], pdfa[3], pdfb[3];
   int pdf_amode[3];         // 1: x^-1/2, 2: x^-1, 0: general power
   int pdf_bint[3];          // integer exponent of (1-x) if >= 0, else general power

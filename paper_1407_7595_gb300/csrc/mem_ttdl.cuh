@@ -26,7 +26,7 @@
 // root is then located in FP32 and finished by FP64 Newton steps. Roots are then
 // polished on the two conics (Newton in 2D, FP64).
 //
-// The solver's stages (dl_system, dl_real_roots, dl_bracket_root, dl_point) are
+// The solver's stages (dl_system(_met), dl_real_roots, dl_bracket_root, dl_point) are
 // kept out of line. Inlined into the integrand, this build (nvcc 13.0, sm_103a)
 // returned incomplete solution sets on about a third of the points of a test
 // batch -- the same functions called from a small kernel, or out of line, agree
@@ -124,7 +124,7 @@ __device__ __forceinline__ T dl_horner(const T* c, int deg, T x, T& dp) {
 // FP32 root of the polynomial c (degree deg) in [a, b], where it changes sign
 // (only the sign of fa is used): Newton steps, replaced by bisection whenever a
 // step leaves the shrinking bracket, to FP32 resolution.
-__device__ __noinline__ float dl_bracket32(const float* c, int deg, float a, float b, float fa) {
+static __device__ __noinline__ float dl_bracket32(const float* c, int deg, float a, float b, float fa) {
   float x = 0.5f * (a + b);
 #pragma unroll 1
   for (int it = 0; it < 64; ++it) {
@@ -147,7 +147,7 @@ __device__ __noinline__ float dl_bracket32(const float* c, int deg, float a, flo
 // the root the iteration then contracts by ~1e-7 per step, which from an
 // FP32-accurate start is the same two steps), bisection whenever a step leaves
 // the shrinking bracket.
-__device__ __noinline__ double dl_bracket_root(const double* c, int deg, double a, double b,
+static __device__ __noinline__ double dl_bracket_root(const double* c, int deg, double a, double b,
                                                double fa, double x0, double tol) {
   double x = (x0 > a && x0 < b) ? x0 : 0.5 * (a + b);
 #pragma unroll 1
@@ -182,7 +182,7 @@ __device__ __noinline__ double dl_bracket_root(const double* c, int deg, double 
 // location gives the exact sign); each root is located in FP32 and finished by
 // FP64 Newton steps inside its bracket. A critical point where the polynomial
 // vanishes to rounding is a double root and is kept once.
-__device__ __noinline__ int dl_real_roots(const double* c, int deg, double* roots) {
+static __device__ __noinline__ int dl_real_roots(const double* c, int deg, double* roots) {
   const double ilead = 1.0 / c[deg];
   float cf[5];
   float bound = 0.f;
@@ -297,11 +297,15 @@ struct DLSystem {
 };
 
 // Builds the system; returns the number of real roots x of the resultant (in xr).
-__device__ __noinline__ int dl_system(const double* b, const double* bb, const double* lp, const double* lm,
-                         double q2wp, double q2wm, double q2t, double q2tb, DLSystem& S,
-                         double* xr) {
-  S.mx = -(lp[1] + lm[1] + b[1] + bb[1]);
-  S.my = -(lp[2] + lm[2] + b[2] + bb[2]);
+// The missing pT (mx, my) is given: the negative visible pT sum of the event's own
+// final state (the dilepton ttbar form below adds the four objects; dilepton ttH
+// adds the Higgs pair too).
+static __device__ __noinline__ int dl_system_met(const double* b, const double* bb, const double* lp,
+                                          const double* lm, double mx, double my, double q2wp,
+                                          double q2wm, double q2t, double q2tb, DLSystem& S,
+                                          double* xr) {
+  S.mx = mx;
+  S.my = my;
   // 2 l.nu = q^2_W and 2 b.nu = q^2_t - q^2_W - 2 b.l (massless b, l, nu)
   const double blp = b[0] * lp[0] - b[1] * lp[1] - b[2] * lp[2] - b[3] * lp[3];
   const double bblm = bb[0] * lm[0] - bb[1] * lm[1] - bb[2] * lm[2] - bb[3] * lm[3];
@@ -340,9 +344,16 @@ __device__ __noinline__ int dl_system(const double* b, const double* bb, const d
   return dl_real_roots(R, deg, xr);
 }
 
+static __device__ __noinline__ int dl_system(const double* b, const double* bb, const double* lp,
+                                      const double* lm, double q2wp, double q2wm, double q2t,
+                                      double q2tb, DLSystem& S, double* xr) {
+  return dl_system_met(b, bb, lp, lm, -(lp[1] + lm[1] + b[1] + bb[1]),
+                       -(lp[2] + lm[2] + b[2] + bb[2]), q2wp, q2wm, q2t, q2tb, S, xr);
+}
+
 // One neutrino solution from a root x of the resultant: y, conic polish, the
 // residual and positive-energy checks. Returns false when the root is rejected.
-__device__ __noinline__ bool dl_point(const DLSystem& S, double xr, double& x, double& y) {
+static __device__ __noinline__ bool dl_point(const DLSystem& S, double xr, double& x, double& y) {
   const double num = -fma(fma(S.u[2], xr, S.u[1]), xr, S.u[0]);
   const double den = fma(S.v[1], xr, S.v[0]);
   if (fabs(den) > 1e-12 * (fabs(num) + 1.0)) {
