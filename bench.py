@@ -77,6 +77,8 @@ WORKLOAD_NAMES = {
     "ttdl": "dilepton ttbar (b l+ nu bbar mu- nubar; both neutrinos from the four "
             "virtualities, up to 4 solutions, FP64 solve), 6-dim integral x 2 b-jet "
             "assignments, 1024 events x 2^18 evaluations/event",
+    "tth": "dilepton ttH, H -> b bbar (Eq. integrand with Eq. mhsolve): 8-dim integral x 12 "
+           "jet assignments, 256 events x 12 x 2^16 evaluations/event",
 }
 
 
@@ -86,7 +88,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["w", "dy", "ttbar", "mix", "flow", "parton", "ttdl"],
+    ap.add_argument("--workload", choices=["w", "dy", "ttbar", "mix", "flow", "parton", "ttdl", "tth"],
                     default="w")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the events-to-1%% leg")
     ap.add_argument("--strat", type=int, default=0,
@@ -206,7 +208,8 @@ def cpu_baseline(kind, seed):
     from oracle import oracle as O
     # (events, evaluations per item): about 10 s of work on 16 Grace cores
     n_ev, n_pts = {synth.PROC_W: (64, 1 << 16), synth.PROC_DY: (16, 1 << 15),
-                   synth.PROC_TTBAR: (2, 1 << 10), synth.PROC_TTBAR_DILEP: (16, 1 << 12)}[kind]
+                   synth.PROC_TTBAR: (2, 1 << 10), synth.PROC_TTBAR_DILEP: (16, 1 << 12),
+                   synth.PROC_TTH_DILEP: (1, 1 << 11)}[kind]
     n_perm = synth.NPERM[kind]
     recs = synth.gen_events(kind, n_ev, seed)
     P = O.process(kind, synth.DEFAULT_PROCESS)
@@ -445,7 +448,7 @@ def run_ours(args):
         t_main = statistics.mean(main_ms) * 1e-3
         achieved = fpe * n_ev * n_perm * n_main / t_main / 1e12 if fpe else None
         dpi = DRAM_BYTES_PER_ITEM_MAIN.get(kind)
-        if kind == synth.PROC_TTBAR_DILEP:
+        if kind in (synth.PROC_TTBAR_DILEP, synth.PROC_TTH_DILEP):
             fpe = None
             f64 = FP64_FLOPS_PER_EVAL.get(kind)
             peak = FP64_PEAK_TFLOPS
@@ -457,7 +460,7 @@ def run_ours(args):
                             if dpi and not args.pdf_grid and not args.strat else None),
                 "peak_source": (f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                 f"{max_mhz:.0f} MHz max SM clock"
-                                if kind != synth.PROC_TTBAR_DILEP else
+                                if kind not in (synth.PROC_TTBAR_DILEP, synth.PROC_TTH_DILEP) else
                                 "nominal GB300 FP64 rate (the FP64 neutrino solution bounds "
                                 "this kernel)"),
                 "flops_per_eval": fpe,
@@ -484,7 +487,7 @@ def run_ours(args):
                "status_ok": ok, "median_rel_err": float(torch.median(err / prob).item()),
                "roofline": roof, "clocks": clocks, "e2e": e2e,
                "gpu_launches": 3 * args.steps}
-        if not args.no_adaptive:
+        if not args.no_adaptive and kind != synth.PROC_TTH_DILEP:   # ttH: fixed budget only
             out["to_1pct"] = adaptive_leg(abi, torch, events, proc, tf, n_ev,
                                           shard(rank, n_ev)["event_id_base"], sp, recs=recs)
         if not args.no_flow:

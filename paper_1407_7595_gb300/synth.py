@@ -92,6 +92,8 @@ WORKLOADS = {
     "parton": dict(proc=PROC_TTBAR, n_events=1 << 20, n_points=0, seed=SEED_BASE + 5),
     # dilepton ttbar (Sec. 3-4 hadron level without the Higgs): 6 dims x 2 b assignments
     "ttdl": dict(proc=3, n_events=1024, n_points=1 << 18, seed=SEED_BASE + 6),
+    # dilepton ttH (Sec. 3-4, the paper's hadron-level signal): 8 dims x 12 jet assignments
+    "tth": dict(proc=4, n_events=256, n_points=12 << 16, seed=SEED_BASE + 7),
 }
 
 
