@@ -112,6 +112,19 @@ double ora_msq_tth_production(const ora_process* P, int channel, const double* k
 double ora_msq_tth(const ora_process* P, int channel, const double* k1, const double* k2,
                    const double* pb, const double* pl, const double* pn, const double* pbb,
                    const double* pm, const double* pnb, const double* ph1, const double* ph2);
+/* g g (channel 0) or q qbar (channel 1) -> t tbar b bbar with on-shell tops and
+ * massless b quarks, all spins and colours summed, initial ones averaged (the ttbb
+ * background of Sec. 3-4). */
+double ora_msq_ttbb_production(const ora_process* P, int channel, const double* k1,
+                               const double* k2, const double* p1, const double* p2,
+                               const double* p3, const double* p4);
+double ora_ttbb_gauge_probe(const ora_process* P, const double* k1, const double* k2,
+                            const double* p1, const double* p2, const double* p3,
+                            const double* p4, int which, int hel);
+void ora_su3_check(double* out);
+void ora_ttbb_qq_ward_probe(const ora_process* P, const double* k1, const double* k2,
+                            const double* p1, const double* p2, const double* p3,
+                            const double* p4, double* out);
 double ora_tth_gauge_probe(const ora_process* P, const double* k1, const double* k2,
                            const double* pt, const double* ptb, const double* pH, int which,
                            int hel);

@@ -18,7 +18,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liboracle.so")
 SOURCES = ["ora_philox.c", "ora_dirac.c", "ora_matrix.c", "ora_process.c", "ora_vegas.c",
-           "ora_integrate.c", "ora_dilep.c"]
+           "ora_integrate.c", "ora_dilep.c", "ora_ttbb.c"]
 NG = 128
 REC = 32
 
@@ -117,6 +117,14 @@ def load():
     lib.ora_tth_gauge_probe.argtypes = [P, _dp, _dp, _dp, _dp, _dp, C.c_int, C.c_int]
     lib.ora_msq_tth.argtypes = [P, C.c_int] + [_dp] * 10
     lib.ora_msq_tth.restype = C.c_double
+    lib.ora_msq_ttbb_production.argtypes = [P, C.c_int] + [_dp] * 6
+    lib.ora_msq_ttbb_production.restype = C.c_double
+    lib.ora_ttbb_gauge_probe.argtypes = [P] + [_dp] * 6 + [C.c_int, C.c_int]
+    lib.ora_ttbb_gauge_probe.restype = C.c_double
+    lib.ora_ttbb_qq_ward_probe.argtypes = [P] + [_dp] * 7
+    lib.ora_ttbb_qq_ward_probe.restype = None
+    lib.ora_su3_check.argtypes = [_dp]
+    lib.ora_su3_check.restype = None
     lib.ora_tth_gauge_probe.restype = C.c_double
     lib.ora_top_decay_probe.argtypes = [P, _dp, _dp, _dp, _dp]
     lib.ora_antitop_decay_probe.argtypes = [P, _dp, _dp, _dp, _dp]
@@ -290,6 +298,29 @@ def msq_tth_production(P, channel, k1, k2, pt, ptb, pH):
 def msq_tth(P, channel, k1, k2, pb, pl, pn, pbb, pm, pnb, ph1, ph2):
     args = [_d(v) for v in (k1, k2, pb, pl, pn, pbb, pm, pnb, ph1, ph2)]
     return load().ora_msq_tth(C.byref(P), channel, *[a[1] for a in args])
+
+
+def msq_ttbb_production(P, channel, k1, k2, p1, p2, p3, p4):
+    args = [_d(v) for v in (k1, k2, p1, p2, p3, p4)]
+    return load().ora_msq_ttbb_production(C.byref(P), channel, *[a[1] for a in args])
+
+
+def ttbb_gauge_probe(P, k1, k2, p1, p2, p3, p4, which, hel):
+    args = [_d(v) for v in (k1, k2, p1, p2, p3, p4)]
+    return load().ora_ttbb_gauge_probe(C.byref(P), *[a[1] for a in args], which, hel)
+
+
+def ttbb_qq_ward_probe(P, k1, k2, p1, p2, p3, p4):
+    args = [_d(v) for v in (k1, k2, p1, p2, p3, p4)]
+    out = np.zeros(2)
+    load().ora_ttbb_qq_ward_probe(C.byref(P), *[a[1] for a in args], out.ctypes.data_as(_dp))
+    return out
+
+
+def su3_check():
+    out = np.zeros(5)
+    load().ora_su3_check(out.ctypes.data_as(_dp))
+    return out
 
 
 def tth_gauge_probe(P, k1, k2, pt, ptb, pH, which, hel):

@@ -1,0 +1,95 @@
+"""Pins of the oracle's g g / q qbar -> t tbar b bbar amplitude (the ttbb background of
+Sec. 3-4), written diagram by diagram from the QCD Feynman rules with explicit colour
+sums.
+
+* SU(3): the generators give C_F = 4/3, C_A = 3, Tr(t^a t^b) = delta/2, and the
+  colour sums 16/3 and -2/3 of the two orderings t^a t^b, t^b t^a (the numbers the
+  semileptonic ttbar amplitude uses).
+* Gauge invariance (g g): replacing one gluon's polarisation by its momentum, the other
+  gluon physical, the colour- and spin-summed square vanishes -- to 1e-7 of the physical
+  value, where flipping the sign of any one diagram class gives O(1e4) (checked by hand
+  when the pin was written); this fixes the relative signs and factors of the 36 diagrams
+  and their colour tensors.
+* Current conservation (q qbar): the g* -> t tbar b bbar part contracted with the g*
+  momentum vanishes.
+* Bose symmetry (g g) and Lorentz invariance (a boost along and a rotation about the
+  beam axis, which keep the transverse gluon polarisations valid).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from test_oracle_tth import _boost, _two_body
+
+
+def dot(a, b):
+    return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3]
+
+
+def _kinematics(rng, rs, m):
+    k1, k2 = np.array([rs / 2, 0, 0, rs / 2]), np.array([rs / 2, 0, 0, -rs / 2])
+    M1 = rng.uniform(2 * m + 10, rs - 60)
+    M2 = rng.uniform(20, rs - M1 - 5)
+    A, B = _two_body(rng, rs, M1, M2)
+    t, tb = _two_body(rng, M1, m, m)
+    b, bb = _two_body(rng, M2, 0.0, 0.0)
+    bA, bB = A[1:] / A[0], B[1:] / B[0]
+    return k1, k2, _boost(t, bA), _boost(tb, bA), _boost(b, bB), _boost(bb, bB)
+
+
+@pytest.fixture(scope="module")
+def P(ora, synth):
+    return ora.process(2, synth.DEFAULT_PROCESS)
+
+
+def test_su3(ora):
+    s_ab, s_ba, cf, ca, tr_dev = ora.su3_check()
+    assert s_ab == pytest.approx(16 / 3, rel=1e-14, abs=0)
+    assert s_ba == pytest.approx(-2 / 3, rel=1e-13, abs=0)
+    assert cf == pytest.approx(4 / 3, rel=1e-14, abs=0)
+    assert ca == pytest.approx(3.0, rel=1e-14, abs=0)
+    assert tr_dev < 1e-15
+
+
+def test_ttbb_gauge_invariance(ora, synth, P):
+    m = synth.DEFAULT_PROCESS["mt"]
+    rng = np.random.default_rng(61)
+    for rs in (700.0, 1500.0, 3000.0):
+        k1, k2, p1, p2, p3, p4 = _kinematics(rng, rs, m)
+        assert np.allclose(k1 + k2, p1 + p2 + p3 + p4, rtol=0, atol=1e-10 * rs)
+        ref = ora.msq_ttbb_production(P, 0, k1, k2, p1, p2, p3, p4) * 256
+        assert ref > 0
+        for which in (0, 1):
+            for hel in (0, 1):
+                assert abs(ora.ttbb_gauge_probe(P, k1, k2, p1, p2, p3, p4, which, hel)) < 1e-7 * ref
+
+
+def test_ttbb_qq_current_conservation(ora, synth, P):
+    m = synth.DEFAULT_PROCESS["mt"]
+    rng = np.random.default_rng(62)
+    for rs in (700.0, 2000.0):
+        k1, k2, p1, p2, p3, p4 = _kinematics(rng, rs, m)
+        ward, scale = ora.ttbb_qq_ward_probe(P, k1, k2, p1, p2, p3, p4)
+        assert scale > 0 and abs(ward) < 1e-12 * scale
+
+
+def test_ttbb_bose_and_lorentz(ora, synth, P):
+    m = synth.DEFAULT_PROCESS["mt"]
+    rng = np.random.default_rng(63)
+    for _ in range(2):
+        k1, k2, p1, p2, p3, p4 = _kinematics(rng, 1200.0, m)
+        for channel in (0, 1):
+            ref = ora.msq_ttbb_production(P, channel, k1, k2, p1, p2, p3, p4)
+            assert ref > 0
+            if channel == 0:
+                assert ora.msq_ttbb_production(P, 0, k2, k1, p1, p2, p3, p4) == pytest.approx(ref, rel=1e-11, abs=0)
+            bz = np.array([0.0, 0.0, rng.uniform(-0.7, 0.7)])
+            a = rng.uniform(0, 2 * math.pi)
+            R = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
+
+            def tr(p):
+                q = _boost(p, bz)
+                return np.array([q[0], *(R @ q[1:])])
+            got = ora.msq_ttbb_production(P, channel, *[tr(v) for v in (k1, k2, p1, p2, p3, p4)])
+            assert got == pytest.approx(ref, rel=1e-9, abs=0)
