@@ -661,3 +661,69 @@ void ora_ttbb_qq_ward_probe(const ora_process* P, const double* k1_, const doubl
           }
         }
 }
+
+/* g g / q qbar -> t tbar b bbar -> (b l+ nu)(bbar mu- nubar) b bbar: the production
+ * terms above between the decaying top row and antitop column of ora_msq_ttbar (the
+ * W- decaying to mu- nubar), with Breit-Wigner t, tbar, W+, W- propagators; spins and
+ * colours summed, the initial ones averaged. (p3, p4) = the extra b, bbar. */
+double ora_msq_ttbb(const ora_process* P, int channel, const double* k1_, const double* k2_,
+                    const double* pb_, const double* pl_, const double* pn_, const double* pbb_,
+                    const double* pm_, const double* pnb_, const double* p3_, const double* p4_) {
+  rv4 k1 = rv(k1_[0], k1_[1], k1_[2], k1_[3]), k2 = rv(k2_[0], k2_[1], k2_[2], k2_[3]);
+  rv4 pb = rv(pb_[0], pb_[1], pb_[2], pb_[3]), pl = rv(pl_[0], pl_[1], pl_[2], pl_[3]);
+  rv4 pn = rv(pn_[0], pn_[1], pn_[2], pn_[3]), pbb = rv(pbb_[0], pbb_[1], pbb_[2], pbb_[3]);
+  rv4 pm = rv(pm_[0], pm_[1], pm_[2], pm_[3]), pnb = rv(pnb_[0], pnb_[1], pnb_[2], pnb_[3]);
+  rv4 p3 = rv(p3_[0], p3_[1], p3_[2], p3_[3]), p4 = rv(p4_[0], p4_[1], p4_[2], p4_[3]);
+  ctx_t c = {P, sqrt(4.0 * M_PI * P->alpha_s), P->mt};
+  const double m = c.m;
+  rv4 pt = rv_add(pb, rv_add(pl, pn)), ptb = rv_add(pbb, rv_add(pm, pnb));
+  rv4 w1 = rv_add(pl, pn), w2 = rv_add(pm, pnb);
+  cplx Dt = rv_dot(pt, pt) - m * m + I * m * P->wt;
+  cplx Dtb = rv_dot(ptb, ptb) - m * m + I * m * P->wt;
+  cplx Dw1 = rv_dot(w1, w1) - P->mw * P->mw + I * P->mw * P->ww;
+  cplx Dw2 = rv_dot(w2, w2) - P->mw * P->mw + I * P->mw * P->ww;
+  double gw2 = 4.0 * M_PI * P->alpha / P->sw2;
+  dmat PL = d_PL();
+  dmat ptm = d_add(d_slash_r(pt), d_scale(d_unit(), m));
+  dmat ptbm = d_add(d_scale(d_slash_r(ptb), -1.0), d_scale(d_unit(), m));
+  if (channel == 0) gg_colour_matrix();
+  else qq_colour_matrix();
+  double sum = 0.0;
+  for (int sbt = 0; sbt < 2; ++sbt)
+    for (int sn = 0; sn < 2; ++sn)
+      for (int sl = 0; sl < 2; ++sl)
+        for (int sbbt = 0; sbbt < 2; ++sbbt)
+          for (int sm = 0; sm < 2; ++sm)
+            for (int snb = 0; snb < 2; ++snb) {
+              cv4 L = d_current(d_bar(d_massless(pn, sn)), PL, d_massless(pl, sl));
+              cv4 H = d_current(d_bar(d_massless(pm, sm)), PL, d_massless(pnb, snb));
+              spin rt = d_vm(d_vm(d_bar(d_massless(pb, sbt)), d_mul(d_slash(L), PL)), ptm);
+              spin ct = d_mv(ptbm, d_mv(d_mul(d_slash(H), PL), d_massless(pbb, sbbt)));
+              for (int sb = 0; sb < 2; ++sb)
+                for (int sbb = 0; sbb < 2; ++sbb) {
+                  spin rb = d_bar(d_massless(p3, sb)), cb = d_massless(p4, sbb);
+                  if (channel == 0) {
+                    for (int h1 = 0; h1 < 2; ++h1)
+                      for (int h2 = 0; h2 < 2; ++h2) {
+                        cplx Lt[NT_GG];
+                        gg_lorentz(&c, k1, k2, pt, ptb, p3, p4, tpol(h1), tpol(h2), rt, ct, rb, cb,
+                                   Lt);
+                        sum += quad_form(1, Lt);
+                      }
+                  } else {
+                    for (int sq = 0; sq < 2; ++sq)
+                      for (int sqb = 0; sqb < 2; ++sqb) {
+                        cplx Lt[NT_QQ];
+                        spin rq = d_bar(d_massless(k2, sqb)), cq = d_massless(k1, sq);
+                        qq_lorentz(&c, k1, k2, pt, ptb, p3, p4, rq, cq, rt, ct, rb, cb, Lt);
+                        sum += quad_form(0, Lt);
+                      }
+                  }
+                }
+            }
+  double dens = creal(Dt * conj(Dt)) * creal(Dtb * conj(Dtb)) * creal(Dw1 * conj(Dw1)) *
+                creal(Dw2 * conj(Dw2));
+  double coup = pow(0.5 * gw2, 4);   /* four W vertices; g_s is inside the terms */
+  double avg = channel == 0 ? 1.0 / (4.0 * 64.0) : 1.0 / (4.0 * 9.0);
+  return sum * coup * avg / dens;
+}

@@ -121,6 +121,11 @@ double ora_msq_ttbb_production(const ora_process* P, int channel, const double* 
 double ora_ttbb_gauge_probe(const ora_process* P, const double* k1, const double* k2,
                             const double* p1, const double* p2, const double* p3,
                             const double* p4, int which, int hel);
+/* The same with the decays t -> b l+ nu, tbar -> bbar mu- nubar (Breit-Wigner t, tbar,
+ * W+, W- propagators); (p3, p4) the extra b, bbar. */
+double ora_msq_ttbb(const ora_process* P, int channel, const double* k1, const double* k2,
+                    const double* pb, const double* pl, const double* pn, const double* pbb,
+                    const double* pm, const double* pnb, const double* p3, const double* p4);
 void ora_su3_check(double* out);
 void ora_ttbb_qq_ward_probe(const ora_process* P, const double* k1, const double* k2,
                             const double* p1, const double* p2, const double* p3,

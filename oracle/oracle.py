@@ -123,6 +123,8 @@ def load():
     lib.ora_ttbb_gauge_probe.restype = C.c_double
     lib.ora_ttbb_qq_ward_probe.argtypes = [P] + [_dp] * 7
     lib.ora_ttbb_qq_ward_probe.restype = None
+    lib.ora_msq_ttbb.argtypes = [P, C.c_int] + [_dp] * 10
+    lib.ora_msq_ttbb.restype = C.c_double
     lib.ora_su3_check.argtypes = [_dp]
     lib.ora_su3_check.restype = None
     lib.ora_tth_gauge_probe.restype = C.c_double
@@ -315,6 +317,11 @@ def ttbb_qq_ward_probe(P, k1, k2, p1, p2, p3, p4):
     out = np.zeros(2)
     load().ora_ttbb_qq_ward_probe(C.byref(P), *[a[1] for a in args], out.ctypes.data_as(_dp))
     return out
+
+
+def msq_ttbb(P, channel, k1, k2, pb, pl, pn, pbb, pm, pnb, p3, p4):
+    args = [_d(v) for v in (k1, k2, pb, pl, pn, pbb, pm, pnb, p3, p4)]
+    return load().ora_msq_ttbb(C.byref(P), channel, *[a[1] for a in args])
 
 
 def su3_check():

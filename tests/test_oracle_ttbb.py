@@ -93,3 +93,40 @@ def test_ttbb_bose_and_lorentz(ora, synth, P):
                 return np.array([q[0], *(R @ q[1:])])
             got = ora.msq_ttbb_production(P, channel, *[tr(v) for v in (k1, k2, p1, p2, p3, p4)])
             assert got == pytest.approx(ref, rel=1e-9, abs=0)
+
+
+def _decay3(rng, M, m12):
+    a, w = _two_body(rng, M, 0.0, m12)
+    b, c = _two_body(rng, m12, 0.0, 0.0)
+    beta = w[1:] / w[0]
+    return a, _boost(b, beta), _boost(c, beta)
+
+
+@pytest.mark.parametrize("channel", [0, 1])
+def test_ttbb_full_chain_factorises(ora, synth, P, channel):
+    """With on-shell tops the full 2 -> 8 |M|^2 (t and W propagator denominators
+    removed), averaged over parity-reflected decays in each top rest frame, equals
+    |M|^2(ttbb production, top spins summed) x (g_W^2/2)^4 c_t c_tbar, c_t = 8 (p_t.p_l+)
+    (p_b.p_nu), c_tbar = 8 (p_tbar.p_mu-)(p_bbar.p_nubar) (the reflection removes the
+    top-spin correlations; the W- decays to one lepton channel)."""
+    prm = synth.DEFAULT_PROCESS
+    m, mw, ww, wt = prm["mt"], prm["mw"], prm["ww"], prm["wt"]
+    gw2 = 4 * math.pi * prm["alpha"] / prm["sw2"]
+    rng = np.random.default_rng(64 + channel)
+    k1, k2, pt, ptb, p3, p4 = _kinematics(rng, 900.0, m)
+    b0, l0, n0 = _decay3(rng, m, 79.0)
+    bb0, m0, nb0 = _decay3(rng, m, 82.0)
+    acc = 0.0
+    for par_t in (1, -1):
+        for par_tb in (1, -1):
+            bt, btb = pt[1:] / pt[0], ptb[1:] / ptb[0]
+            pb, pl, pn = (_boost(np.array([v[0], *(par_t * v[1:])]), bt) for v in (b0, l0, n0))
+            pbb, pm, pnb = (_boost(np.array([v[0], *(par_tb * v[1:])]), btb) for v in (bb0, m0, nb0))
+            w1, w2 = pl + pn, pm + pnb
+            dens = (wt * m) ** 4 * ((dot(w1, w1) - mw * mw) ** 2 + (mw * ww) ** 2) * \
+                ((dot(w2, w2) - mw * mw) ** 2 + (mw * ww) ** 2)
+            acc += ora.msq_ttbb(P, channel, k1, k2, pb, pl, pn, pbb, pm, pnb, p3, p4) * dens
+            ct = 8 * dot(pt, pl) * dot(pb, pn)
+            ctb = 8 * dot(ptb, pm) * dot(pbb, pnb)
+    prod = ora.msq_ttbb_production(P, channel, k1, k2, pt, ptb, p3, p4)
+    assert acc / 4 == pytest.approx(prod * (gw2 / 2) ** 4 * ct * ctb, rel=1e-9, abs=0)
