@@ -20,8 +20,8 @@
 #include "oracle.h"
 #include "ora_dirac.h"
 
-int ora_dims(int kind) { return kind == 0 ? 2 : kind == 1 ? 4 : kind == 2 ? 7 : kind == 3 ? 6 : 8; }
-int ora_nperm(int kind) { return kind == 2 ? 24 : kind == 3 ? 2 : kind == 4 ? 12 : 1; }
+int ora_dims(int kind) { return kind == 0 ? 2 : kind == 1 ? 4 : kind == 2 ? 7 : kind == 3 ? 6 : 8; }  /* 4, 5: 8 */
+int ora_nperm(int kind) { return kind == 2 ? 24 : kind == 3 ? 2 : (kind == 4 || kind == 5) ? 12 : 1; }
 
 double ora_pdf(const ora_process* P, int type, double x) {
   if (!(x > 0.0 && x < 1.0)) return 0.0;
@@ -387,7 +387,10 @@ static int states_ttdl(const ora_process* P, const ora_tf* T, const float* rec, 
  * m_H^2 = 2 E1 E2 (1 - cos theta_12), E1,2 = (f +- sqrt(f^2 - 4 E1 E2)) / 2, both
  * orderings, each with 1 / |d(f, m_H^2)/d(E1, E2)| = 1 / (2 (1 - cos theta_12) |E1 - E2|);
  * an energy outside its jet window has no weight. Then the missing pT is the visible
- * imbalance and the neutrinos follow from Eq. "dilepsolv" as for dilepton ttbar. */
+ * imbalance and the neutrinos follow from Eq. "dilepsolv" as for dilepton ttbar.
+ * Dilepton ttbb (kind 5, the background) uses the same variables (Sec. 4 applies the
+ * transformations to both processes) with the extra b bbar pair in the role of the Higgs
+ * pair; its mass is not resonant, so m^2 is mapped uniformly over the same range. */
 static void tth_perm(int perm, int* jb, int* jbb, int* j1, int* j2) {
   int rest[3], n = 0;
   const int ib = perm / 3;
@@ -436,7 +439,14 @@ static int states_tthdl(const ora_process* P, const ora_tf* T, const float* rec,
   const double omc = 0.5 * (dx * dx + dy * dy + dz * dz); /* 1 - cos theta_12 */
   if (!(omc > 0.0)) return 0;
   double J7;
-  const double m2 = bw_map(0.0, 0.5 * f * f * omc, P->mh, P->wh, x[7], &J7);
+  const double m2max = 0.5 * f * f * omc;
+  double m2;
+  if (P->kind == 4) {
+    m2 = bw_map(0.0, m2max, P->mh, P->wh, x[7], &J7);
+  } else {
+    m2 = x[7] * m2max;
+    J7 = m2max;
+  }
   const double disc = f * f - 2.0 * m2 / omc;
   if (!(disc > 0.0)) return 0;
   const double sq = sqrt(disc);
@@ -486,7 +496,8 @@ static int build_states(const ora_process* P, const ora_tf* T, const float* rec,
     case 1: return states_w(P, T, rec, x, st);
     case 2: return states_tt(P, T, rec, perm, x, st);
     case 3: return states_ttdl(P, T, rec, perm, x, st);
-    case 4: return states_tthdl(P, T, rec, perm, x, st);
+    case 4:
+    case 5: return states_tthdl(P, T, rec, perm, x, st);
   }
   return 0;
 }
@@ -534,6 +545,21 @@ static double flavour_sum(const ora_process* P, const rv4* b, rv4 k1, rv4 k2, do
       sum += fqb1 * fq2 *
              ora_msq_tth(P, 1, k2.v, k1.v, b[0].v, b[1].v, b[2].v, b[3].v, b[4].v, b[5].v,
                          b[6].v, b[7].v);
+    }
+  } else if (P->kind == 5) {   /* dilepton ttbb: the extra pair's two jets as (b, bbar) and (bbar, b) */
+    for (int o = 0; o < 2; ++o) {
+      const rv4 x3 = o == 0 ? b[6] : b[7], x4 = o == 0 ? b[7] : b[6];
+      sum += fg1 * fg2 *
+             ora_msq_ttbb(P, 0, k1.v, k2.v, b[0].v, b[1].v, b[2].v, b[3].v, b[4].v, b[5].v, x3.v,
+                          x4.v);
+      for (int fl = 0; fl < 2; ++fl) {
+        sum += fq1 * fqb2 *
+               ora_msq_ttbb(P, 1, k1.v, k2.v, b[0].v, b[1].v, b[2].v, b[3].v, b[4].v, b[5].v,
+                            x3.v, x4.v);
+        sum += fqb1 * fq2 *
+               ora_msq_ttbb(P, 1, k2.v, k1.v, b[0].v, b[1].v, b[2].v, b[3].v, b[4].v, b[5].v,
+                            x3.v, x4.v);
+      }
     }
   } else {   /* ttbar (kind 2) and dilepton ttbar (kind 3) */
     sum += fg1 * fg2 *

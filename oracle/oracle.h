@@ -33,7 +33,7 @@ extern "C" {
 
 typedef struct {
   int32_t kind; /* 0 Drell-Yan, 1 W -> e nu, 2 semileptonic ttbar, 3 dilepton ttbar,
-                 * 4 dilepton ttH (H -> b bbar) */
+                 * 4 dilepton ttH (H -> b bbar), 5 dilepton ttbb */
   int32_t pad;
   double sqrt_s;
   double mz, wz, mw, ww, mt, wt;

@@ -227,7 +227,7 @@ def kinematics(P, T, rec, perm, x, root):
     n = load().ora_kinematics(C.byref(P), C.byref(T), rp, perm, xp, root,
                               fs.ctypes.data_as(_dp), lab.ctypes.data_as(_dp),
                               k12.ctypes.data_as(_dp), aux.ctypes.data_as(_dp))
-    nfs = 2 if P.kind < 2 else (8 if P.kind == 4 else 6)
+    nfs = 2 if P.kind < 2 else (8 if P.kind >= 4 else 6)
     return {"n": n, "fs": fs.reshape(8, 4)[:nfs], "lab": lab.reshape(8, 4)[:nfs], "k12": k12.reshape(2, 4),
             "aux": aux}
 

@@ -130,3 +130,91 @@ def test_ttbb_full_chain_factorises(ora, synth, P, channel):
             ctb = 8 * dot(ptb, pm) * dot(pbb, pnb)
     prod = ora.msq_ttbb_production(P, channel, k1, k2, pt, ptb, p3, p4)
     assert acc / 4 == pytest.approx(prod * (gw2 / 2) ** 4 * ct * ctb, rel=1e-9, abs=0)
+
+
+# ---------------------------------------------------------------------------
+# The dilepton ttbb integrand (process kind 5): the variables of dilepton ttH with the
+# extra b bbar pair in the Higgs pair's place and its mass mapped uniformly.
+# ---------------------------------------------------------------------------
+from test_oracle_tth import _phys8, _states, _find_point, _which_object  # noqa: E402
+
+KIND_TTBB = 5
+
+
+@pytest.fixture(scope="module")
+def ttbb_setup(ora, synth):
+    recs = synth.gen_tth_dilep(3, 97).copy()
+    recs[:, 27] = KIND_TTBB     # two leptons and four b jets: the same record layout
+    return (ora.process(KIND_TTBB, synth.DEFAULT_PROCESS), ora.tf(synth.DEFAULT_TF[4]), recs)
+
+
+def test_ttbb_integrand_map(ora, synth, ttbb_setup):
+    """8 variables, 12 assignments; at every state momentum conservation, zero total
+    pT, the virtualities of the produced momenta, and the full map's Jacobian against
+    central differences in (E_b, E_bbar, nu, nubar_z, E_b1, E_b2)."""
+    P, T, recs = ttbb_setup
+    assert ora.dims(KIND_TTBB) == 8 and ora.nperm(KIND_TTBB) == 12
+    rng = np.random.default_rng(65)
+    n_ok = 0
+    for rec in recs:
+        for _ in range(40):
+            x = rng.uniform(0.05, 0.95, size=8)
+            perm = int(rng.integers(0, 12))
+            for k in _states(ora, P, T, rec, perm, x):
+                fs, lab, k12, aux = k["fs"], k["lab"], k["k12"], k["aux"]
+                tot = fs.sum(axis=0)
+                assert np.allclose(k12[0] + k12[1], tot, rtol=0, atol=1e-12 * tot[0])
+                ltot = lab.sum(axis=0)
+                assert abs(ltot[1]) < 1e-10 * ltot[0] and abs(ltot[2]) < 1e-10 * ltot[0]
+                b, lp, nu, bb, lm, nub, h1, h2 = lab
+                want = (dot(lp + nu, lp + nu), dot(lm + nub, lm + nub),
+                        dot(b + lp + nu, b + lp + nu), dot(bb + lm + nub, bb + lm + nub))
+                for g, w in zip(aux[:4], want):
+                    assert g == pytest.approx(w, rel=1e-9, abs=0)
+                f0 = _phys8(lab)
+                M = np.zeros((8, 8))
+                ok = True
+                for j in range(8):
+                    cols = []
+                    for sgn in (1, -1):
+                        xs = x.copy()
+                        xs[j] += sgn * 1e-6
+                        cand = [_phys8(q["lab"]) for q in _states(ora, P, T, rec, perm, xs)]
+                        if not cand:
+                            ok = False
+                            break
+                        d = sorted((np.max(np.abs(c - f0)), i) for i, c in enumerate(cand))
+                        if len(d) > 1 and d[1][0] < 10 * d[0][0]:
+                            ok = False
+                            break
+                        cols.append(cand[d[0][1]])
+                    if not ok:
+                        break
+                    M[:, j] = (cols[0] - cols[1]) / 2e-6
+                if ok:
+                    assert abs(np.linalg.det(M)) == pytest.approx(aux[6], rel=2e-5, abs=0)
+                    n_ok += 1
+    assert n_ok >= 5
+
+
+def test_ttbb_flavour_sum_both_pair_orientations(ora, synth, ttbb_setup):
+    """The extra pair's two jets enter as (b, bbar) and as (bbar, b): the flavour-summed
+    |M|^2 at a state equals the sum over both orientations of the ttbb amplitudes."""
+    P, T, recs = ttbb_setup
+    rng = np.random.default_rng(66)
+    rec = recs[0]
+    x = _find_point(ora, P, T, rec, 0, rng)
+    assert x is not None
+    k = _states(ora, P, T, rec, 0, x)[0]
+    fs, k12 = k["fs"], k["k12"]
+    x1, x2 = k["aux"][4], k["aux"][5]
+    got = ora.flavour_msq(P, fs, k12, x1, x2, rec)
+    Q = math.sqrt(x1 * x2) * synth.DEFAULT_PROCESS["sqrt_s"]
+    f = {t: (ora.pdf_q(P, t, x1, Q), ora.pdf_q(P, t, x2, Q)) for t in (0, 1, 2)}
+    want = 0.0
+    for a, bq in ((fs[6], fs[7]), (fs[7], fs[6])):
+        mom = (fs[0], fs[1], fs[2], fs[3], fs[4], fs[5], a, bq)
+        want += f[2][0] * f[2][1] * ora.msq_ttbb(P, 0, k12[0], k12[1], *mom)
+        want += 2 * f[0][0] * f[1][1] * ora.msq_ttbb(P, 1, k12[0], k12[1], *mom)
+        want += 2 * f[1][0] * f[0][1] * ora.msq_ttbb(P, 1, k12[1], k12[0], *mom)
+    assert got == pytest.approx(want, rel=1e-12, abs=0)
