@@ -306,7 +306,12 @@ def run_reference(args):
                        "d2h_bytes_per_step": 0}}
         print(json.dumps(out), flush=True)
         return
-    n_ev, n_pts = 16, 1 << 14
+    # a bounded sample per step (seconds of host work), the points per item (event x
+    # permutation) as in the GPU arm's count
+    n_ev, n_pts = {synth.PROC_DY: (16, 1 << 14), synth.PROC_W: (16, 1 << 14),
+                   synth.PROC_TTBAR: (2, 1 << 10), synth.PROC_TTBAR_DILEP: (4, 1 << 11),
+                   synth.PROC_TTH_DILEP: (1, 1 << 10)}[kind]
+    n_perm = synth.NPERM[kind]
     recs = synth.gen_events(kind, n_ev, w["seed"])
     P = O.process(kind, synth.DEFAULT_PROCESS)
     T = O.tf(synth.DEFAULT_TF[kind])
@@ -319,8 +324,9 @@ def run_reference(args):
         O.integrate(P, T, recs, seed=i, n_points=n_pts, n_threads=cores)
         times.append(time.perf_counter() - t)
     step = sum(times) / len(times)
-    value = n_ev * n_pts / step
-    sample = f"{n_ev} events x {n_pts} evaluations/event per step of the {args.workload} workload"
+    value = n_ev * n_perm * n_pts / step
+    sample = (f"{n_ev} events x {n_perm} permutations x {n_pts} evaluations per step of the "
+              f"{args.workload} workload")
     out = {"impl": "reference", "metric": "integrand evaluations per second", "value": value,
            "unit": "integrand evals/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak",
