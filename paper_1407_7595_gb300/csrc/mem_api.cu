@@ -60,16 +60,16 @@ uint32_t strat_side(uint64_t n, int d, int k) {
 
 int dims_of(int kind) {
   return kind == PROC_DY ? 2 : kind == PROC_W ? 4 : kind == PROC_TTBAR ? 7 : kind == PROC_TTDL ? 6
-       : kind == PROC_TTH ? 8 : -1;
+       : (kind == PROC_TTH || kind == PROC_TTBB) ? 8 : -1;
 }
 int nperm_of(int kind) {
-  return kind == PROC_TTBAR ? 24 : kind == PROC_TTDL ? 2 : kind == PROC_TTH ? 12
+  return kind == PROC_TTBAR ? 24 : kind == PROC_TTDL ? 2 : (kind == PROC_TTH || kind == PROC_TTBB) ? 12
        : (kind == PROC_DY || kind == PROC_W) ? 1 : -1;
 }
 uint32_t chunk_points(int kind) {  // points of one frozen-grid CTA: THREADS x points per thread
   return THREADS * (uint32_t)(kind == PROC_DY ? PPT_DY
                               : kind == PROC_W ? PPT_W
-                              : (kind == PROC_TTDL || kind == PROC_TTH) ? PPT_DL
+                              : (kind == PROC_TTDL || kind == PROC_TTH || kind == PROC_TTBB) ? PPT_DL
                                                                         : PPT_TT);
 }
 
@@ -80,6 +80,7 @@ cudaError_t launch_integrate(int kind, const IntegrateArgs& a, cudaStream_t st) 
     case PROC_TTBAR: return launch_integrate_tt(a, st);
     case PROC_TTDL: return launch_integrate_ttdl(a, st);
     case PROC_TTH: return launch_integrate_tth(a, st);
+    case PROC_TTBB: return launch_integrate_ttbb(a, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -89,6 +90,7 @@ size_t cache_size(int kind) {
          : kind == PROC_W ? cache_size_w()
          : kind == PROC_TTDL ? cache_size_ttdl()
          : kind == PROC_TTH ? cache_size_tth()
+         : kind == PROC_TTBB ? cache_size_ttbb()
                             : cache_size_tt();
 }
 
@@ -99,6 +101,7 @@ cudaError_t launch_eval(int kind, const EvalArgs& a, cudaStream_t st) {
     case PROC_TTBAR: return launch_eval_tt(a, st);
     case PROC_TTDL: return launch_eval_ttdl(a, st);
     case PROC_TTH: return launch_eval_tth(a, st);
+    case PROC_TTBB: return launch_eval_ttbb(a, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -258,6 +261,8 @@ ProcConst make_proc_const(const mem_process_desc& d) {
   P.mh2 = (float)(d.mh * d.mh);
   P.mhgh = (float)(d.mh * d.wh);
   P.tth_c = (float)(yt * yt * 3.0 * yb * yb / 6.0);
+  P.gs = (float)std::sqrt(gs2);
+  P.ttbb_c = (float)(std::pow(0.5 * g2, 4) * 64.0);
   for (int t = 0; t < 3; ++t) {
     P.pdfA[t] = (float)d.pdf_A[t];
     P.pdfa[t] = (float)d.pdf_a[t];
@@ -271,7 +276,7 @@ ProcConst make_proc_const(const mem_process_desc& d) {
   const double tp = 2.0 * PI_D;
   if (d.kind == PROC_DY) P.prefactor = (2.0 / s) / (4.0 * tp * tp);
   else if (d.kind == PROC_W) P.prefactor = (2.0 / s) / (8.0 * tp * tp);
-  else if (d.kind == PROC_TTH)   // eight final-state particles
+  else if (d.kind == PROC_TTH || d.kind == PROC_TTBB)   // eight final-state particles
     P.prefactor = (2.0 / s) * std::pow(tp, 4.0 - 24.0) / 256.0 / TTH_WEIGHT_SCALE / TTH_DEC_SCALE;
   else P.prefactor = (2.0 / s) * std::pow(tp, 4.0 - 18.0) / 64.0 / TT_WEIGHT_SCALE;
   return P;
@@ -313,7 +318,7 @@ mem_status check_tf(const mem_tf_desc* tf, int kind) {
     return fail(MEM_ERR_INVALID_ARG, "lepton TF needs lep_rel > 0, window_k > 0, lep_rel*window_k < 1");
   if ((kind == PROC_W || kind == PROC_TTBAR) && !(tf->met_sigma > 0 && tf->met_box_k > 0))
     return fail(MEM_ERR_INVALID_ARG, "MET TF needs met_sigma > 0 and met_box_k > 0");
-  if ((kind == PROC_TTBAR || kind == PROC_TTDL || kind == PROC_TTH) &&
+  if ((kind == PROC_TTBAR || kind == PROC_TTDL || kind == PROC_TTH || kind == PROC_TTBB) &&
       !(tf->jet_core > 0 && tf->jet_tail > 0 && tf->jet_tail_w >= 0 && tf->jet_tail_w <= 1 &&
         tf->jet_lo_div > 1 && tf->jet_hi_mul > 1))
     return fail(MEM_ERR_INVALID_ARG, "invalid jet TF parameters");

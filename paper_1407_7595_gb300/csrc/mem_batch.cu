@@ -211,9 +211,9 @@ extern "C" mem_status mem_integrate_batch(int32_t n_groups, const mem_events* co
     if (ev->kind != pr->desc.kind)
       return bfail(MEM_ERR_INVALID_ARG, "group " + std::to_string(g) + ": process kind mismatch");
     const int kind = pr->desc.kind, d = dims_of(kind), np = nperm_of(kind);
-    if (kind == PROC_TTH)
-      return bfail(MEM_ERR_INVALID_ARG,
-                   "group " + std::to_string(g) + ": dilepton ttH is integrated at a fixed budget only");
+    if (kind == PROC_TTH || kind == PROC_TTBB)
+      return bfail(MEM_ERR_INVALID_ARG, "group " + std::to_string(g) +
+                                            ": dilepton ttH and ttbb are integrated at a fixed budget only");
     const mem_tf_desc& T = *tfs[g];
     if ((kind == PROC_DY || kind == PROC_W) &&
         !(T.lep_rel > 0 && T.window_k > 0 && T.lep_rel * T.window_k < 1))

@@ -100,11 +100,13 @@ cudaError_t launch_integrate_w(const IntegrateArgs&, cudaStream_t);
 cudaError_t launch_integrate_tt(const IntegrateArgs&, cudaStream_t);
 cudaError_t launch_integrate_ttdl(const IntegrateArgs&, cudaStream_t);
 cudaError_t launch_integrate_tth(const IntegrateArgs&, cudaStream_t);
+cudaError_t launch_integrate_ttbb(const IntegrateArgs&, cudaStream_t);
 cudaError_t launch_eval_dy(const EvalArgs&, cudaStream_t);
 cudaError_t launch_eval_w(const EvalArgs&, cudaStream_t);
 cudaError_t launch_eval_tt(const EvalArgs&, cudaStream_t);
 cudaError_t launch_eval_ttdl(const EvalArgs&, cudaStream_t);
 cudaError_t launch_eval_tth(const EvalArgs&, cudaStream_t);
+cudaError_t launch_eval_ttbb(const EvalArgs&, cudaStream_t);
 
 // constants and error reporting shared with entry points outside mem_api.cu
 ProcConst make_proc_const_from(const void* mem_process_desc_ptr);
@@ -116,6 +118,7 @@ size_t cache_size_w();
 size_t cache_size_tt();
 size_t cache_size_ttdl();
 size_t cache_size_tth();
+size_t cache_size_ttbb();
 size_t cache_size(int kind);
 
 struct BatchArgs;

@@ -1,0 +1,219 @@
+// Kernel instantiations for the dilepton ttbb process (fixed-budget integration and
+// point evaluation), and the colour matrices of its production terms.
+#include <complex>
+#include <vector>
+
+#include "mem_launch.cuh"
+#include "mem_launch_config.h"
+#include "mem_ttbb.cuh"
+
+namespace mem {
+namespace {
+
+using cd = std::complex<double>;
+
+// SU(3) generators t^a = lambda^a / 2 and structure constants f^{abc} = -2 i Tr([t^a, t^b] t^c)
+struct SU3 {
+  cd t[8][3][3];
+  double f[8][8][8];
+  SU3() {
+    for (auto& a : t)
+      for (auto& r : a)
+        for (auto& x : r) x = 0.0;
+    const cd I(0.0, 1.0);
+    const double h = 0.5, r3 = 1.0 / std::sqrt(3.0);
+    t[0][0][1] = t[0][1][0] = h;
+    t[1][0][1] = -I * h; t[1][1][0] = I * h;
+    t[2][0][0] = h; t[2][1][1] = -h;
+    t[3][0][2] = t[3][2][0] = h;
+    t[4][0][2] = -I * h; t[4][2][0] = I * h;
+    t[5][1][2] = t[5][2][1] = h;
+    t[6][1][2] = -I * h; t[6][2][1] = I * h;
+    t[7][0][0] = t[7][1][1] = h * r3; t[7][2][2] = -2.0 * h * r3;
+    for (int a = 0; a < 8; ++a)
+      for (int b = 0; b < 8; ++b)
+        for (int c = 0; c < 8; ++c) {
+          cd tr = 0.0;
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+              for (int k = 0; k < 3; ++k)
+                tr += (t[a][i][j] * t[b][j][k] - t[b][i][j] * t[a][j][k]) * t[c][k][i];
+          f[a][b][c] = std::real(-2.0 * I * tr);
+        }
+  }
+  // (t^{x0} t^{x1} ...)_{ij}
+  cd prod(const int* x, int n, int i, int j) const {
+    cd M[3][3], R[3][3];
+    for (int p = 0; p < 3; ++p)
+      for (int q = 0; q < 3; ++q) M[p][q] = p == q ? 1.0 : 0.0;
+    for (int s = 0; s < n; ++s) {
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) {
+          R[p][q] = 0.0;
+          for (int r = 0; r < 3; ++r) R[p][q] += M[p][r] * t[x[s]][r][q];
+        }
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) M[p][q] = R[p][q];
+    }
+    return M[i][j];
+  }
+};
+
+const int kPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+// colour tensor of g g term n (the order of ttbb_amp2) at gluon colours a, b, top i,
+// antitop j, b k, bbar l
+cd gg_colour(const SU3& S, int n, int a, int b, int i, int j, int k, int l) {
+  cd s = 0.0;
+  if (n < 12) {   // A (top line) and B (b line): the three vertices in order, pair gluon c
+    const bool top = n < 6;
+    const int* pm = kPerm[top ? n : n - 6];
+    for (int c = 0; c < 8; ++c) {
+      const int idx[3] = {a, b, c};
+      const int x[3] = {idx[pm[0]], idx[pm[1]], idx[pm[2]]};
+      s += top ? S.prod(x, 3, i, j) * S.t[c][k][l] : S.prod(x, 3, k, l) * S.t[c][i][j];
+    }
+    return s;
+  }
+  if (n < 20) {   // C: order x, b-line order, top-line order
+    const int r = n - 12, xg = r / 4, bo = (r / 2) % 2, to = r % 2;
+    const int cx = xg == 0 ? a : b, cy = xg == 0 ? b : a;
+    for (int c = 0; c < 8; ++c) {
+      int xt[2], xb[2];
+      xt[to] = cx; xt[1 - to] = c;
+      xb[bo] = cy; xb[1 - bo] = c;
+      s += S.prod(xt, 2, i, j) * S.prod(xb, 2, k, l);
+    }
+    return s;
+  }
+  if (n < 24) {   // D: f^{abe}, gluon e on a line with the other pair's gluon c
+    const int r = n - 20, line = r / 2, o = r % 2;
+    for (int e = 0; e < 8; ++e)
+      for (int c = 0; c < 8; ++c) {
+        if (S.f[a][b][e] == 0.0) continue;
+        int x[2];
+        x[o] = e; x[1 - o] = c;
+        s += S.f[a][b][e] * (line == 0 ? S.prod(x, 2, i, j) * S.t[c][k][l] : S.prod(x, 2, k, l) * S.t[c][i][j]);
+      }
+    return s;
+  }
+  if (n < 32) {   // E: f^{x c e}: legs (external x, pair gluon c, joining gluon e)
+    const int r = n - 24, xg = r / 4, line = (r / 2) % 2, o = r % 2;
+    const int cx = xg == 0 ? a : b, cy = xg == 0 ? b : a;
+    for (int c = 0; c < 8; ++c)
+      for (int e = 0; e < 8; ++e) {
+        if (S.f[cx][c][e] == 0.0) continue;
+        int x[2];
+        x[o] = cy; x[1 - o] = e;
+        s += S.f[cx][c][e] * (line == 0 ? S.prod(x, 2, i, j) * S.t[c][k][l] : S.prod(x, 2, k, l) * S.t[c][i][j]);
+      }
+    return s;
+  }
+  for (int c = 0; c < 8; ++c)    // F and G: pair gluons c (top), d (b)
+    for (int d = 0; d < 8; ++d) {
+      const cd td = S.t[c][i][j] * S.t[d][k][l];
+      if (td == 0.0) continue;
+      double f = 0.0;
+      for (int e = 0; e < 8; ++e) {
+        switch (n) {
+          case 32: f += S.f[a][b][e] * S.f[c][d][e]; break;
+          case 33: f += S.f[a][c][e] * S.f[b][d][e]; break;
+          case 34: f += S.f[a][d][e] * S.f[b][c][e]; break;
+          case 35: f += S.f[a][b][e] * S.f[e][c][d]; break;
+          case 36: f += S.f[a][c][e] * S.f[b][d][e]; break;
+          default: f += S.f[b][c][e] * S.f[a][d][e]; break;
+        }
+      }
+      s += f * td;
+    }
+  return s;
+}
+
+// colour tensor of q qbar term n at the quark iq, antiquark jq colours (the light line
+// read from the antiquark row to the quark column: (t ...)_{jq iq})
+cd qq_colour(const SU3& S, int n, int iq, int jq, int i, int j, int k, int l) {
+  cd s = 0.0;
+  if (n < 4) {
+    const int line = n / 2, o = n % 2;
+    for (int e = 0; e < 8; ++e)
+      for (int c = 0; c < 8; ++c) {
+        int x[2];
+        x[o] = e; x[1 - o] = c;
+        s += S.t[e][jq][iq] * (line == 0 ? S.prod(x, 2, i, j) * S.t[c][k][l] : S.prod(x, 2, k, l) * S.t[c][i][j]);
+      }
+    return s;
+  }
+  if (n == 4) {
+    for (int e = 0; e < 8; ++e)
+      for (int c = 0; c < 8; ++c)
+        for (int d = 0; d < 8; ++d)
+          if (S.f[e][c][d] != 0.0) s += S.t[e][jq][iq] * S.f[e][c][d] * S.t[c][i][j] * S.t[d][k][l];
+    return s;
+  }
+  const int o = n - 5;
+  for (int c = 0; c < 8; ++c)
+    for (int d = 0; d < 8; ++d) {
+      int x[2];
+      x[o] = c; x[1 - o] = d;
+      s += S.prod(x, 2, jq, iq) * S.t[c][i][j] * S.t[d][k][l];
+    }
+  return s;
+}
+
+std::vector<float2> colour_matrix(bool gg) {
+  static const SU3 S;
+  const int N = gg ? TTBB_NGG : TTBB_NQQ, ext = gg ? 64 : 9;
+  std::vector<cd> Cm((size_t)N * ext * 81);
+  for (int n = 0; n < N; ++n) {
+    size_t q = (size_t)n * ext * 81;
+    for (int a = 0; a < (gg ? 8 : 3); ++a)
+      for (int b = 0; b < (gg ? 8 : 3); ++b)
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k)
+              for (int l = 0; l < 3; ++l)
+                Cm[q++] = gg ? gg_colour(S, n, a, b, i, j, k, l) : qq_colour(S, n, a, b, i, j, k, l);
+  }
+  std::vector<float2> K((size_t)N * N);
+  for (int n = 0; n < N; ++n)
+    for (int m = 0; m < N; ++m) {
+      cd s = 0.0;
+      for (int q = 0; q < ext * 81; ++q) s += std::conj(Cm[(size_t)n * ext * 81 + q]) * Cm[(size_t)m * ext * 81 + q];
+      K[(size_t)n * N + m] = make_float2((float)s.real(), (float)s.imag());
+    }
+  return K;
+}
+
+// The colour matrices in this context's constant memory (set on every launch path
+// call: constant memory belongs to the current device's context).
+cudaError_t ttbb_colour_upload() {
+  static const std::vector<float2> kgg = colour_matrix(true), kqq = colour_matrix(false);
+  cudaError_t e = cudaMemcpyToSymbol(c_ttbb_kgg, kgg.data(), kgg.size() * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ttbb_kqq, kqq.data(), kqq.size() * sizeof(float2));
+  return e;
+}
+
+cudaError_t ttbb_stack() {
+  size_t cur = 0;
+  cudaError_t e = cudaDeviceGetLimit(&cur, cudaLimitStackSize);
+  if (e == cudaSuccess && cur < 4096) e = cudaDeviceSetLimit(cudaLimitStackSize, 4096);
+  return e;
+}
+
+}  // namespace
+
+cudaError_t launch_integrate_ttbb(const IntegrateArgs& a, cudaStream_t st) {
+  cudaError_t e = ttbb_stack();
+  if (e == cudaSuccess) e = ttbb_colour_upload();
+  if (e != cudaSuccess) return e;
+  return run_integrate<PhysTTBB, PPT_DL, MINB_DL, MINB_DL_MAIN>(a, st);
+}
+cudaError_t launch_eval_ttbb(const EvalArgs& a, cudaStream_t st) {
+  cudaError_t e = ttbb_stack();
+  if (e == cudaSuccess) e = ttbb_colour_upload();
+  if (e != cudaSuccess) return e;
+  return run_eval<PhysTTBB>(a, st);
+}
+size_t cache_size_ttbb() { return cache_bytes<PhysTTBB>(); }
+
+}  // namespace mem

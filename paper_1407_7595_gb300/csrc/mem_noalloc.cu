@@ -79,7 +79,7 @@ extern "C" mem_status mem_integrate_noalloc(const mem_process_desc* desc, const 
     return bad("lepton TF needs lep_rel > 0, window_k > 0, lep_rel*window_k < 1");
   if ((kind == PROC_W || kind == PROC_TTBAR) && !(tf->met_sigma > 0 && tf->met_box_k > 0))
     return bad("MET TF needs met_sigma > 0 and met_box_k > 0");
-  if ((kind == PROC_TTBAR || kind == PROC_TTDL || kind == PROC_TTH) &&
+  if ((kind == PROC_TTBAR || kind == PROC_TTDL || kind == PROC_TTH || kind == PROC_TTBB) &&
       !(tf->jet_core > 0 && tf->jet_tail > 0 && tf->jet_tail_w >= 0 && tf->jet_tail_w <= 1 &&
         tf->jet_lo_div > 1 && tf->jet_hi_mul > 1))
     return bad("invalid jet TF parameters");

@@ -13,7 +13,7 @@
 
 namespace mem {
 
-enum { PROC_DY = 0, PROC_W = 1, PROC_TTBAR = 2, PROC_TTDL = 3, PROC_TTH = 4 };
+enum { PROC_DY = 0, PROC_W = 1, PROC_TTBAR = 2, PROC_TTDL = 3, PROC_TTH = 4, PROC_TTBB = 5 };
 
 // ttbar weights are carried in FP32 multiplied by 2^40 (an exact power of two,
 // divided out of the FP64 prefactor) so that products of small factors in
@@ -38,6 +38,8 @@ struct ProcConst {
   float tt_gg, tt_qq;       // ttbar: couplings x colour x averaging factors
   float mh2, mhgh;          // Higgs mass^2 and mass x width (ttH)
   float tth_c;              // ttH over ttbar couplings: y_t^2 x 3 y_b^2 / 6
+  float gs;                 // strong coupling g_s (ttbb: inside its production terms)
+  float ttbb_c;             // ttbb decay couplings: (g_W^2 / 2)^4 x 64 (Fierz)
   float pdfA[3], pdfa[3], pdfb[3];
   int pdf_amode[3];         // 1: x^-1/2, 2: x^-1, 0: general power
   int pdf_bint[3];          // integer exponent of (1-x) if >= 0, else general power

@@ -76,9 +76,10 @@ PROC_TTBAR_DILEP = 3
 # dilepton ttbar: leptons measured exactly, b jets as in semileptonic ttbar
 DEFAULT_TF[PROC_TTBAR_DILEP] = dict(DEFAULT_TF[PROC_TTBAR])
 DEFAULT_TF[4] = dict(DEFAULT_TF[PROC_TTBAR])   # dilepton ttH
+DEFAULT_TF[5] = dict(DEFAULT_TF[PROC_TTBAR])   # dilepton ttbb (same records as ttH)
 
-DIMS = {PROC_DY: 2, PROC_W: 4, PROC_TTBAR: 7, PROC_TTBAR_DILEP: 6, 4: 8}
-NPERM = {PROC_DY: 1, PROC_W: 1, PROC_TTBAR: 24, PROC_TTBAR_DILEP: 2, 4: 12}
+DIMS = {PROC_DY: 2, PROC_W: 4, PROC_TTBAR: 7, PROC_TTBAR_DILEP: 6, 4: 8, 5: 8}
+NPERM = {PROC_DY: 1, PROC_W: 1, PROC_TTBAR: 24, PROC_TTBAR_DILEP: 2, 4: 12, 5: 12}
 
 # The five workloads: (process, events, points per event, base seed).
 SEED_BASE = 0x4D454D00

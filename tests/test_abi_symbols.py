@@ -44,15 +44,18 @@ def test_host_only_entry_points(libmem):
     """Calls that need no device: dimension tables and argument validation."""
     from paper_1407_7595_gb300 import abi, synth
     L = abi.lib()
-    assert [L.mem_process_dims(k) for k in (0, 1, 2)] == [2, 4, 7]
-    assert [L.mem_process_nperm(k) for k in (0, 1, 2)] == [1, 1, 24]
+    assert [L.mem_process_dims(k) for k in (0, 1, 2, 3, 4, 5)] == [2, 4, 7, 6, 8, 8]
+    assert [L.mem_process_nperm(k) for k in (0, 1, 2, 3, 4, 5)] == [1, 1, 24, 2, 12, 12]
     assert L.mem_process_dims(7) == -1
     d = abi.process_desc(0, synth.DEFAULT_PROCESS)
     d.mz = -1.0
     with pytest.raises(abi.MemError) as e:
         abi.mem_create_process(d)
     assert e.value.status == abi.MEM_ERR_INVALID_ARG
-    d = abi.process_desc(5, synth.DEFAULT_PROCESS)
+    d = abi.process_desc(9, synth.DEFAULT_PROCESS)       # no such process
+    with pytest.raises(abi.MemError):
+        abi.mem_create_process(d)
+    d = abi.process_desc(4, dict(synth.DEFAULT_PROCESS, wh=0.0))   # ttH needs a Higgs width
     with pytest.raises(abi.MemError):
         abi.mem_create_process(d)
     h = abi.mem_create_process(abi.process_desc(1, synth.DEFAULT_PROCESS))
