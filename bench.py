@@ -79,6 +79,8 @@ WORKLOAD_NAMES = {
             "assignments, 1024 events x 2^18 evaluations/event",
     "tth": "dilepton ttH, H -> b bbar (Eq. integrand with Eq. mhsolve): 8-dim integral x 12 "
            "jet assignments, 256 events x 12 x 2^16 evaluations/event",
+    "ttbb": "dilepton ttbb background (36 + 7 production diagrams): 8-dim integral x 12 jet "
+            "assignments, 64 events x 12 x 2^14 evaluations/event",
 }
 
 
@@ -88,7 +90,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["w", "dy", "ttbar", "mix", "flow", "parton", "ttdl", "tth"],
+    ap.add_argument("--workload", choices=["w", "dy", "ttbar", "mix", "flow", "parton", "ttdl", "tth",
+                                           "ttbb"],
                     default="w")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the events-to-1%% leg")
     ap.add_argument("--strat", type=int, default=0,
@@ -209,7 +212,7 @@ def cpu_baseline(kind, seed):
     # (events, evaluations per item): about 10 s of work on 16 Grace cores
     n_ev, n_pts = {synth.PROC_W: (64, 1 << 16), synth.PROC_DY: (16, 1 << 15),
                    synth.PROC_TTBAR: (2, 1 << 10), synth.PROC_TTBAR_DILEP: (16, 1 << 12),
-                   synth.PROC_TTH_DILEP: (1, 1 << 11)}[kind]
+                   synth.PROC_TTH_DILEP: (1, 1 << 11), synth.PROC_TTBB_DILEP: (1, 1 << 9)}[kind]
     n_perm = synth.NPERM[kind]
     recs = synth.gen_events(kind, n_ev, seed)
     P = O.process(kind, synth.DEFAULT_PROCESS)
@@ -310,7 +313,7 @@ def run_reference(args):
     # permutation) as in the GPU arm's count
     n_ev, n_pts = {synth.PROC_DY: (16, 1 << 14), synth.PROC_W: (16, 1 << 14),
                    synth.PROC_TTBAR: (2, 1 << 10), synth.PROC_TTBAR_DILEP: (4, 1 << 11),
-                   synth.PROC_TTH_DILEP: (1, 1 << 10)}[kind]
+                   synth.PROC_TTH_DILEP: (1, 1 << 10), synth.PROC_TTBB_DILEP: (1, 1 << 8)}[kind]
     n_perm = synth.NPERM[kind]
     recs = synth.gen_events(kind, n_ev, w["seed"])
     P = O.process(kind, synth.DEFAULT_PROCESS)
@@ -454,7 +457,7 @@ def run_ours(args):
         t_main = statistics.mean(main_ms) * 1e-3
         achieved = fpe * n_ev * n_perm * n_main / t_main / 1e12 if fpe else None
         dpi = DRAM_BYTES_PER_ITEM_MAIN.get(kind)
-        if kind in (synth.PROC_TTBAR_DILEP, synth.PROC_TTH_DILEP):
+        if kind in (synth.PROC_TTBAR_DILEP, synth.PROC_TTH_DILEP, synth.PROC_TTBB_DILEP):
             fpe = None
             f64 = FP64_FLOPS_PER_EVAL.get(kind)
             peak = FP64_PEAK_TFLOPS
@@ -466,7 +469,8 @@ def run_ours(args):
                             if dpi and not args.pdf_grid and not args.strat else None),
                 "peak_source": (f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                 f"{max_mhz:.0f} MHz max SM clock"
-                                if kind not in (synth.PROC_TTBAR_DILEP, synth.PROC_TTH_DILEP) else
+                                if kind not in (synth.PROC_TTBAR_DILEP, synth.PROC_TTH_DILEP,
+                                                synth.PROC_TTBB_DILEP) else
                                 "nominal GB300 FP64 rate (the FP64 neutrino solution bounds "
                                 "this kernel)"),
                 "flops_per_eval": fpe,
@@ -493,7 +497,7 @@ def run_ours(args):
                "status_ok": ok, "median_rel_err": float(torch.median(err / prob).item()),
                "roofline": roof, "clocks": clocks, "e2e": e2e,
                "gpu_launches": 3 * args.steps}
-        if not args.no_adaptive and kind != synth.PROC_TTH_DILEP:   # ttH: fixed budget only
+        if not args.no_adaptive and kind not in (synth.PROC_TTH_DILEP, synth.PROC_TTBB_DILEP):
             out["to_1pct"] = adaptive_leg(abi, torch, events, proc, tf, n_ev,
                                           shard(rank, n_ev)["event_id_base"], sp, recs=recs)
         if not args.no_flow:

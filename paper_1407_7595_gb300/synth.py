@@ -95,6 +95,7 @@ WORKLOADS = {
     "ttdl": dict(proc=3, n_events=1024, n_points=1 << 18, seed=SEED_BASE + 6),
     # dilepton ttH (Sec. 3-4, the paper's hadron-level signal): 8 dims x 12 jet assignments
     "tth": dict(proc=4, n_events=256, n_points=12 << 16, seed=SEED_BASE + 7),
+    "ttbb": dict(proc=5, n_events=64, n_points=12 << 14, seed=SEED_BASE + 8),
 }
 
 
@@ -475,7 +476,7 @@ def tth_perm_index(jb, jbb):
     return 3 * jb + rest.index(jbb)
 
 
-def gen_tth_dilep(n, seed, tf=None, truth=False):
+def gen_tth_dilep(n, seed, tf=None, truth=False, pair_mass=None):
     """Dilepton ttH events (Sec. 3-4, the signal of the paper's hadron-level
     analysis): t -> b e+ nu, tbar -> bbar mu- nubar, H -> b bbar. Partonic mass
     uniform in [m_t1 + m_t2 + m_H + 20 GeV, 1500 GeV], rapidity U[-1, 1]; the t tbar
@@ -486,7 +487,8 @@ def gen_tth_dilep(n, seed, tf=None, truth=False):
     Record: objects 0 e+, 1 mu-, 2..5 the b jets; [24], [25] MET = nu_T + nubar_T +
     N(0, 15^2); [26] = 6; [27] = 4; [28] = tth_perm_index of the true b and bbar jets.
     With truth=True also returns the (n, 8, 4) parton momenta of b, bbar, e+, mu-, nu,
-    nubar, b(H), bbar(H)."""
+    nubar, b(H), bbar(H). pair_mass = (lo, hi): the extra pair's mass uniform over
+    [lo, hi] instead of m_H, and [27] = 5 (the ttbb background's stand-in events)."""
     tf = tf or DEFAULT_TF[PROC_TTBAR]
     P = DEFAULT_PROCESS
     mh = P["mh"]
@@ -500,11 +502,12 @@ def gen_tth_dilep(n, seed, tf=None, truth=False):
         mt2 = _bw_mass_v(rng, P["mt"], P["wt"], 15.0, m)
         mw1 = _bw_mass_v(rng, P["mw"], P["ww"], 15.0, m)
         mw2 = _bw_mass_v(rng, P["mw"], P["ww"], 15.0, m)
-        rs = rng.uniform(0.0, 1.0, m) * (1500.0 - (mt1 + mt2 + mh + 20.0)) + mt1 + mt2 + mh + 20.0
-        mtt = rng.uniform(0.0, 1.0, m) * (rs - mh - 1.0 - (mt1 + mt2 + 1.0)) + mt1 + mt2 + 1.0
+        mp = np.full(m, mh) if pair_mass is None else rng.uniform(pair_mass[0], pair_mass[1], m)
+        rs = rng.uniform(0.0, 1.0, m) * (1500.0 - (mt1 + mt2 + mp + 20.0)) + mt1 + mt2 + mp + 20.0
+        mtt = rng.uniform(0.0, 1.0, m) * (rs - mp - 1.0 - (mt1 + mt2 + 1.0)) + mt1 + mt2 + 1.0
         y = rng.uniform(-1.0, 1.0, m)
         sysp = np.stack([rs * np.cosh(y), 0 * y, 0 * y, rs * np.sinh(y)], axis=1)
-        hq, ttq = _two_body_v(rng, rs, np.full(m, mh), mtt)
+        hq, ttq = _two_body_v(rng, rs, mp, mtt)
         t, tb = _two_body_v(rng, mtt, mt1, mt2)
         t, tb = _boost_v(t, ttq), _boost_v(tb, ttq)
         hq, t, tb = _boost_v(hq, sysp), _boost_v(t, sysp), _boost_v(tb, sysp)
@@ -516,7 +519,7 @@ def gen_tth_dilep(n, seed, tf=None, truth=False):
         bb, wm = _boost_v(bb, tb), _boost_v(wm, tb)
         lm, nub = _two_body_v(rng, mw2, 0.0, 0.0)
         lm, nub = _boost_v(lm, wm), _boost_v(nub, wm)
-        h1, h2 = _two_body_v(rng, np.full(m, mh), 0.0, 0.0)
+        h1, h2 = _two_body_v(rng, mp, 0.0, 0.0)
         h1, h2 = _boost_v(h1, hq), _boost_v(h2, hq)
         ok = np.ones(m, dtype=bool)
         for q in (lp, lm, b, bb, h1, h2):
@@ -549,7 +552,7 @@ def gen_tth_dilep(n, seed, tf=None, truth=False):
         r[:, 24] = (nu[idx, 1] + nub[idx, 1]) + tf["met_sigma"] * rng.standard_normal(len(idx))
         r[:, 25] = (nu[idx, 2] + nub[idx, 2]) + tf["met_sigma"] * rng.standard_normal(len(idx))
         r[:, 26] = 6
-        r[:, 27] = PROC_TTH_DILEP
+        r[:, 27] = PROC_TTH_DILEP if pair_mass is None else 5
         slot_of = np.argsort(order, axis=1)                         # quark -> jet slot
         r[:, 28] = [tth_perm_index(int(a), int(c)) for a, c in zip(slot_of[:, 0], slot_of[:, 1])]
         for k, q in enumerate((b, bb, lp, lm, nu, nub, h1, h2)):
@@ -558,8 +561,19 @@ def gen_tth_dilep(n, seed, tf=None, truth=False):
     return (out, tr) if truth else out
 
 
+PROC_TTBB_DILEP = 5
+
+
+def gen_ttbb_dilep(n, seed, tf=None, truth=False):
+    """Stand-in dilepton ttbb events: the ttH chain with the extra b bbar pair's mass
+    uniform in [20, 300] GeV (a continuum instead of the Higgs peak); record layout as
+    for gen_tth_dilep with [27] = 5."""
+    return gen_tth_dilep(n, seed, tf=tf, truth=truth, pair_mass=(20.0, 300.0))
+
+
 GENERATORS = {PROC_DY: gen_dy, PROC_W: gen_w, PROC_TTBAR: gen_ttbar,
-              PROC_TTBAR_DILEP: gen_ttbar_dilep, PROC_TTH_DILEP: gen_tth_dilep}
+              PROC_TTBAR_DILEP: gen_ttbar_dilep, PROC_TTH_DILEP: gen_tth_dilep,
+              PROC_TTBB_DILEP: gen_ttbb_dilep}
 
 
 def gen_events(proc, n, seed):
