@@ -273,6 +273,14 @@ mem_status mem_discriminant(int64_t n, const double* prob_s, const double* err_s
                             const double* prob_b, const double* err_b, double* D, double* err_D,
                             int32_t* status, void* stream);
 
+/* The colour matrices of the dilepton ttbb production terms (MEM_PROC_TTBB_DILEP):
+ * K_nm = sum over external colours of conj(C_n) C_m for the 38 g g terms and the 7
+ * q qbar terms, in the kernels' term order (see the header of csrc/mem_ttbb.cuh), as
+ * interleaved (real, imaginary) float pairs, row major: kgg 38 x 38 x 2 and kqq
+ * 7 x 7 x 2 floats of host memory, caller-owned. Host computation; no device needed.
+ * Errors: MEM_ERR_INVALID_ARG (NULL pointers). */
+mem_status mem_ttbb_colour_matrices(float* kgg, float* kqq);
+
 /* Working memory of mem_integrate_noalloc, fixed at build time (32 MiB per GPU). */
 #define MEM_NOALLOC_SCRATCH_BYTES (32u << 20)
 

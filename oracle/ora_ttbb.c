@@ -727,3 +727,19 @@ double ora_msq_ttbb(const ora_process* P, int channel, const double* k1_, const 
   double avg = channel == 0 ? 1.0 / (4.0 * 64.0) : 1.0 / (4.0 * 9.0);
   return sum * coup * avg / dens;
 }
+
+/* The colour matrices (kgg 38 x 38, kqq 7 x 7; interleaved real, imaginary doubles). */
+void ora_ttbb_colour_matrices(double* kgg, double* kqq) {
+  gg_colour_matrix();
+  qq_colour_matrix();
+  for (int n = 0; n < NT_GG; ++n)
+    for (int m = 0; m < NT_GG; ++m) {
+      kgg[2 * (n * NT_GG + m)] = Kgg[n][m][0];
+      kgg[2 * (n * NT_GG + m) + 1] = Kgg[n][m][1];
+    }
+  for (int n = 0; n < NT_QQ; ++n)
+    for (int m = 0; m < NT_QQ; ++m) {
+      kqq[2 * (n * NT_QQ + m)] = Kqq[n][m][0];
+      kqq[2 * (n * NT_QQ + m) + 1] = Kqq[n][m][1];
+    }
+}

@@ -127,6 +127,7 @@ double ora_msq_ttbb(const ora_process* P, int channel, const double* k1, const d
                     const double* pb, const double* pl, const double* pn, const double* pbb,
                     const double* pm, const double* pnb, const double* p3, const double* p4);
 void ora_su3_check(double* out);
+void ora_ttbb_colour_matrices(double* kgg, double* kqq);
 void ora_ttbb_qq_ward_probe(const ora_process* P, const double* k1, const double* k2,
                             const double* p1, const double* p2, const double* p3,
                             const double* p4, double* out);

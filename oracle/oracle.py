@@ -125,6 +125,8 @@ def load():
     lib.ora_ttbb_qq_ward_probe.restype = None
     lib.ora_msq_ttbb.argtypes = [P, C.c_int] + [_dp] * 10
     lib.ora_msq_ttbb.restype = C.c_double
+    lib.ora_ttbb_colour_matrices.argtypes = [_dp, _dp]
+    lib.ora_ttbb_colour_matrices.restype = None
     lib.ora_su3_check.argtypes = [_dp]
     lib.ora_su3_check.restype = None
     lib.ora_tth_gauge_probe.restype = C.c_double
@@ -322,6 +324,13 @@ def ttbb_qq_ward_probe(P, k1, k2, p1, p2, p3, p4):
 def msq_ttbb(P, channel, k1, k2, pb, pl, pn, pbb, pm, pnb, p3, p4):
     args = [_d(v) for v in (k1, k2, pb, pl, pn, pbb, pm, pnb, p3, p4)]
     return load().ora_msq_ttbb(C.byref(P), channel, *[a[1] for a in args])
+
+
+def ttbb_colour_matrices():
+    kgg = np.zeros(38 * 38 * 2)
+    kqq = np.zeros(7 * 7 * 2)
+    load().ora_ttbb_colour_matrices(kgg.ctypes.data_as(_dp), kqq.ctypes.data_as(_dp))
+    return kgg.view(np.complex128).reshape(38, 38), kqq.view(np.complex128).reshape(7, 7)
 
 
 def su3_check():

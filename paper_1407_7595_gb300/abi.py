@@ -100,6 +100,7 @@ SIGNATURES = [
     ("mem_process_set_pdf_grid", C.c_int, [_vp, _vp, C.c_int32, C.c_int32, C.c_double,
                                            C.c_double, C.c_double, C.c_double]),
     ("mem_discriminant", C.c_int, [C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("mem_ttbb_colour_matrices", C.c_int, [_vp, _vp]),
     ("mem_destroy", None, [_vp]),
     ("mem_last_error", C.c_char_p, []),
     ("mem_eval_points", C.c_int, [_vp, _vp, C.POINTER(mem_tf_desc), C.c_int64, C.c_int32,
@@ -244,6 +245,14 @@ def mem_autotune(events, proc, tf, seed, opts, stream=None):
     _check(lib().mem_autotune(events, proc, C.byref(tf), seed, C.byref(opts), C.byref(best),
                               C.byref(rate), C.byref(tried), stream))
     return best, rate.value, tried.value
+
+
+def mem_ttbb_colour_matrices():
+    """The dilepton ttbb kernels' colour matrices: (38, 38) and (7, 7) complex64."""
+    kgg = np.zeros(38 * 38 * 2, dtype=np.float32)
+    kqq = np.zeros(7 * 7 * 2, dtype=np.float32)
+    _check(lib().mem_ttbb_colour_matrices(kgg.ctypes.data, kqq.ctypes.data))
+    return (kgg.view(np.complex64).reshape(38, 38), kqq.view(np.complex64).reshape(7, 7))
 
 
 def mem_process_set_pdf_grid(proc, grid):

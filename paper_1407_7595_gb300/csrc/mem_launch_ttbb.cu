@@ -217,3 +217,17 @@ cudaError_t launch_eval_ttbb(const EvalArgs& a, cudaStream_t st) {
 size_t cache_size_ttbb() { return cache_bytes<PhysTTBB>(); }
 
 }  // namespace mem
+
+extern "C" mem_status mem_ttbb_colour_matrices(float* kgg, float* kqq) {
+  if (!kgg || !kqq) return MEM_ERR_INVALID_ARG;
+  const std::vector<float2> a = mem::colour_matrix(true), b = mem::colour_matrix(false);
+  for (size_t q = 0; q < a.size(); ++q) {
+    kgg[2 * q] = a[q].x;
+    kgg[2 * q + 1] = a[q].y;
+  }
+  for (size_t q = 0; q < b.size(); ++q) {
+    kqq[2 * q] = b[q].x;
+    kqq[2 * q + 1] = b[q].y;
+  }
+  return MEM_OK;
+}

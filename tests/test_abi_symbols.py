@@ -61,3 +61,18 @@ def test_host_only_entry_points(libmem):
     h = abi.mem_create_process(abi.process_desc(1, synth.DEFAULT_PROCESS))
     abi.mem_destroy(h)
     abi.mem_destroy(None)
+
+
+def test_ttbb_colour_matrices_match_the_oracle(libmem, ora):
+    """The colour matrices the GPU kernels use (computed on the host by the library, with
+    its own SU(3) code) equal the oracle's, term by term, to FP32 rounding: the term
+    order, the colour tensors and the f^{abc} conventions of the two sides agree."""
+    import numpy as np
+    from paper_1407_7595_gb300 import abi
+    kgg, kqq = abi.mem_ttbb_colour_matrices()
+    ogg, oqq = ora.ttbb_colour_matrices()
+    for k, o in ((kgg, ogg), (kqq, oqq)):
+        scale = np.max(np.abs(o))
+        assert scale > 0
+        assert np.max(np.abs(k.astype(np.complex128) - o)) < 1e-6 * scale
+        assert np.allclose(o, o.conj().T, rtol=0, atol=1e-12 * scale)   # Hermitian

@@ -218,3 +218,4 @@ def test_ttbb_flavour_sum_both_pair_orientations(ora, synth, ttbb_setup):
         want += 2 * f[0][0] * f[1][1] * ora.msq_ttbb(P, 1, k12[0], k12[1], *mom)
         want += 2 * f[1][0] * f[0][1] * ora.msq_ttbb(P, 1, k12[1], k12[0], *mom)
     assert got == pytest.approx(want, rel=1e-12, abs=0)
+
