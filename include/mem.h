@@ -60,13 +60,15 @@ enum {
                             * top virtualities, the Higgs pair's f = E1 + E2 and m_H^2), 12 jet
                             * assignments. Records: objects 0 l+ (kind 4), 1 mu- (kind 1), 2..5 the
                             * b jets (kind 5). Needs mh, wh, mb in the process description.
-                            * mem_integrate at a fixed budget (no target_rel_err),
-                            * mem_integrate_noalloc and mem_eval_points. */,
+                            * mem_integrate at a fixed budget (no target_rel_err) and
+                            * mem_eval_points (mem_integrate_noalloc rejects it: its kernels
+                            * raise the per-thread stack limit, which reserves device memory). */,
   MEM_PROC_TTBB_DILEP = 5  /* gg, q qbar -> t tbar b bbar -> (b l+ nu)(bbar mu- nubar) b bbar, the
                             * background of Sec. 3-4: the variables and 12 jet assignments of
                             * MEM_PROC_TTH_DILEP with the extra pair's mass mapped uniformly (no
                             * resonance); the pair's jets enter as (b, bbar) and (bbar, b). Same
-                            * records and entry points as MEM_PROC_TTH_DILEP. */
+                            * records and entry points as MEM_PROC_TTH_DILEP; its kernels also
+                            * keep the colour matrices in constant memory. */
 };
 
 typedef struct mem_process mem_process; /* opaque, library-owned */

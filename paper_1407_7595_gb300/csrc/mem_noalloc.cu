@@ -66,6 +66,10 @@ extern "C" mem_status mem_integrate_noalloc(const mem_process_desc* desc, const 
   const int kind = desc->kind;
   const int d = dims_of(kind), np = nperm_of(kind);
   if (d < 0 || desc->reserved != 0) return bad("unknown process kind or reserved != 0");
+  // the dilepton ttH and ttbb kernels raise the context's per-thread stack limit before
+  // their first launch, which reserves device memory: not this entry point's contract
+  if (kind == PROC_TTH || kind == PROC_TTBB)
+    return bad("dilepton ttH and ttbb need mem_integrate (their kernels reserve a larger stack)");
   const double v[] = {desc->sqrt_s, desc->mz, desc->wz, desc->mw, desc->ww, desc->mt,
                       desc->wt, desc->alpha, desc->sw2, desc->alpha_s};
   for (double x : v)
