@@ -219,3 +219,18 @@ def test_ttbb_flavour_sum_both_pair_orientations(ora, synth, ttbb_setup):
         want += 2 * f[1][0] * f[0][1] * ora.msq_ttbb(P, 1, k12[1], k12[0], *mom)
     assert got == pytest.approx(want, rel=1e-12, abs=0)
 
+
+
+def test_ttbb_pair_exchange_symmetry_with_massless_tops(ora, synth):
+    """With m_t = 0 the two quark pairs differ only by their labels: |M|^2 is symmetric
+    under exchanging (t, tbar) with (b, bbar), in both channels. This ties the top-line
+    diagrams to the b-line ones (classes A/B, the two halves of D and E) and the two
+    orders of the pair gluons on the light line."""
+    P = ora.process(2, dict(synth.DEFAULT_PROCESS, mt=0.0))
+    rng = np.random.default_rng(67)
+    for rs in (500.0, 1500.0):
+        k1, k2, p1, p2, p3, p4 = _kinematics(rng, rs, 0.0)
+        for channel in (0, 1):
+            a = ora.msq_ttbb_production(P, channel, k1, k2, p1, p2, p3, p4)
+            b = ora.msq_ttbb_production(P, channel, k1, k2, p3, p4, p1, p2)
+            assert a > 0 and b == pytest.approx(a, rel=1e-12, abs=0)
