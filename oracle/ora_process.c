@@ -624,6 +624,29 @@ int ora_integrand_roots(const ora_process* P, const ora_tf* T, const float* rec,
   return n;
 }
 
+/* Density at given lab-frame final-state momenta with delta-function transfer
+ * functions and no change of variables (Sec. 1, Eq. "mem_def" with the n-body
+ * phase-space element): PDF-weighted, flavour-summed |M|^2, flux 1/(|q1||q2|),
+ * (2 pi)^4, the 2/s of the consumed dx1 dx2 and prod_i 1/((2 pi)^3 2 E_i) at the lab
+ * energies; the transverse imbalance is removed by the transverse boost of
+ * to_parton_frame. lab: nfs x (E, px, py, pz) in the process's lab order; rec
+ * supplies the lepton charge (W). aux as for state_weight. */
+double ora_density(const ora_process* P, int nfs, const double* lab, const float* rec,
+                   double* aux) {
+  if (nfs < 1 || nfs > 8) return 0.0;
+  state_t S;
+  memset(&S, 0, sizeof(S));
+  S.nfs = nfs;
+  S.meas = 1.0;
+  S.tf = 1.0;
+  S.jac = 1.0;
+  for (int i = 0; i < nfs; ++i) {
+    S.lab[i] = rv(lab[4 * i], lab[4 * i + 1], lab[4 * i + 2], lab[4 * i + 3]);
+    S.meas *= inv_ps(lab[4 * i]);
+  }
+  return state_weight(P, &S, rec, aux);
+}
+
 /* Parton-level ttbar weight (Sec. 4, parton level): every final-state momentum is
  * known, so all transfer functions are delta functions and nothing is integrated.
  * The record holds l+, the two b quarks, d, ubar and the neutrino as objects 0..5;

@@ -90,6 +90,13 @@ double ora_integrand(const ora_process* P, const ora_tf* T, const float* rec, in
  * fs_lab receives the same momenta before the boost (lab frame).
  * Returns the number of root branches (0 if the point has no solution).
  * `root` picks the branch. Extra diagnostics in aux (process dependent). */
+/* Density at lab-frame final-state momenta (nfs x 4: E, px, py, pz) with
+ * delta-function TFs and no change of variables: flavour-summed PDF x |M|^2,
+ * flux, (2 pi)^4 2/s, prod 1/((2 pi)^3 2E); aux (optional, 4): x1, x2, s-hat,
+ * PDF-weighted |M|^2. rec supplies the lepton charge for W. */
+double ora_density(const ora_process* P, int nfs, const double* lab, const float* rec,
+                   double* aux);
+
 /* Parton-level ttbar weight (Sec. 4): delta TFs for all six final-state partons of a
  * parton-level record (objects l+, b-quark, b-quark, d, ubar, neutrino); bperm 0/1
  * assigns objects 1/2 to (b, bbar) or (bbar, b). aux (NULL or 4 doubles): x1, x2,

@@ -103,6 +103,8 @@ def load():
     lib.ora_strat_side.restype = C.c_uint64
     lib.ora_pdf_q.argtypes = [P, C.c_int, C.c_double, C.c_double]
     lib.ora_pdf_q.restype = C.c_double
+    lib.ora_density.argtypes = [P, C.c_int, _dp, fp, _dp]
+    lib.ora_density.restype = C.c_double
     lib.ora_parton_ttbar.argtypes = [P, fp, C.c_int, _dp]
     lib.ora_parton_ttbar.restype = C.c_double
     lib.ora_parton_batch.argtypes = [P, fp, C.c_int64, C.c_int, _dp, _dp]
@@ -256,6 +258,20 @@ def flavour_msq(P, fs, k12, x1, x2, rec):
 
 def pdf_q(P, t, x, Q):
     return load().ora_pdf_q(C.byref(P), t, x, Q)
+
+
+def density(P, lab, rec=None):
+    """Density at lab-frame final-state momenta lab (nfs, 4) with delta-function
+    transfer functions and no change of variables; returns (density, aux = (x1, x2,
+    s-hat, PDF-weighted |M|^2)). rec (optional) supplies the W lepton charge."""
+    lab = np.ascontiguousarray(lab, dtype=np.float64).reshape(-1, 4)
+    if rec is None:
+        rec = np.zeros(REC, dtype=np.float32)
+    rec, rp = _rec_ptr(rec)
+    aux = np.zeros(4)
+    w = load().ora_density(C.byref(P), lab.shape[0], lab.ctypes.data_as(_dp), rp,
+                           aux.ctypes.data_as(_dp))
+    return w, aux
 
 
 def parton_ttbar(P, rec, bperm):

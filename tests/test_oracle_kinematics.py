@@ -8,8 +8,10 @@ E^2 sin(theta) dE) and of its transfer-function normalisation (Sec. 1).
 * The Jacobian the oracle multiplies in equals |det d(physical variables)/dx|
   computed by central finite differences of the map itself.
 * Parton-level limit (Sec. 4, first analysis level: delta-function TFs): with
-  a vanishing lepton resolution the Drell-Yan integral reduces to the integrand
-  evaluated at the measured momenta.
+  a vanishing lepton resolution the Drell-Yan integral approaches the
+  delta-TF evaluation at the measured momenta as O(r^2). This restates the
+  density's prefactor, so it checks the limit only; the prefactor itself is
+  pinned in test_oracle_normalisation.py.
 """
 import math
 
