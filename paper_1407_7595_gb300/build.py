@@ -13,6 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmem.so")
+PEAK_SRC = os.path.join(HERE, "peaks", "alu_peak.cu")
+PEAK_LIB = os.path.join(HERE, "libpeak.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Division and square root at 2 ulp (MUFU-based) and flush-to-zero: the FP32 integrand
@@ -33,7 +35,34 @@ def _newest_input():
     return max(os.path.getmtime(f) for f in files)
 
 
+def build_peak(force=False, verbose=False):
+    """The ALU microbenchmark library (FP32/FP64/MUFU peaks for the roofline); not
+    part of the integrator."""
+    if not force and os.path.exists(PEAK_LIB) and os.path.getmtime(PEAK_LIB) >= os.path.getmtime(PEAK_SRC):
+        return PEAK_LIB
+    tmp = PEAK_LIB + f".tmp{os.getpid()}"
+    cmd = [NVCC] + ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
+                           "-cudart", "static", PEAK_SRC, "-o", tmp]
+    if verbose:
+        print(" ".join(cmd), flush=True)
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, PEAK_LIB)
+    return PEAK_LIB
+
+
 def build(force=False, verbose=False):
+    peak = None
+    if force or not os.path.exists(PEAK_LIB):
+        peak = subprocess.Popen([sys.executable, "-c", "import sys; sys.path.insert(0, %r); "
+                                 "import build as B; B.build_peak(force=True)" % HERE])
+    try:
+        return _build_lib(force, verbose)
+    finally:
+        if peak is not None and peak.wait() != 0:
+            raise RuntimeError("nvcc failed for peaks/alu_peak.cu")
+
+
+def _build_lib(force=False, verbose=False):
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
