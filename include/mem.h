@@ -60,9 +60,11 @@ enum {
                             * top virtualities, the Higgs pair's f = E1 + E2 and m_H^2), 12 jet
                             * assignments. Records: objects 0 l+ (kind 4), 1 mu- (kind 1), 2..5 the
                             * b jets (kind 5). Needs mh, wh, mb in the process description.
-                            * mem_integrate at a fixed budget (no target_rel_err) and
+                            * mem_integrate (fixed or adaptive budget), mem_integrate_batch and
                             * mem_eval_points (mem_integrate_noalloc rejects it: its kernels
-                            * raise the per-thread stack limit, which reserves device memory). */,
+                            * raise the per-thread stack limit, which reserves device memory;
+                            * the first call on a device does that set-up, so it should come
+                            * before any stream capture). */,
   MEM_PROC_TTBB_DILEP = 5  /* gg, q qbar -> t tbar b bbar -> (b l+ nu)(bbar mu- nubar) b bbar, the
                             * background of Sec. 3-4: the variables and 12 jet assignments of
                             * MEM_PROC_TTH_DILEP with the extra pair's mass mapped uniformly (no
@@ -295,17 +297,27 @@ mem_status mem_ttbb_colour_matrices(float* kgg, float* kqq);
  * as mem_integrate with the default plan (5 VEGAS adaptation iterations of
  * min(2^14, n/8) points, alpha 1.5) and takes the process and transfer
  * functions by descriptor (no handles). `records` (n_events x 32 float32),
- * `prob`, `err` and `ev_status` (optional) must be DEVICE memory; the call is
+ * `prob`, `err` and `ev_status` (optional) must be plain DEVICE memory of the
+ * current device (not host, pinned, managed or another GPU's memory; anything
+ * else is rejected with MEM_ERR_INVALID_ARG before any launch); the call is
  * asynchronous on `stream` and copies nothing.
  * Working memory (grids, per-item constants, partial sums) is one static
  * device array of MEM_NOALLOC_SCRATCH_BYTES that every GPU loading the library
  * keeps until exit; a call needing more is rejected with MEM_ERR_INVALID_ARG
- * (about 2,400 Drell-Yan or W events at 2^20 points per event fit). The
- * first call on a device, with that device current, looks up the array's
- * device address (cudaGetSymbolAddress) and caches it; make that first call
- * before any stream capture. All calls share the array: calls that overlap on
- * the GPU (other streams, other host threads) race on it and must be
- * serialised by the caller. Nothing in it needs clearing between calls. */
+ * (about 2,400 Drell-Yan or W events at 2^20 points per event fit).
+ * Set-up: the first call on a device, with that device current, looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it; with CUDA's
+ * lazy module loading that call, and the first launch of each kernel, also
+ * loads the module and kernels, which reserves device memory. A caller that
+ * may not allocate later makes one small call per process kind it will use
+ * (e.g. 1 event, 16 points) at start-up, before it reserves its memory pool
+ * and before any stream capture; later calls allocate nothing. Kinds 0-3 need
+ * at most 752 bytes of per-thread stack, inside the default 1024-byte limit,
+ * so no launch grows the context's local memory; kinds 4 and 5 are rejected.
+ * All calls share the array: calls that overlap on the GPU (other streams,
+ * other host threads) race on it and must be serialised by the caller.
+ * Nothing in it needs clearing between calls: every region is written by the
+ * call before the call reads it. */
 mem_status mem_integrate_noalloc(const mem_process_desc* desc, const mem_tf_desc* tf,
                                  const float* records, int64_t n_events, uint64_t n_points,
                                  uint64_t seed, uint64_t event_id_base, double* prob,
@@ -322,6 +334,18 @@ mem_status mem_integrate_noalloc(const mem_process_desc* desc, const mem_tf_desc
  * |A| = 4 (k even) or 3 (k odd) and |B| = 7 - |A|: W1a [|A|][128], W1c [16][128],
  * b1 [128], W2 [128][128], b2 [128], W3 [128][2|B|], b3 [2|B|]. */
 typedef struct mem_flow mem_flow;
+
+/* Poll limit of every bounded tensor-core completion wait in the flow's
+ * sampling kernels (mem_integrate_flow, mem_flow_eval_points) on the current
+ * device; MEM_TC_WAIT_DEFAULT at load. A wait that reaches the limit gives up:
+ * its CTA drains the products it has committed (a second bounded wait),
+ * releases its tensor memory and stops, and the call returns MEM_ERR_TIMEOUT
+ * with the context still usable. Lowering the limit (0 gives up at once) is a
+ * test of that path; no paper counterpart. Synchronous; not to be called while
+ * kernels of this library run.
+ * Errors: MEM_ERR_CUDA. */
+#define MEM_TC_WAIT_DEFAULT (1u << 20)
+mem_status mem_set_tc_wait_limit(uint32_t polls);
 
 /* Number of FP32 parameters of the flow. */
 int64_t mem_flow_param_count(void);

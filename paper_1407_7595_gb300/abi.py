@@ -75,6 +75,7 @@ SIGNATURES = [
                                 C.POINTER(mem_opts), _vp, _vp, _vp, _vp, _vp]),
     ("mem_integrate_batch", C.c_int, [C.c_int32, _vp, _vp, _vp, C.c_uint64, C.POINTER(mem_opts),
                                       _vp, _vp, _vp, _vp, _vp]),
+    ("mem_set_tc_wait_limit", C.c_int, [C.c_uint32]),
     ("mem_integrate_noalloc", C.c_int, [C.POINTER(mem_process_desc), C.POINTER(mem_tf_desc),
                                         _vp, C.c_int64, C.c_uint64, C.c_uint64, C.c_uint64,
                                         _vp, _vp, _vp, _vp]),
@@ -284,10 +285,42 @@ def mem_discriminant(prob_s, err_s, prob_b, err_b, D, err_D=None, status=None, s
 
 def mem_integrate_noalloc(desc, tf, records, n_points, seed, event_id_base, prob, err,
                           ev_status=None, stream=None):
-    """Allocation-free integration: records, prob, err, ev_status are device tensors."""
-    _check(lib().mem_integrate_noalloc(C.byref(desc), C.byref(tf), _ptr(records),
-                                       records.shape[0], n_points, seed, event_id_base,
-                                       _ptr(prob), _ptr(err), _ptr(ev_status), stream))
+    """Allocation-free integration: records (n, 32) float32, prob and err (>= n)
+    float64, ev_status (>= n, optional) int32, all contiguous CUDA tensors on the
+    current device. Anything else raises MemError(MEM_ERR_INVALID_ARG) here,
+    before the library is called, so that no kernel reads or writes past a
+    buffer."""
+    import torch
+    dev = torch.cuda.current_device()
+
+    def check(t, name, dtype, n=None, width=None):
+        ok = (isinstance(t, torch.Tensor) and t.is_cuda and t.device.index == dev and
+              t.dtype == dtype and t.is_contiguous())
+        if ok and width is not None:
+            ok = t.dim() == 2 and t.shape[1] == width
+        if ok and n is not None:
+            ok = t.numel() >= n
+        if not ok:
+            msg = (f"{name} must be a contiguous {dtype} CUDA tensor on device {dev}"
+                   + (f" of shape (n, {width})" if width else f" with at least {n} elements"))
+            raise MemError(MEM_ERR_INVALID_ARG, msg)
+    check(records, "records", torch.float32, width=REC)
+    n = records.shape[0]
+    check(prob, "prob", torch.float64, n)
+    check(err, "err", torch.float64, n)
+    if ev_status is not None:
+        check(ev_status, "ev_status", torch.int32, n)
+    _check(lib().mem_integrate_noalloc(C.byref(desc), C.byref(tf), _ptr(records), n, n_points,
+                                       seed, event_id_base, _ptr(prob), _ptr(err),
+                                       _ptr(ev_status), stream))
+
+
+MEM_TC_WAIT_DEFAULT = 1 << 20
+
+
+def mem_set_tc_wait_limit(polls):
+    """Poll limit of the flow kernels' tensor-core waits on the current device."""
+    _check(lib().mem_set_tc_wait_limit(polls))
 
 
 def mem_destroy(handle):

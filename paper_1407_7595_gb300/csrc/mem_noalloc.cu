@@ -10,6 +10,18 @@
 // libraries call cudaMalloc. Such callers pass event records and outputs in
 // device memory they own; the working memory (VEGAS grids, per-item
 // constants, partial sums) comes from one fixed array in this file.
+//
+// The first call on a device is a set-up call: it resolves the array's device
+// address, and CUDA's lazy module loading loads the kernels' module (which
+// holds the array) and the kernels on their first launch, which reserves
+// device memory. A caller that may not allocate later makes one small call
+// per process kind it uses at start-up, before it reserves its memory pool
+// and before any stream capture; later calls allocate nothing.
+//
+// Stack: the kernels of kinds 0-3 need at most 752 bytes of per-thread stack
+// (ptxas), within the context's default 1024-byte limit, so no launch grows
+// the context's local memory; the dilepton ttH and ttbb kernels need more and
+// are rejected.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -43,13 +55,16 @@ mem_status cuda_bad(cudaError_t e, const char* what) {
   return MEM_ERR_CUDA;
 }
 
-bool on_device(const void* p) {
+// True for plain device memory of device `dev` (not host, pinned, managed or
+// another GPU's memory): the kernels of this entry point read and write these
+// pointers directly and copy nothing.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes at;
   if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -93,9 +108,14 @@ extern "C" mem_status mem_integrate_noalloc(const mem_process_desc* desc, const 
   const int iters = 5;
   const uint64_t na = n_points / 8 < 16384 ? n_points / 8 : 16384;
   if (na < 1 || n_points < (uint64_t)iters * na + 2) return bad("n_points too small (need >= 16)");
-  if (!on_device(records)) return bad("records must be device memory");
-  if (!on_device(prob) || !on_device(err) || (ev_status && !on_device(ev_status)))
-    return bad("prob, err and ev_status must be device memory (this entry point copies nothing)");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_bad(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return bad("device index above the supported 64");
+  if (!on_device(records, dev)) return bad("records must be device memory of the current device");
+  if (!on_device(prob, dev) || !on_device(err, dev) || (ev_status && !on_device(ev_status, dev)))
+    return bad("prob, err and ev_status must be device memory of the current device (this entry "
+               "point copies nothing)");
 
   const int64_t n_items = n_events * np;
   const uint32_t n_main = (uint32_t)(n_points - (uint64_t)iters * na);
@@ -110,10 +130,6 @@ extern "C" mem_status mem_integrate_noalloc(const mem_process_desc* desc, const 
                std::to_string((size_t)MEM_NOALLOC_SCRATCH_BYTES) +
                " bytes of mem_integrate_noalloc: use fewer events or points per call");
 
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_bad(e, "cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices) return bad("device index above the supported 64");
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> g(g_scratch_lock);

@@ -1,11 +1,15 @@
 """mem_integrate_noalloc, the entry point for callers that may not allocate
 device memory while running (e.g. an online event selection that reserves all
 GPU memory at start-up): its results must match mem_integrate's, call after
-call, while its working memory comes from the library's fixed device array.
+call, while its working memory comes from the library's fixed device array, and
+a call after the set-up call must not change the device's free memory.
 
 Collected last on purpose (file name), so that a run stopping at the first
-failure has already run every other test.
+failure has already run every other test. Passes alone in a fresh process and
+after the rest of the suite.
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -22,10 +26,10 @@ def setup():
     return torch, abi, synth
 
 
-@pytest.mark.parametrize("kind", [0, 1])
-def test_noalloc_matches_mem_integrate_on_two_calls(setup, kind):
+@pytest.mark.parametrize("kind,n_ev,n_pts", [(0, 40, 50000), (1, 40, 50000), (2, 8, 1 << 15),
+                                             (3, 8, 1 << 15)])
+def test_noalloc_matches_mem_integrate_on_two_calls(setup, kind, n_ev, n_pts):
     torch, abi, synth = setup
-    n_ev, n_pts = 40, 50000
     recs = synth.gen_events(kind, n_ev, 6100 + kind)
     ref = abi.Integrator(kind, recs, synth.DEFAULT_PROCESS, synth.DEFAULT_TF[kind])
     want = ref.integrate(n_pts, seed=77, opts=abi.make_opts(event_id_base=5))
@@ -34,20 +38,47 @@ def test_noalloc_matches_mem_integrate_on_two_calls(setup, kind):
     tf = abi.tf_desc(synth.DEFAULT_TF[kind])
     d_recs = torch.from_numpy(recs).cuda()
     stream = torch.cuda.current_stream().cuda_stream
-    for call in range(2):
-        prob = torch.full((n_ev,), -1.0, dtype=torch.float64, device="cuda")
-        err = torch.full_like(prob, -1.0)
-        st = torch.full((n_ev,), 99, dtype=torch.int32, device="cuda")
+    outs = [(torch.full((n_ev,), -1.0, dtype=torch.float64, device="cuda"),
+             torch.full((n_ev,), -1.0, dtype=torch.float64, device="cuda"),
+             torch.full((n_ev,), 99, dtype=torch.int32, device="cuda")) for _ in range(2)]
+    torch.cuda.synchronize()
+    free = []
+    for call, (prob, err, st) in enumerate(outs):
         abi.mem_integrate_noalloc(desc, tf, d_recs, n_pts, 77, 5, prob, err, st, stream)
         torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
         # same kernels and points; the adaptation histograms use FP32 shared-memory
-        # atomics, so the two paths agree to rounding, not bit for bit
-        np.testing.assert_allclose(prob.cpu().numpy(), want["prob"], rtol=1e-6)
-        np.testing.assert_allclose(err.cpu().numpy(), want["err"], rtol=1e-4)
+        # atomics whose order varies, so the adapted grids differ in the last bits.
+        # Drell-Yan and W estimates then agree to rounding. The ttbar kinds have
+        # heavy-tailed weights (dilepton ttbar most: its neutrino Jacobian peaks at
+        # branch points, where a grid edge moved by 1e-7 moves a weight a lot), so
+        # two calls behave like independent MC estimates: they are held to the
+        # rule for independent runs, 3 combined standard errors
+        p, e = prob.cpu().numpy(), err.cpu().numpy()
+        if kind in (0, 1):
+            np.testing.assert_allclose(p, want["prob"], rtol=1e-6)
+            np.testing.assert_allclose(e, want["err"], rtol=1e-4)
+        else:
+            assert np.all(np.abs(p - want["prob"]) <= 3.0 * np.sqrt(e ** 2 + want["err"] ** 2))
+            assert np.all((e > 0) & (e < 3.0 * want["err"]) & (want["err"] < 3.0 * e))
         assert np.all(st.cpu().numpy() == want["status"])
+    # the second call (after the set-up call) allocated nothing on the device
+    assert free[1] == free[0]
 
 
-def test_noalloc_rejects_oversize_and_host_buffers(setup):
+@pytest.mark.parametrize("kind", [4, 5])
+def test_noalloc_rejects_the_large_stack_kinds(setup, kind):
+    torch, abi, synth = setup
+    desc = abi.process_desc(kind, synth.DEFAULT_PROCESS)
+    tf = abi.tf_desc(synth.DEFAULT_TF[kind])
+    d_recs = torch.from_numpy(synth.gen_events(kind, 2, 6300 + kind)).cuda()
+    prob = torch.zeros(2, dtype=torch.float64, device="cuda")
+    with pytest.raises(abi.MemError) as e:
+        abi.mem_integrate_noalloc(desc, tf, d_recs, 4096, 1, 0, prob, torch.zeros_like(prob))
+    assert e.value.status == abi.MEM_ERR_INVALID_ARG
+
+
+def test_noalloc_rejects_oversize_and_wrong_buffers(setup):
     torch, abi, synth = setup
     kind = 1
     desc = abi.process_desc(kind, synth.DEFAULT_PROCESS)
@@ -64,5 +95,22 @@ def test_noalloc_rejects_oversize_and_host_buffers(setup):
     with pytest.raises(abi.MemError) as e:
         abi.mem_integrate_noalloc(desc, tf, big, 1 << 20, 1, 0, pb, torch.zeros_like(pb))
     assert "working memory" in str(e.value)
-    with pytest.raises(abi.MemError):
-        abi.mem_integrate_noalloc(desc, tf, d_recs, 50000, 1, 0, np.zeros(8), np.zeros(8))
+    # the binding refuses wrong buffers before the library sees them
+    bad_cases = [
+        (d_recs, torch.zeros(8, dtype=torch.float32, device="cuda"), err),    # prob dtype
+        (d_recs, torch.zeros(4, dtype=torch.float64, device="cuda"), err),    # prob too short
+        (d_recs[:, :16].contiguous(), prob, err),                             # record width
+        (d_recs.double(), prob, err),                                         # record dtype
+        (d_recs, prob.cpu(), err),                                            # host tensor
+        (d_recs.t(), prob, err),                                              # not contiguous
+    ]
+    for r, p, q in bad_cases:
+        with pytest.raises(abi.MemError) as e:
+            abi.mem_integrate_noalloc(desc, tf, r, 50000, 1, 0, p, q)
+        assert e.value.status == abi.MEM_ERR_INVALID_ARG
+    # the library itself refuses host (pinned) outputs: called without the binding
+    host = torch.zeros(8, dtype=torch.float64).pin_memory()
+    rc = abi.lib().mem_integrate_noalloc(C.byref(desc), C.byref(tf), C.c_void_p(d_recs.data_ptr()), 8,
+                                         50000, 1, 0, C.c_void_p(host.data_ptr()),
+                                         C.c_void_p(err.data_ptr()), None, None)
+    assert rc == abi.MEM_ERR_INVALID_ARG
