@@ -173,6 +173,12 @@ mem_status mem_flow_samples(const mem_events* events, const mem_process* process
   return MEM_OK;
 }
 
+mem_status mem_set_tc_wait_limit(uint32_t polls) {
+  const cudaError_t e = cudaMemcpyToSymbol(mem::c_tc_wait_limit, &polls, sizeof(polls));
+  if (e != cudaSuccess) return cuda_fail("mem_set_tc_wait_limit", e);
+  return MEM_OK;
+}
+
 mem_status mem_flow_eval_points(const mem_process* process, const mem_tf_desc* tf,
                                 const mem_flow* flow, const float* record, int32_t perm,
                                 uint64_t seed, uint32_t event_id, uint32_t point0, int64_t n,

@@ -28,7 +28,11 @@ constexpr int FROWS = 128;       // rows per tensor-core tile (M of the MMA)
 // tensor memory of a CTA: 128 x 128 FP32, the first-layer accumulator and then
 // the hidden layer's
 constexpr uint32_t F_TMEM_COLS = 128;
-constexpr uint32_t F_WAIT_LIMIT = 1u << 20;  // polls of one MMA-completion wait
+constexpr uint32_t F_WAIT_LIMIT = 1u << 20;   // polls of one MMA-completion wait (default)
+constexpr uint32_t F_DRAIN_LIMIT = 1u << 22;  // polls of the drain wait after a wait gave up
+// Poll limit of the MMA-completion waits of the flow kernels on this device
+// (mem_set_tc_wait_limit; tests lower it to exercise the timeout path).
+__constant__ uint32_t c_tc_wait_limit = F_WAIT_LIMIT;
 constexpr int FTS = 128;         // training samples per item
 
 // The 16 conditioning features of an item (event record, jet permutation), in
@@ -310,7 +314,12 @@ __device__ __forceinline__ bool flow_tc_mma(uint32_t d_tmem, uint32_t a_addr, ui
       umma_bf16(d_tmem, umma_desc(a_addr + 256u * (uint32_t)s, 128, sbo_a),
                 umma_desc(b_addr + 256u * (uint32_t)s, 128, sbo_b), idesc, s > 0 ? 1u : 0u);
     umma_commit(mbar);
-    if (!mbar_wait(mbar, phase, F_WAIT_LIMIT)) *abort = 1;
+    if (!mbar_wait(mbar, phase, c_tc_wait_limit)) {
+      // give up, but first drain the committed products (bounded as well) so that
+      // nothing writes this CTA's tensor memory after it is released
+      *abort = 1;
+      mbar_wait(mbar, phase, F_DRAIN_LIMIT);
+    }
   }
   phase ^= 1u;
   __syncthreads();   // the issuing thread saw the product complete
