@@ -277,7 +277,8 @@ ProcConst make_proc_const(const mem_process_desc& d) {
   if (d.kind == PROC_DY) P.prefactor = (2.0 / s) / (4.0 * tp * tp);
   else if (d.kind == PROC_W) P.prefactor = (2.0 / s) / (8.0 * tp * tp);
   else if (d.kind == PROC_TTH || d.kind == PROC_TTBB)   // eight final-state particles
-    P.prefactor = (2.0 / s) * std::pow(tp, 4.0 - 24.0) / 256.0 / TTH_WEIGHT_SCALE / TTH_DEC_SCALE;
+    P.prefactor = (2.0 / s) * std::pow(tp, 4.0 - 24.0) / 256.0 / TTH_WEIGHT_SCALE / TTH_DEC_SCALE /
+                  (double)TTH_OUT_SCALE;
   else P.prefactor = (2.0 / s) * std::pow(tp, 4.0 - 18.0) / 64.0 / TT_WEIGHT_SCALE;
   return P;
 }

@@ -211,19 +211,22 @@ extern "C" mem_status mem_integrate_batch(int32_t n_groups, const mem_events* co
     if (ev->kind != pr->desc.kind)
       return bfail(MEM_ERR_INVALID_ARG, "group " + std::to_string(g) + ": process kind mismatch");
     const int kind = pr->desc.kind, d = dims_of(kind), np = nperm_of(kind);
-    if (kind == PROC_TTH || kind == PROC_TTBB)
-      return bfail(MEM_ERR_INVALID_ARG, "group " + std::to_string(g) +
-                                            ": dilepton ttH and ttbb are integrated at a fixed budget only");
     const mem_tf_desc& T = *tfs[g];
     if ((kind == PROC_DY || kind == PROC_W) &&
         !(T.lep_rel > 0 && T.window_k > 0 && T.lep_rel * T.window_k < 1))
       return bfail(MEM_ERR_INVALID_ARG, "lepton TF parameters invalid");
     if ((kind == PROC_W || kind == PROC_TTBAR) && !(T.met_sigma > 0 && T.met_box_k > 0))
       return bfail(MEM_ERR_INVALID_ARG, "MET TF parameters invalid");
-    if ((kind == PROC_TTBAR || kind == PROC_TTDL) &&
+    if ((kind == PROC_TTBAR || kind == PROC_TTDL || kind == PROC_TTH || kind == PROC_TTBB) &&
         !(T.jet_core > 0 && T.jet_tail > 0 && T.jet_tail_w >= 0 && T.jet_tail_w <= 1 &&
           T.jet_lo_div > 1 && T.jet_hi_mul > 1))
       return bfail(MEM_ERR_INVALID_ARG, "jet TF parameters invalid");
+    // per-device set-up that may synchronise: before the graph capture below
+    if (kind == PROC_TTH || kind == PROC_TTBB) {
+      const cudaError_t pe = kind == PROC_TTH ? prepare_tth() : prepare_ttbb();
+      if (pe != cudaSuccess)
+        return bfail(MEM_ERR_CUDA, std::string("kernel set-up: ") + cudaGetErrorString(pe));
+    }
     // this group's schedule: its plan entry where given, else the common options
     const mem_plan* pl = opts->plans ? &opts->plans[g] : nullptr;
     const int iters = pl && pl->n_adapt_iters ? pl->n_adapt_iters : opts->n_adapt_iters;
@@ -333,6 +336,8 @@ extern "C" mem_status mem_integrate_batch(int32_t n_groups, const mem_events* co
       ce = kind == PROC_DY     ? launch_batch_dy(plans[g].b, gs[g])
            : kind == PROC_W    ? launch_batch_w(plans[g].b, gs[g])
            : kind == PROC_TTDL ? launch_batch_ttdl(plans[g].b, gs[g])
+           : kind == PROC_TTH  ? launch_batch_tth(plans[g].b, gs[g])
+           : kind == PROC_TTBB ? launch_batch_ttbb(plans[g].b, gs[g])
                                : launch_batch_tt(plans[g].b, gs[g]);
       if (ce == cudaSuccess) ce = cudaEventRecord(done[g], gs[g]);
       if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cs, done[g], 0);

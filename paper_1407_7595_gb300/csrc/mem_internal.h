@@ -126,6 +126,13 @@ cudaError_t launch_batch_dy(const BatchArgs&, cudaStream_t);
 cudaError_t launch_batch_w(const BatchArgs&, cudaStream_t);
 cudaError_t launch_batch_tt(const BatchArgs&, cudaStream_t);
 cudaError_t launch_batch_ttdl(const BatchArgs&, cudaStream_t);
+cudaError_t launch_batch_tth(const BatchArgs&, cudaStream_t);
+cudaError_t launch_batch_ttbb(const BatchArgs&, cudaStream_t);
+// Per-device set-up of the dilepton ttH / ttbb kernels (per-thread stack limit,
+// ttbb colour matrices); host calls that may synchronise, so they run before
+// any stream capture.
+cudaError_t prepare_tth();
+cudaError_t prepare_ttbb();
 // The same with tabulated PDFs (P.pdf_grid set): kernels built for that path
 // (mem_launch_grid.cu); the functions above forward to them.
 cudaError_t launch_integrate_dy_grid(const IntegrateArgs&, cudaStream_t);

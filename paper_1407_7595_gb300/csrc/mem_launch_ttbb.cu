@@ -1,6 +1,7 @@
 // Kernel instantiations for the dilepton ttbb process (fixed-budget integration and
 // point evaluation), and the colour matrices of its production terms.
 #include <complex>
+#include <mutex>
 #include <vector>
 
 #include "mem_launch.cuh"
@@ -184,15 +185,28 @@ std::vector<float2> colour_matrix(bool gg) {
   return K;
 }
 
-// The colour matrices in this context's constant memory (set on every launch path
-// call: constant memory belongs to the current device's context).
+// The colour matrices in constant memory: uploaded once per device (constant
+// memory belongs to each device's context), at the first call that launches a
+// ttbb kernel on it, before any stream capture.
 cudaError_t ttbb_colour_upload() {
   static const std::vector<float2> kgg = colour_matrix(true), kqq = colour_matrix(false);
-  cudaError_t e = cudaMemcpyToSymbol(c_ttbb_kgg, kgg.data(), kgg.size() * sizeof(float2));
+  static std::mutex lock;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(lock);
+  if (done[dev]) return cudaSuccess;
+  e = cudaMemcpyToSymbol(c_ttbb_kgg, kgg.data(), kgg.size() * sizeof(float2));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ttbb_kqq, kqq.data(), kqq.size() * sizeof(float2));
+  if (e == cudaSuccess) done[dev] = true;
   return e;
 }
 
+// The ttbb kernels keep up to ~3 KB per thread on the stack (ptxas: see the
+// stack-frame record in profiles/); raise the context's per-thread stack limit
+// to 4 KB if it is lower (this reserves device memory once per context).
 cudaError_t ttbb_stack() {
   size_t cur = 0;
   cudaError_t e = cudaDeviceGetLimit(&cur, cudaLimitStackSize);
@@ -202,20 +216,33 @@ cudaError_t ttbb_stack() {
 
 }  // namespace
 
-cudaError_t launch_integrate_ttbb(const IntegrateArgs& a, cudaStream_t st) {
+cudaError_t prepare_ttbb() {
   cudaError_t e = ttbb_stack();
   if (e == cudaSuccess) e = ttbb_colour_upload();
+  return e;
+}
+
+cudaError_t launch_integrate_ttbb(const IntegrateArgs& a, cudaStream_t st) {
+  cudaError_t e = prepare_ttbb();
   if (e != cudaSuccess) return e;
   return run_integrate<PhysTTBB, PPT_DL, MINB_DL, MINB_DL_MAIN>(a, st);
 }
 cudaError_t launch_eval_ttbb(const EvalArgs& a, cudaStream_t st) {
-  cudaError_t e = ttbb_stack();
-  if (e == cudaSuccess) e = ttbb_colour_upload();
+  cudaError_t e = prepare_ttbb();
   if (e != cudaSuccess) return e;
   return run_eval<PhysTTBB>(a, st);
 }
 size_t cache_size_ttbb() { return cache_bytes<PhysTTBB>(); }
 
+}  // namespace mem
+
+#include "mem_batch.cuh"
+
+namespace mem {
+// adaptive rounds; prepare_ttbb() must have run on this device (outside any capture)
+cudaError_t launch_batch_ttbb(const BatchArgs& b, cudaStream_t st) {
+  return run_batch<PhysTTBB, MINB_DL>(b, st);
+}
 }  // namespace mem
 
 extern "C" mem_status mem_ttbb_colour_matrices(float* kgg, float* kqq) {

@@ -24,6 +24,11 @@ constexpr double TT_WEIGHT_SCALE = 1099511627776.0;
 // decay factor 2^40 (both exact powers of two, divided out of the FP64 prefactor).
 constexpr double TTH_WEIGHT_SCALE = 1208925819614629174706176.0;
 constexpr double TTH_DEC_SCALE = 1099511627776.0;
+// ... and the finished per-point weight is multiplied by 2^-64 (exact; also divided
+// out of the prefactor) so that it and its square stay inside the FP32 range of the
+// adaptation histograms and variance sums: with the 2^120 of the intermediates the
+// weights reach ~1e27 and their squares would overflow to infinity.
+constexpr float TTH_OUT_SCALE = 5.42101086242752217e-20f;   // 2^-64
 
 // Constants of a process, built on the host in FP64 and rounded once.
 struct ProcConst {

@@ -673,8 +673,8 @@ struct PhysTTBB_ {
     if (total == 0.f) return 0.f;
     const float gb = dgauss_g(c, c.Ebm, Eb), gbb = dgauss_g(c, c.Ebbm, Ebb);
     // the pair-mass map's Jacobian mmax, the f and (E1, E2) Jacobians f L_f and JH
-    return c.cst * Eb * Ebb * gb * gbb * (wp.R * wm.R) * (tq.R * tbq.R) * mmax * (f * c.Lf) * JH *
-           total;
+    return (c.cst * Eb * Ebb * gb * gbb * (wp.R * wm.R) * (tq.R * tbq.R) * mmax * (f * c.Lf) * JH *
+           total) * TTH_OUT_SCALE;
   }
 };
 using PhysTTBB = PhysTTBB_<PDF_ANY>;

@@ -346,8 +346,8 @@ struct PhysTTH_ {
     if (total == 0.f) return 0.f;
     const float gb = dgauss_g(c, c.Ebm, Eb), gbb = dgauss_g(c, c.Ebbm, Ebb);
     // Higgs decay 2 m_H^2, the f and (E1, E2) Jacobians f L_f and JH
-    return c.cst * Eb * Ebb * gb * gbb * (wp.R * wm.R) * (tq.R * tbq.R) * hq.R *
-           (2.f * hq.q2) * (f * c.Lf) * JH * total;
+    return (c.cst * Eb * Ebb * gb * gbb * (wp.R * wm.R) * (tq.R * tbq.R) * hq.R *
+           (2.f * hq.q2) * (f * c.Lf) * JH * total) * TTH_OUT_SCALE;
   }
 };
 using PhysTTH = PhysTTH_<PDF_ANY>;
