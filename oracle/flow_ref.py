@@ -85,13 +85,19 @@ def _log_sig_prime(z):
     return -a - 2.0 * np.log1p(np.exp(-a))
 
 
-def _mlp(L, za, c):
-    """za: (n, |A|), c: (n, C) -> s, t (n, |B|) and the hidden activations."""
+def _ident(a):
+    return a
+
+
+def _mlp(L, za, c, rnd=_ident):
+    """za: (n, |A|), c: (n, C) -> s, t (n, |B|) and the hidden activations.
+    rnd: rounding applied to the operands of the hidden and output products
+    (the hidden activations and the weights W2, W3), identity by default."""
     a1 = za @ L["W1a"] + c @ L["W1c"] + L["b1"]
-    h1 = np.maximum(a1, 0.0)
-    a2 = h1 @ L["W2"] + L["b2"]
-    h2 = np.maximum(a2, 0.0)
-    o = h2 @ L["W3"] + L["b3"]
+    h1 = rnd(np.maximum(a1, 0.0))
+    a2 = h1 @ rnd(L["W2"]) + L["b2"]
+    h2 = rnd(np.maximum(a2, 0.0))
+    o = h2 @ rnd(L["W3"]) + L["b3"]
     nb = o.shape[1] // 2
     s_raw, t = o[:, :nb], o[:, nb:]
     s = S_MAX * np.tanh(s_raw / S_MAX)
@@ -113,14 +119,14 @@ def forward(layers, u, c):
     return _sig(z), logj
 
 
-def inverse(layers, y, c):
+def inverse(layers, y, c, rnd=_ident):
     """y (n, d) -> u (n, d), log|dy/du| at that point (n,)."""
     d = y.shape[1]
     z = np.log(y) - np.log1p(-y)
     logj = np.sum(_log_sig_prime(z), axis=1)
     for k in reversed(range(len(layers))):
         A, B = masks(d, k)
-        s, t, _ = _mlp(layers[k], z[:, A], c)
+        s, t, _ = _mlp(layers[k], z[:, A], c, rnd)
         z = z.copy()
         z[:, B] = (z[:, B] - t) * np.exp(-s)
         logj += np.sum(s, axis=1)
@@ -128,15 +134,19 @@ def inverse(layers, y, c):
     return _sig(z), logj
 
 
-def loss(layers, y, w, c):
+def loss(layers, y, w, c, rnd=_ident):
     """L = -sum_i w_i log q(y_i) = sum_i w_i log|dy/du|(y_i)."""
-    _, logj = inverse(layers, y, c)
+    _, logj = inverse(layers, y, c, rnd)
     return float(np.sum(w * logj))
 
 
-def grad(layers, y, w, c):
+def grad(layers, y, w, c, rnd=_ident):
     """Gradient of loss() with respect to every parameter, by hand-written
-    reverse-mode differentiation through the inverse map."""
+    reverse-mode differentiation through the inverse map. rnd: rounding of the
+    operands of every product with the hidden layers (activations, weights,
+    dL/d(out) and dL/da2), identity by default; with BF16 rounding it states the
+    same computation as tensor-core kernels that take BF16 operands and
+    accumulate in higher precision."""
     d = y.shape[1]
     n_layers = len(layers)
     z = np.log(y) - np.log1p(-y)
@@ -146,7 +156,7 @@ def grad(layers, y, w, c):
     for k in reversed(range(n_layers)):
         A, B = masks(d, k)
         zk1 = zs[k + 1]
-        s, t, cache = _mlp(layers[k], zk1[:, A], c)
+        s, t, cache = _mlp(layers[k], zk1[:, A], c, rnd)
         zk = zk1.copy()
         zk[:, B] = (zk1[:, B] - t) * np.exp(-s)
         zs[k] = zk
@@ -170,13 +180,13 @@ def grad(layers, y, w, c):
         g_t = -gzb * e
         g_s = -gzb * (zk1[:, B] - t) * e + w[:, None]          # + direct loss term
         g_sraw = g_s * (1.0 - np.tanh(s_raw / S_MAX) ** 2)
-        g_o = np.concatenate([g_sraw, g_t], axis=1)
+        g_o = rnd(np.concatenate([g_sraw, g_t], axis=1))
         G = {"W3": h2.T @ g_o, "b3": g_o.sum(0)}
-        g_h2 = g_o @ L["W3"].T
-        g_a2 = g_h2 * (a2 > 0)
+        g_h2 = g_o @ rnd(L["W3"]).T
+        g_a2 = rnd(g_h2 * (a2 > 0))
         G["W2"] = h1.T @ g_a2
         G["b2"] = g_a2.sum(0)
-        g_h1 = g_a2 @ L["W2"].T
+        g_h1 = g_a2 @ rnd(L["W2"]).T
         g_a1 = g_h1 * (a1 > 0)
         G["W1a"] = zk1[:, A].T @ g_a1
         G["W1c"] = c.T @ g_a1

@@ -54,6 +54,15 @@ __global__ void k_flow_bf16(const FlowW* __restrict__ W, FlowB* __restrict__ B) 
     }
     B->W2u[k][umma_kmajor(n, i, FKH)] = v;
   }
+  // W2 with rows = inputs, K = outputs (the training's backward product)
+  for (int t = threadIdx.x; t < FH * FH; t += blockDim.x) {
+    const int n = t / FH, i = t % FH;
+    B->W2v[k][umma_kmajor(n, i, FH)] = __float2bfloat16_rn(W->W2[k][n][i]);
+  }
+}
+
+cudaError_t set_train_wait_limit(uint32_t polls) {
+  return cudaMemcpyToSymbol(c_train_wait_limit, &polls, sizeof(polls));
 }
 
 // Forward map of n points sharing one conditioning vector: 128 points per CTA.
@@ -236,11 +245,16 @@ mem_status mem_flow_map(const mem_flow* f, const float* cond, const float* u, in
 
 namespace {
 
+static_assert(sizeof(FlowTrainSmem) <= 227 * 1024, "training CTA shared memory above 227 KB");
+
 // set on every call: the attribute belongs to the current device's context
 cudaError_t train_smem_attr() {
   return cudaFuncSetAttribute(k_flow_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sizeof(FlowTrainSmem));
 }
+
+// per-CTA z snapshots of the training kernel (FK + 1 levels x TS samples x 8)
+constexpr size_t ZSCR_PER_CTA = (size_t)(FK + 1) * TS * 8;
 
 }  // namespace
 
@@ -253,15 +267,21 @@ mem_status mem_flow_grad(mem_flow* f, const float* ys, const float* ws, const fl
   for (int64_t i = 0; i < n_items; ++i) b[i] = (int32_t)i;
   int32_t* db = nullptr;
   float* dl = nullptr;
+  float* zscr = nullptr;
+  int* derr = nullptr;
+  int herr = 0;
   cudaError_t e = train_smem_attr();
   if (e == cudaSuccess) e = cudaMalloc(&db, n_items * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&dl, sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&zscr, (size_t)n_items * ZSCR_PER_CTA * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&derr, sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(db, b.data(), n_items * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(dl, 0, sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(derr, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(f->grad, 0, sizeof(FlowW), st);
   if (e == cudaSuccess) {
     k_flow_train<<<(unsigned)n_items, 256, sizeof(FlowTrainSmem), st>>>(
-        f->W, f->B, ys, ws, cs, db, reinterpret_cast<FlowW*>(f->grad), dl);
+        f->W, f->B, ys, ws, cs, db, reinterpret_cast<FlowW*>(f->grad), dl, zscr, derr);
     e = cudaGetLastError();
   }
   std::vector<FlowW> h(1);
@@ -269,9 +289,13 @@ mem_status mem_flow_grad(mem_flow* f, const float* ys, const float* ws, const fl
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaMemcpy(h.data(), f->grad, sizeof(FlowW), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(&lh, dl, sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
   cudaFree(db);
   cudaFree(dl);
+  cudaFree(zscr);
+  cudaFree(derr);
   if (e != cudaSuccess) return ffail(MEM_ERR_CUDA, std::string("mem_flow_grad: ") + cudaGetErrorString(e));
+  if (herr) return ffail(MEM_ERR_TIMEOUT, "mem_flow_grad: a tensor-core wait gave up");
   padded_to_flat(h[0], grad);
   if (loss) *loss = lh;
   return MEM_OK;
@@ -299,9 +323,15 @@ mem_status mem_flow_train(mem_flow* f, const float* ys, const float* ws, const f
     }
   int32_t* db = nullptr;
   float* dl = nullptr;
+  float* zscr = nullptr;
+  int* derr = nullptr;
+  int herr = 0;
   cudaError_t e = train_smem_attr();
   if (e == cudaSuccess) e = cudaMalloc(&db, batches.size() * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&dl, (size_t)n_steps * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&zscr, (size_t)batch_items * ZSCR_PER_CTA * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&derr, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(db, batches.data(), batches.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(dl, 0, (size_t)n_steps * sizeof(float), st);
@@ -311,7 +341,7 @@ mem_status mem_flow_train(mem_flow* f, const float* ys, const float* ws, const f
   for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
     k_flow_train<<<batch_items, 256, sizeof(FlowTrainSmem), st>>>(
         f->W, f->B, ys, ws, cs, db + (size_t)s * batch_items, reinterpret_cast<FlowW*>(f->grad),
-        dl + s);
+        dl + s, zscr, derr);
     ++f->step;
     const float bc1 = 1.f - std::pow(b1, (float)f->step), bc2 = 1.f - std::pow(b2, (float)f->step);
     k_flow_adam<<<256, 256, 0, st>>>(f->W, f->m, f->v, reinterpret_cast<FlowW*>(f->grad), nparam,
@@ -322,9 +352,13 @@ mem_status mem_flow_train(mem_flow* f, const float* ys, const float* ws, const f
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess && loss_trace)
     e = cudaMemcpy(loss_trace, dl, (size_t)n_steps * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
   cudaFree(db);
   cudaFree(dl);
+  cudaFree(zscr);
+  cudaFree(derr);
   if (e != cudaSuccess) return ffail(MEM_ERR_CUDA, std::string("mem_flow_train: ") + cudaGetErrorString(e));
+  if (herr) return ffail(MEM_ERR_TIMEOUT, "mem_flow_train: a tensor-core wait gave up");
   return MEM_OK;
 }
 

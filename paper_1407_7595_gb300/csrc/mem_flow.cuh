@@ -8,11 +8,13 @@
 //   A = coordinates with parity k % 2, B = the rest; c = 16 measured-momentum features
 //   log|dy/du| = sum log sigmoid'(z_out) + sum_k sum_B s - sum log sigmoid'(z_in)  (exact)
 //
-// Tensor cores: the layers run as mma.sync m16n8k16 BF16 x BF16 -> FP32 per warp
-// on 16-point row blocks; the per-item conditioning term c W1c + b1 is FP32 and
-// initialises the first layer's accumulators. The accumulator fragments of one
-// layer are re-packed in registers as the A operand of the next. The training
-// kernels evaluate the first layer (K = |A| <= 4) in FP32; inference runs it as a
+// Tensor cores: the sampling kernels (mem_flow_int.cuh) and the training kernel
+// (mem_flow_train.cuh) run the first and hidden products on tcgen05 with tensor-
+// memory accumulators; the sampling kernels' 8-wide output layer stays on warp-
+// level mma.sync, where a tensor-memory round trip costs more than the product.
+// The small forward map entry point (mem_flow_map) runs every layer as mma.sync
+// m16n8k16 on 16-point row blocks (flow_layer_rows below). The training kernel
+// evaluates the first layer (K = |A| <= 4) in FP32; inference runs it as a
 // K = 16 product of a two-part BF16 split of z_A and of W1a (~16 bits kept).
 #pragma once
 #include "mem_fastmath.cuh"
@@ -57,7 +59,7 @@ struct FlowW {
 // = 0; the activation operand carries 1, 1, 0 ... in those columns.
 // W1u and W3u are the first and output layers as tcgen05 B operands (same
 // layout): W1u N 128 x K 16 in the split form of W1t; W3u N 16 x K 128, rows
-// n < 8 = W3[k][.][n], rows 8-15 zero.
+// n < 8 = W3[k][.][n], rows 8-15 zero; W2v below.
 struct FlowB {
   __nv_bfloat16 W2t[FK][FH][FLD];
   __nv_bfloat16 W3t[FK][8][FLD];
@@ -65,6 +67,8 @@ struct FlowB {
   __nv_bfloat16 W2u[FK][FH * FKH];
   __nv_bfloat16 W1u[FK][FH * 16];
   __nv_bfloat16 W3u[FK][16 * FH];
+  __nv_bfloat16 W2v[FK][FH * FH];   // W2 as the B operand of dL/dh1 = dL/da2 W2^T (training):
+                                    // N 128 (in) x K 128 (out), K-major, no swizzle
 };
 
 // Element index of (row m, column k) of a K-column tile in the tcgen05
@@ -103,111 +107,6 @@ __device__ __forceinline__ float log_sig_prime(float z) {
   // log(sigmoid(z)(1 - sigmoid(z))) = -|z| - 2 log(1 + e^-|z|)
   const float a = fabsf(z);
   return -a - 2.f * log1pf(__expf(-a));
-}
-
-// Shared-memory image of one layer for the forward pass.
-struct __align__(16) FlowLayerSmem {
-  __nv_bfloat16 W2t[FH][FLD];
-  __nv_bfloat16 W3t[8][FLD];
-  float W1a[4][FH];
-  float cb1[FH];   // c W1c + b1 for the CTA's item
-  float b2[FH];
-  float b3[8];
-};
-
-// Cooperative load of layer k (BF16 operands + FP32 small parts) and the
-// per-item conditioning bias c W1c + b1.
-__device__ inline void flow_load_layer(FlowLayerSmem& L, const FlowW* __restrict__ W,
-                                       const FlowB* __restrict__ Bw, int k, const float* c) {
-  const uint4* src = reinterpret_cast<const uint4*>(&Bw->W2t[k][0][0]);
-  uint4* dst = reinterpret_cast<uint4*>(&L.W2t[0][0]);
-  for (int t = threadIdx.x; t < (int)(sizeof(L.W2t) / 16); t += blockDim.x) dst[t] = src[t];
-  const uint4* src3 = reinterpret_cast<const uint4*>(&Bw->W3t[k][0][0]);
-  uint4* dst3 = reinterpret_cast<uint4*>(&L.W3t[0][0]);
-  for (int t = threadIdx.x; t < (int)(sizeof(L.W3t) / 16); t += blockDim.x) dst3[t] = src3[t];
-  for (int t = threadIdx.x; t < 4 * FH; t += blockDim.x) (&L.W1a[0][0])[t] = (&W->W1a[k][0][0])[t];
-  for (int n = threadIdx.x; n < FH; n += blockDim.x) {
-    float s = W->b1[k][n];
-#pragma unroll
-    for (int q = 0; q < FC; ++q) s = fmaf(c[q], W->W1c[k][q][n], s);
-    L.cb1[n] = s;
-    L.b2[n] = W->b2[k][n];
-  }
-  if (threadIdx.x < 8) L.b3[threadIdx.x] = W->b3[k][threadIdx.x];
-}
-
-// One warp: MLP of layer k on the 16 points r0..r0+15 whose z live in zs
-// (row stride 8 floats); writes the raw outputs (s_raw | t, + bias) into st[16][8].
-__device__ inline void flow_mlp_st(const FlowLayerSmem& L, int k, const float* zs, int r0,
-                                   float (*st)[8]) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int na = flow_na(k);
-  float za0[4], za1[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    za0[j] = j < na ? zs[(r0 + g) * 8 + flow_a(k, j)] : 0.f;
-    za1[j] = j < na ? zs[(r0 + g + 8) * 8 + flow_a(k, j)] : 0.f;
-  }
-  // first layer in FP32, produced directly as BF16 A fragments (8 k-steps)
-  uint32_t a[8][4];
-#pragma unroll
-  for (int kk = 0; kk < 8; ++kk) {
-    float h[2][4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int col = kk * 16 + 2 * t + (q & 1) + ((q >> 1) << 3);
-      float v0 = L.cb1[col], v1 = L.cb1[col];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        v0 = fmaf(za0[j], L.W1a[j][col], v0);
-        v1 = fmaf(za1[j], L.W1a[j][col], v1);
-      }
-      h[0][q] = fmaxf(v0, 0.f);
-      h[1][q] = fmaxf(v1, 0.f);
-    }
-    a[kk][0] = pack_bf16(h[0][0], h[0][1]);
-    a[kk][1] = pack_bf16(h[1][0], h[1][1]);
-    a[kk][2] = pack_bf16(h[0][2], h[0][3]);
-    a[kk][3] = pack_bf16(h[1][2], h[1][3]);
-  }
-  // hidden layer: 16 n-tiles of 8 columns, K = 128; output layer accumulated on the fly
-  float o[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-  for (int jp = 0; jp < 8; ++jp) {
-    float acc[2][4];
-#pragma unroll
-    for (int h2 = 0; h2 < 2; ++h2) {
-      const int j = 2 * jp + h2;
-      acc[h2][0] = acc[h2][1] = acc[h2][2] = acc[h2][3] = 0.f;
-      const __nv_bfloat16* brow = &L.W2t[j * 8 + g][0];
-#pragma unroll
-      for (int kk = 0; kk < 8; ++kk) {
-        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(brow + kk * 16 + 2 * t);
-        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(brow + kk * 16 + 2 * t + 8);
-        mma_bf16(acc[h2], a[kk], b0, b1);
-      }
-      const float bb0 = L.b2[j * 8 + 2 * t], bb1 = L.b2[j * 8 + 2 * t + 1];
-      acc[h2][0] = fmaxf(acc[h2][0] + bb0, 0.f);
-      acc[h2][1] = fmaxf(acc[h2][1] + bb1, 0.f);
-      acc[h2][2] = fmaxf(acc[h2][2] + bb0, 0.f);
-      acc[h2][3] = fmaxf(acc[h2][3] + bb1, 0.f);
-    }
-    // the two n-tiles (16 hidden columns) are the A fragment of output k-step jp
-    uint32_t a2[4];
-    a2[0] = pack_bf16(acc[0][0], acc[0][1]);
-    a2[1] = pack_bf16(acc[0][2], acc[0][3]);
-    a2[2] = pack_bf16(acc[1][0], acc[1][1]);
-    a2[3] = pack_bf16(acc[1][2], acc[1][3]);
-    const __nv_bfloat16* brow3 = &L.W3t[g][0];
-    const uint32_t b0 = *reinterpret_cast<const uint32_t*>(brow3 + jp * 16 + 2 * t);
-    const uint32_t b1 = *reinterpret_cast<const uint32_t*>(brow3 + jp * 16 + 2 * t + 8);
-    mma_bf16(o, a2, b0, b1);
-  }
-  st[g][2 * t] = o[0] + L.b3[2 * t];
-  st[g][2 * t + 1] = o[1] + L.b3[2 * t + 1];
-  st[g + 8][2 * t] = o[2] + L.b3[2 * t];
-  st[g + 8][2 * t + 1] = o[3] + L.b3[2 * t + 1];
-  __syncwarp();
 }
 
 // ---------------------------------------------------------------------------

@@ -174,7 +174,8 @@ mem_status mem_flow_samples(const mem_events* events, const mem_process* process
 }
 
 mem_status mem_set_tc_wait_limit(uint32_t polls) {
-  const cudaError_t e = cudaMemcpyToSymbol(mem::c_tc_wait_limit, &polls, sizeof(polls));
+  cudaError_t e = cudaMemcpyToSymbol(mem::c_tc_wait_limit, &polls, sizeof(polls));
+  if (e == cudaSuccess) e = mem::set_train_wait_limit(polls);
   if (e != cudaSuccess) return cuda_fail("mem_set_tc_wait_limit", e);
   return MEM_OK;
 }

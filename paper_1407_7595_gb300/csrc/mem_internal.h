@@ -51,6 +51,9 @@ void mem_flow_release(mem_flow* f);
 
 namespace mem {
 
+// Poll limit of the training kernel's tensor-core waits on the current device.
+cudaError_t set_train_wait_limit(uint32_t polls);
+
 struct IntegrateArgs {
   const float* recs;        // device, n_events x REC
   int64_t n_events, n_items;

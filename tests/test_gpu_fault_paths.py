@@ -9,8 +9,9 @@ limit; nothing here faults, traps or hangs the GPU.
 * Exhausted tensor-core wait: with the flow kernels' poll limit at 0 every
   MMA-completion wait gives up at once; each CTA drains its committed products
   (a second bounded wait), releases its tensor memory and stops, and the call
-  returns MEM_ERR_TIMEOUT. With the default limit restored the same call gives
-  the same results as before: the context stayed usable.
+  returns MEM_ERR_TIMEOUT -- for the sampling kernel (mem_flow_eval_points) and
+  the training kernel (mem_flow_grad). With the default limit restored the same
+  calls give the same results as before: the context stayed usable.
 """
 import math
 
@@ -68,16 +69,29 @@ def test_exhausted_tensor_core_wait_returns_timeout(env):
         abi.mem_flow_eval_points(integ.proc, integ.tf, f, rec, int(recs[0, 28]), 9, 0, 0, n, z, lj, w)
         return z.cpu().numpy(), w.cpu().numpy()
 
+    # training data: 4 items of 128 samples (the gradient kernel's tensor-core waits)
+    rng = np.random.default_rng(5)
+    ys = torch.tensor(rng.uniform(0.05, 0.95, (4, 128, 7)), dtype=torch.float32, device="cuda")
+    ws = torch.full((4, 128), 1.0 / 128, dtype=torch.float32, device="cuda")
+    cs = torch.tensor(rng.normal(size=(4, 16)), dtype=torch.float32, device="cuda")
     try:
         z0, w0 = run()
+        g0, l0 = abi.mem_flow_grad(f, ys, ws, cs)
         abi.mem_set_tc_wait_limit(0)
         with pytest.raises(abi.MemError) as e:
             run()
+        assert e.value.status == abi.MEM_ERR_TIMEOUT
+        with pytest.raises(abi.MemError) as e:
+            abi.mem_flow_grad(f, ys, ws, cs)
         assert e.value.status == abi.MEM_ERR_TIMEOUT
     finally:
         abi.mem_set_tc_wait_limit(abi.MEM_TC_WAIT_DEFAULT)
     z1, w1 = run()
     assert np.array_equal(z0, z1) and np.array_equal(w0, w1)
+    g1, l1 = abi.mem_flow_grad(f, ys, ws, cs)
+    # the gradient sums FP32 atomics across CTAs: equal to rounding
+    np.testing.assert_allclose(g1, g0, rtol=1e-4, atol=1e-6 * np.abs(g0).max())
+    assert l1 == pytest.approx(l0, rel=1e-5)
     # the fixed-budget path still works in the same context
     res = integ.integrate(1 << 12, seed=3, opts=abi.make_opts(n_adapt_iters=1, adapt_points=512))
     assert np.all(res["status"] == abi.MEM_OK)
