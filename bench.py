@@ -48,11 +48,12 @@ from paper_1407_7595_gb300 import synth  # noqa: E402
 # re-counted whenever a kernel changes. MUFU, integer (Philox), conversion and
 # memory instructions are not counted as flops. k_adapt adds its shared-memory
 # histogram work to the integrand.
-FLOPS_MAIN_PER_EVAL = {synth.PROC_DY: 157.0, synth.PROC_W: 345.7, synth.PROC_TTBAR: 2842.3}
-FLOPS_ADAPT_PER_EVAL = {}
+FLOPS_MAIN_PER_EVAL = {synth.PROC_DY: 157.0, synth.PROC_W: 345.7, synth.PROC_TTBAR: 2834.9}
+FLOPS_ADAPT_PER_EVAL = {synth.PROC_TTBAR: 2817.6}
 # FP64 flops (DADD, DMUL = 1; DFMA = 2) per evaluation of the dilepton kernels (the
 # neutrino solution runs in FP64 and bounds them), ncu instruction counters.
-FP64_FLOPS_PER_EVAL = {synth.PROC_TTBAR_DILEP: 1002.6}
+FP64_FLOPS_PER_EVAL = {synth.PROC_TTBAR_DILEP: 1002.6, synth.PROC_TTH_DILEP: 1223.3}
+FP64_FLOPS_ADAPT_PER_EVAL = {synth.PROC_TTH_DILEP: 942.0}
 FP64_KINDS = (synth.PROC_TTBAR_DILEP, synth.PROC_TTH_DILEP, synth.PROC_TTBB_DILEP)
 FP32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 FP32 lanes
 # DRAM bytes (read + write) per launch unit from one ncu capture of the current
@@ -95,6 +96,8 @@ def parse():
     ap.add_argument("--workload", choices=["w", "dy", "ttbar", "mix", "flow", "parton", "ttdl", "tth",
                                            "ttbb"],
                     default="ttbar")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip the ALU peak measurement (profiling runs); the roofline then has no peak")
     ap.add_argument("--no-extra", action="store_true",
                     help="default workload: skip the W line and the mix leg in the same JSON line")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the events-to-1%% leg")
@@ -496,7 +499,7 @@ def integrand_leg(abi, torch, name, kind, n_ev, n_pts, seed, steps, warmup, args
                                 t_main, peaks, FLOPS_MAIN_PER_EVAL, FP64_FLOPS_PER_EVAL, sms, clk)
         r_adapt = roofline_entry("k_adapt (VEGAS adaptation + refinement)", kind,
                                  n_ev * n_perm * 5 * n_adapt, t_adapt, peaks,
-                                 FLOPS_ADAPT_PER_EVAL, {}, sms, clk)
+                                 FLOPS_ADAPT_PER_EVAL, FP64_FLOPS_ADAPT_PER_EVAL, sms, clk)
         r_main["share_of_step"] = t_main / t_step
         r_adapt["share_of_step"] = t_adapt / t_step
         dpi = DRAM_BYTES_PER_ITEM_MAIN.get(kind)
@@ -534,7 +537,7 @@ def run_ours(args):
     w = workload(args)
     kind, n_ev, n_pts = w["proc"], w["n_events"], w["n_points"]
     sp = torch.cuda.current_stream().cuda_stream
-    peaks = measure_peaks() if rank == 0 else {}
+    peaks = measure_peaks() if rank == 0 and not args.no_peaks else {}
     main = integrand_leg(abi, torch, args.workload, kind, n_ev, n_pts, w["seed"], args.steps,
                          args.warmup,
                          args, peaks, rank, world, e2e=not args.no_e2e)
@@ -573,6 +576,26 @@ def run_ours(args):
                       min(args.steps, 5), 2, rank, world)
         if rank == 0:
             out["mix"] = mix
+        # the paper's own hadron-level processes (Sec. 3-4): dilepton ttH(H -> b bbar) and
+        # its ttbb background, 8-dim integrals x 12 jet assignments: fixed-budget evals/s
+        # with rooflines, and events brought to 1 % per second (default schedule)
+        for name, n_fix, n_to1 in (("tth", 64, 32), ("ttbb", 16, 8)):
+            wl = synth.WORKLOADS[name]
+            leg = integrand_leg(abi, torch, name, wl["proc"], n_fix, wl["n_points"], wl["seed"],
+                                3, 1, args, peaks, rank, world, e2e=False, clocks=False)
+            ev_h, proc_h, tf_h, _ = leg.pop("handles")
+            abi.mem_destroy(ev_h)
+            ev_a = abi.mem_upload_events(proc_h, synth.gen_events(wl["proc"], n_to1, wl["seed"] + 1), sp)
+            to1 = adaptive_leg(abi, torch, ev_a, proc_h, tf_h, n_to1, 0, sp, kind=wl["proc"],
+                               cal_seed=0, reps=1, autotune=False)
+            abi.mem_destroy(ev_a)
+            abi.mem_destroy(proc_h)
+            if rank == 0:
+                leg["config"]["workload"] = (WORKLOAD_NAMES[name].split(":")[0] +
+                                             f": 8-dim integral x 12 jet assignments, {n_fix} events x "
+                                             f"{wl['n_points']} evaluations/event")
+                leg["to_1pct"] = to1
+                out[name + "_line"] = leg
     if rank == 0 and not args.no_flow:
         out["flow_ab"] = flow_ab_leg(abi, torch, sp, args.flow_train, args.flow_eval,
                                      steps=args.flow_steps)
@@ -585,7 +608,7 @@ def run_ours(args):
 
 
 def adaptive_leg(abi, torch, events, proc, tf, n_ev, eid_base, sp, kind, cal_seed, target=0.01,
-                 reps=3):
+                 reps=3, autotune=True):
     """The same events integrated with the per-event stop rule (err/prob <= 1 %,
     cap 2^24 points per event). value = events that reached the target per second
     (events stopped at the cap are not counted). The schedule is the one the
@@ -612,13 +635,17 @@ def adaptive_leg(abi, torch, events, proc, tf, n_ev, eid_base, sp, kind, cal_see
         return statistics.mean(ms) * 1e-3, statistics.mean(conv)
 
     m_default, c_default = run(abi.make_opts(**base))
-    t = time.perf_counter()
-    cal = abi.mem_upload_events(proc, synth.gen_events(kind, 256, cal_seed), sp)
-    plan, rate, tried = abi.mem_autotune(cal, proc, tf, 77, abi.make_opts(**base), sp)
-    abi.mem_destroy(cal)
-    tuned = {"plan": plan.as_dict(), "plans_timed": tried, "seconds": time.perf_counter() - t,
-             "calibration": f"256 events of the same generator, seed {cal_seed} (not timed)"}
-    m, c = run(abi.make_opts(plans=[plan], **base))
+    if autotune:
+        t = time.perf_counter()
+        cal = abi.mem_upload_events(proc, synth.gen_events(kind, 256, cal_seed), sp)
+        plan, rate, tried = abi.mem_autotune(cal, proc, tf, 77, abi.make_opts(**base), sp)
+        abi.mem_destroy(cal)
+        tuned = {"plan": plan.as_dict(), "plans_timed": tried, "seconds": time.perf_counter() - t,
+                 "calibration": f"256 events of the same generator, seed {cal_seed} (not timed)"}
+        m, c = run(abi.make_opts(plans=[plan], **base))
+    else:
+        tuned = "not run: the library's default schedule"
+        m, c = m_default, c_default
     return {"metric": "events integrated to 1% relative error per second (converged events only)",
             "value": c / m, "unit": "events/s", "ms_per_step": m * 1e3, "events": n_ev,
             "converged_fraction": c / n_ev, "all_events_per_s": n_ev / m,
