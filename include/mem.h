@@ -335,6 +335,18 @@ mem_status mem_integrate_noalloc(const mem_process_desc* desc, const mem_tf_desc
  * b1 [128], W2 [128][128], b2 [128], W3 [128][2|B|], b3 [2|B|]. */
 typedef struct mem_flow mem_flow;
 
+/* The dilepton neutrino solution of the integrand kernels (Sec. 3, Eq.
+ * "dilepsolv": nu and nubar from the W+, W-, t and tbar virtualities and the
+ * missing pT), exposed for parity tests like mem_eval_points. in: n x 22 HOST
+ * doubles per system -- b, bbar, l+, mu- four-momenta (E, px, py, pz; GeV,
+ * massless), MET x, y, q^2 of W+, W-, t, tbar (GeV^2). Writes nsol[n] (0..4), nu
+ * [n][4][8] (per solution nu then nubar, GeV; unused slots 0) and jac [n][4]
+ * (1 / |det d(q^2_W+, q^2_t, q^2_W-, q^2_tbar)/d(nu_x, nu_y, nu_z, nubar_z)|, GeV^-4):
+ * the same FP64 solver stages, checks and de-duplication as the integrand, one
+ * GPU thread per system. Synchronous. Errors: MEM_ERR_INVALID_ARG (NULL, n < 1
+ * or n > 2^24), MEM_ERR_CUDA. */
+mem_status mem_dilep_solve(const double* in, int64_t n, int32_t* nsol, double* nu, double* jac);
+
 /* Poll limit of every bounded tensor-core completion wait in the flow's
  * sampling kernels (mem_integrate_flow, mem_flow_eval_points) on the current
  * device; MEM_TC_WAIT_DEFAULT at load. A wait that reaches the limit gives up:

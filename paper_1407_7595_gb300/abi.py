@@ -76,6 +76,7 @@ SIGNATURES = [
     ("mem_integrate_batch", C.c_int, [C.c_int32, _vp, _vp, _vp, C.c_uint64, C.POINTER(mem_opts),
                                       _vp, _vp, _vp, _vp, _vp]),
     ("mem_set_tc_wait_limit", C.c_int, [C.c_uint32]),
+    ("mem_dilep_solve", C.c_int, [_vp, C.c_int64, _vp, _vp, _vp]),
     ("mem_integrate_noalloc", C.c_int, [C.POINTER(mem_process_desc), C.POINTER(mem_tf_desc),
                                         _vp, C.c_int64, C.c_uint64, C.c_uint64, C.c_uint64,
                                         _vp, _vp, _vp, _vp]),
@@ -313,6 +314,18 @@ def mem_integrate_noalloc(desc, tf, records, n_points, seed, event_id_base, prob
     _check(lib().mem_integrate_noalloc(C.byref(desc), C.byref(tf), _ptr(records), n, n_points,
                                        seed, event_id_base, _ptr(prob), _ptr(err),
                                        _ptr(ev_status), stream))
+
+
+def mem_dilep_solve(systems):
+    """The integrand's dilepton neutrino solver on host systems (n, 22) float64:
+    (nsol (n,), solutions (n, 4, 2, 4) nu / nubar in GeV, jacobians (n, 4))."""
+    a = np.ascontiguousarray(systems, dtype=np.float64).reshape(-1, 22)
+    n = a.shape[0]
+    ns = np.zeros(n, dtype=np.int32)
+    nu = np.zeros((n, 4, 2, 4))
+    jac = np.zeros((n, 4))
+    _check(lib().mem_dilep_solve(a.ctypes.data, n, ns.ctypes.data, nu.ctypes.data, jac.ctypes.data))
+    return ns, nu, jac
 
 
 MEM_TC_WAIT_DEFAULT = 1 << 20

@@ -243,10 +243,35 @@ static __device__ __noinline__ int dl_real_roots(const double* c, int deg, doubl
   const double B = (double)bound;
   double a = -B, dpa;
   double fa = dl_horner(c, deg, a, dpa);
+  // derivative coefficients (FP64) for refining critical points near a double root
+  double c1[4];
+  for (int k = 0; k < deg; ++k) c1[k] = (k + 1) * c[k + 1];
   for (int i = 0; i <= ncrit; ++i) {
-    const double b = i < ncrit ? fmin(fmax((double)crit[i], -B), B) : B;
+    double b = i < ncrit ? fmin(fmax((double)crit[i], -B), B) : B;
     double dpb;
-    const double fb = dl_horner(c, deg, b, dpb);
+    double fb = dl_horner(c, deg, b, dpb);
+    if (i < ncrit && deg >= 2) {
+      // Where the polynomial is small at a critical point, two roots may lie closer
+      // together than the FP32 critical point's error, which would put both on one
+      // side of it and lose them: move it to FP64 accuracy (Newton on p') first.
+      double mag = 0.0, pw = 1.0;
+      for (int k = 0; k <= deg; ++k, pw *= fabs(b)) mag += fabs(c[k]) * pw;
+      if (fabs(fb) <= 1e-6 * mag) {
+        const double hi = i + 1 < ncrit ? fmin(fmax((double)crit[i + 1], -B), B) : B;
+#pragma unroll 1
+        for (int it = 0; it < 4; ++it) {
+          double d2p;   // p''(b), from the Horner pass over p'
+          const double p1 = dl_horner(c1, deg - 1, b, d2p);
+          if (!(d2p != 0.0)) break;
+          const double bn = b - p1 / d2p;
+          if (!(bn > a && bn < hi)) break;
+          const bool done = fabs(bn - b) <= 1e-15 * (1.0 + fabs(b));
+          b = bn;
+          if (done) break;
+        }
+        fb = dl_horner(c, deg, b, dpb);
+      }
+    }
     if (b > a && ((fa < 0.0 && fb > 0.0) || (fa > 0.0 && fb < 0.0))) {
       // the monic FP32 copy has the sign of c times that of the leading coefficient
       const float sa = ((fa < 0.0) != (ilead < 0.0)) ? -1.f : 1.f;
