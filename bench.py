@@ -59,7 +59,7 @@ FP32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 FP32 lanes
 # DRAM bytes (read + write) per launch unit from one ncu capture of the current
 # kernels: k_main reads each item's grid and constants once (other CTAs of the item
 # hit L2), so its traffic grows with the items; k_parton_tt reads each record once.
-DRAM_BYTES_PER_ITEM_MAIN = {synth.PROC_W: 9008.0}
+DRAM_BYTES_PER_ITEM_MAIN = {synth.PROC_W: 9008.0, synth.PROC_TTBAR: 14910.0}
 DRAM_BYTES_PER_PARTON_EVENT = 128.2
 
 # FP32 flops of the parton-level kernel per event (both b-quark assignments; FADD,
