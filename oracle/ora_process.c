@@ -380,17 +380,18 @@ static int states_ttdl(const ora_process* P, const ora_tf* T, const float* rec, 
  * 2..5) of the b and the bbar -- the (perm / 3)-th jet and the (perm % 3)-th of the
  * other three -- and gives the remaining two to the Higgs pair in object order (the
  * two energy solutions below cover both energy orderings of the pair, so the pair is
- * unordered). Variables: x0..x5 as in dilepton ttbar; x6 -> f = E1 + E2 log-uniform
- * over [lo1 + lo2, hi1 + hi2] (the sum of the two jet windows); x7 -> m_H^2
- * (Breit-Wigner map over [0, f^2 (1 - cos theta_12) / 2], the largest invariant mass
- * two massless partons of energy sum f along these directions reach). Given f and
- * m_H^2 = 2 E1 E2 (1 - cos theta_12), E1,2 = (f +- sqrt(f^2 - 4 E1 E2)) / 2, both
- * orderings, each with 1 / |d(f, m_H^2)/d(E1, E2)| = 1 / (2 (1 - cos theta_12) |E1 - E2|);
- * an energy outside its jet window has no weight. Then the missing pT is the visible
- * imbalance and the neutrinos follow from Eq. "dilepsolv" as for dilepton ttbar.
+ * unordered). Variables: x0..x5 as in dilepton ttbar; x7 -> m_H^2 = 2 E1 E2 (1 - cos
+ * theta_12) (Breit-Wigner map over [2 (1 - cos) lo1 lo2, 2 (1 - cos) hi1 hi2], the values
+ * the two jet windows allow); with K = E1 E2 the energy E1 lies in [A, B] = [max(lo1,
+ * K/hi2), min(hi1, K/lo2)] and f = E1 + E2 = E1 + K/E1 in [f_min, f_max], its image (f_min
+ * = 2 sqrt(K) when sqrt(K) is inside); x6 -> f = f_min + (f_max - f_min) x6^2 (the square
+ * removes the 1/sqrt end-point singularity below). Given f and K, E1,2 = (f +-
+ * sqrt(f^2 - 4K)) / 2, both orderings, each with 1 / |d(f, m_H^2)/d(E1, E2)| =
+ * 1 / (2 (1 - cos theta_12) |E1 - E2|); at least one ordering lies inside both jet
+ * windows by construction, one that leaves a window has no weight. Then the missing pT is the visible imbalance and the neutrinos follow from Eq. "dilepsolv" as for dilepton ttbar.
  * Dilepton ttbb (kind 5, the background) uses the same variables (Sec. 4 applies the
  * transformations to both processes) with the extra b bbar pair in the role of the Higgs
- * pair; its mass is not resonant, so m^2 is mapped uniformly over the same range. */
+ * pair; its mass is not resonant, so m^2 is mapped log-uniformly over the same window. */
 static void tth_perm(int perm, int* jb, int* jbb, int* j1, int* j2) {
   int rest[3], n = 0;
   const int ib = perm / 3;
@@ -429,25 +430,33 @@ static int states_tthdl(const ora_process* P, const ora_tf* T, const float* rec,
   if (!(lo_t < s && lo_tb < s)) return 0;
   const double q2t = bw_map(lo_t, s, P->mt, P->wt, x[4], &j4);
   const double q2tb = bw_map(lo_tb, s, P->mt, P->wt, x[5], &j5);
-  /* the Higgs pair */
+  /* the Higgs pair: m^2 = 2 E1 E2 (1 - cos theta_12) first, over the range the two jet
+   * windows allow, then f = E1 + E2 over the values its energies reach inside them */
   double lo1, hi1, lo2, hi2;
   jet_window(P, T, h1.E, &lo1, &hi1);
   jet_window(P, T, h2.E, &lo2, &hi2);
-  const double Lf = log((hi1 + hi2) / (lo1 + lo2));
-  const double f = (lo1 + lo2) * exp(x[6] * Lf), J6 = f * Lf;
   const double dx = h1.n[0] - h2.n[0], dy = h1.n[1] - h2.n[1], dz = h1.n[2] - h2.n[2];
   const double omc = 0.5 * (dx * dx + dy * dy + dz * dz); /* 1 - cos theta_12 */
   if (!(omc > 0.0)) return 0;
-  double J7;
-  const double m2max = 0.5 * f * f * omc;
-  double m2;
+  const double mlo = 2.0 * omc * lo1 * lo2, mhi = 2.0 * omc * hi1 * hi2;
+  double J7, m2;
   if (P->kind == 4) {
-    m2 = bw_map(0.0, m2max, P->mh, P->wh, x[7], &J7);
-  } else {
-    m2 = x[7] * m2max;
-    J7 = m2max;
+    m2 = bw_map(mlo, mhi, P->mh, P->wh, x[7], &J7);
+  } else { /* the extra pair's mass is not resonant: m^2 log-uniform over its window */
+    const double Lm = log(mhi / mlo);
+    m2 = mlo * exp(x[7] * Lm);
+    J7 = m2 * Lm;
   }
-  const double disc = f * f - 2.0 * m2 / omc;
+  const double K = m2 / (2.0 * omc); /* E1 E2 */
+  const double A = fmax(lo1, K / hi2), B = fmin(hi1, K / lo2); /* E1 inside both windows */
+  if (!(A < B)) return 0;
+  const double r = sqrt(K), fA = A + K / A, fB = B + K / B;
+  const double fmn = (A <= r && r <= B) ? 2.0 * r : fmin(fA, fB), fmx = fmax(fA, fB);
+  /* f = fmn + (fmx - fmn) v^2: the pre-map cancels the 1/sqrt(f - 2 sqrt(K)) end-point
+   * singularity of the (E1, E2) Jacobian when f can reach 2 sqrt(K) */
+  const double v = x[6];
+  const double f = fmn + (fmx - fmn) * v * v, J6 = 2.0 * v * (fmx - fmn);
+  const double disc = f * f - 4.0 * K;
   if (!(disc > 0.0)) return 0;
   const double sq = sqrt(disc);
   const double JH = 1.0 / (2.0 * omc * sq);

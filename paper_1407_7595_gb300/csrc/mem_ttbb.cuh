@@ -3,7 +3,8 @@
 //
 // Variables and assignments as for dilepton ttH (mem_tth.cuh; Sec. 4 applies the same
 // transformations to both processes) with the extra b bbar pair in the Higgs pair's
-// place; its mass is not resonant and is mapped uniformly over [0, f^2 (1 - cos)/2].
+// place; its mass is not resonant, so m^2 is mapped log-uniformly over the pair's
+// window [2 (1 - cos) lo1 lo2, 2 (1 - cos) hi1 hi2].
 // The pair's two jets enter |M|^2 as (b, bbar) and as (bbar, b).
 //
 // |M|^2: the Fierz-collapsed top row and antitop column of mem_ttbar.cuh around the
@@ -494,7 +495,6 @@ struct PhysTTBB_ {
       c.ok = c.ok && hi[q] > lo[q];
     }
     const double Lb = c.ok ? log(hi[0] / lo[0]) : 0.0, Lbb = c.ok ? log(hi[1] / lo[1]) : 0.0;
-    const double Lf = c.ok ? log((hi[2] + hi[3]) / (lo[2] + lo[3])) : 0.0;
     c.b_lo = (float)lo[0];
     c.Lb = (float)Lb;
     c.bb_lo = (float)lo[1];
@@ -503,8 +503,6 @@ struct PhysTTBB_ {
     c.h1_hi = (float)hi[2];
     c.h2_lo = (float)lo[3];
     c.h2_hi = (float)hi[3];
-    c.f_lo = (float)(lo[2] + lo[3]);
-    c.Lf = (float)Lf;
     float* dirs[4][5] = {{&c.bnx, &c.bny, &c.bnz, &c.blcp, &c.blcm},
                          {&c.bbnx, &c.bbny, &c.bbnz, &c.bblcp, &c.bblcm},
                          {&c.h1nx, &c.h1ny, &c.h1nz, &c.h1lcp, &c.h1lcm},
@@ -540,6 +538,7 @@ struct PhysTTBB_ {
     c.omc_bbl = (float)omc(nv[1], nv[5]);
     c.omc_h = (float)omc(nv[2], nv[3]);
     c.ok = c.ok && c.omc_h > 0.f;
+    th_pair_window(c, P, lo[2], hi[2], lo[3], hi[3], omc(nv[2], nv[3]));
     c.psi_w = (float)atan2((double)P.mwgw, (double)P.s - (double)P.mw2);
     c.psi_t = (float)atan2((double)P.mtgt, (double)P.s - (double)P.mt2);
     const double tw = T.jet_tail_w;
@@ -568,14 +567,11 @@ struct PhysTTBB_ {
     if (!(lo_t < P.s && lo_tb < P.s)) return 0.f;
     const BW tq = bw_map(lo_t, P.s - lo_t, P.mt2, P.mtgt, x[4], xc[4], c.psi_t);
     const BW tbq = bw_map(lo_tb, P.s - lo_tb, P.mt2, P.mtgt, x[5], xc[5], c.psi_t);
-    // the Higgs pair: f, m_H^2 -> (E1, E2), both orderings
-    const float f = c.f_lo * __expf(x[6] * c.Lf);
-    const float mmax = 0.5f * f * f * c.omc_h;
-    // the pair mass is not resonant: uniform over [0, mmax] (Jacobian mmax)
-    const float rel = xc[7];
-    if (!(rel > 0.f)) return 0.f;
-    const float sq = f * sqrtf(rel);
-    const float JH = 1.f / (2.f * c.omc_h * sq);
+    // the extra pair: its mass is not resonant, m^2 log-uniform over its window
+    // (Jacobian m^2 L_m), then f -> (E1, E2) as for the Higgs pair
+    const float m2p = c.m_lo * __expf(x[7] * c.Lm);
+    float e_big, e_small, Jf;
+    if (!th_pair(c, m2p, x[6], e_big, e_small, Jf)) return 0.f;
     // FP64 momenta in units of DL_UNIT
     const double iu = 1.0 / DL_UNIT, iu2 = iu * iu;
     const double eb = (double)Eb * iu, ebb = (double)Ebb * iu;
@@ -593,7 +589,7 @@ struct PhysTTBB_ {
     float total = 0.f;
 #pragma unroll 1
     for (int o = 0; o < 2; ++o) {
-      const float E1 = 0.5f * (o == 0 ? f + sq : f - sq), E2 = 0.5f * (o == 0 ? f - sq : f + sq);
+      const float E1 = o == 0 ? e_big : e_small, E2 = o == 0 ? e_small : e_big;
       if (!(E1 >= c.h1_lo && E1 <= c.h1_hi && E2 >= c.h2_lo && E2 <= c.h2_hi)) continue;
       const double e1 = (double)E1 * iu, e2 = (double)E2 * iu;
       const double mx = -(lp[1] + lm[1] + b[1] + bb[1] + e1 * c.h1nx + e2 * c.h2nx);
@@ -672,8 +668,8 @@ struct PhysTTBB_ {
     }
     if (total == 0.f) return 0.f;
     const float gb = dgauss_g(c, c.Ebm, Eb), gbb = dgauss_g(c, c.Ebbm, Ebb);
-    // the pair-mass map's Jacobian mmax, the f and (E1, E2) Jacobians f L_f and JH
-    return (c.cst * Eb * Ebb * gb * gbb * (wp.R * wm.R) * (tq.R * tbq.R) * mmax * (f * c.Lf) * JH *
+    // the pair-mass map's Jacobian m^2 L_m, the f map's and the (E1, E2) Jacobians
+    return (c.cst * Eb * Ebb * gb * gbb * (wp.R * wm.R) * (tq.R * tbq.R) * (m2p * c.Lm) * Jf *
            total) * TTH_OUT_SCALE;
   }
 };

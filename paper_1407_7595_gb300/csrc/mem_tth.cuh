@@ -3,11 +3,14 @@
 // (b l+ nu)(bbar mu- nubar)(b bbar).
 //
 // Variables (8): those of dilepton ttbar (mem_ttdl.cuh: E_b, E_bbar, q^2 of W+, W-,
-// t, tbar) and the Higgs pair's f = E1 + E2 (log-uniform over the sum of the two jet
-// windows) and m_H^2 = 2 E1 E2 (1 - cos theta_12) (Breit-Wigner map over
-// [0, f^2 (1 - cos theta_12) / 2], the largest mass the pair reaches at this f).
-// E1,2 = (f +- s) / 2 with s = f sqrt(1 - m_H^2 / max), both orderings, each with
-// 1 / (2 (1 - cos theta_12) s); an energy outside its jet window has no weight. The
+// t, tbar) and the Higgs pair's m_H^2 = 2 E1 E2 (1 - cos theta_12) (Breit-Wigner map
+// over [2 (1 - cos) lo1 lo2, 2 (1 - cos) hi1 hi2], the values the two jet windows
+// allow) and f = E1 + E2 over its image at that K = E1 E2: the larger energy runs over
+// [A, B] = [max(lo1, K/hi2), min(hi1, K/lo2)], f = E + K/E over [f_min, f_max], mapped
+// as f_min + (f_max - f_min) v^2 so that the 1 / sqrt(f^2 - 4K) of the inverse map is
+// cancelled. E1,2 = (f +- sqrt(f^2 - 4K)) / 2 in both orderings, each with
+// 1 / (2 (1 - cos theta_12) sqrt(f^2 - 4K)); at least one ordering lies inside both
+// windows by construction, one that leaves a window has no weight. The
 // missing pT is the visible imbalance including the Higgs pair, and the neutrinos
 // follow from Eq. "dilepsolv" with the FP64 solver of mem_ttdl.cuh. 12 jet
 // assignments: the (perm / 3)-th jet is the b, the (perm % 3)-th of the other three
@@ -30,7 +33,8 @@ namespace mem {
 struct THCache {
   float b_lo, Lb, bb_lo, Lbb;                   // b, bbar jet windows: lo, ln(hi / lo)
   float h1_lo, h1_hi, h2_lo, h2_hi;             // Higgs-pair jet windows
-  float f_lo, Lf;                               // f window: lo1 + lo2, ln((hi1 + hi2) / (lo1 + lo2))
+  float m_lo, m_rng, psi_h, Lm;                 // pair m^2 window [m_lo, m_lo + m_rng], atan2(m G, hi - m^2),
+                                                // ln(hi / lo)
   float bnx, bny, bnz, blcp, blcm;
   float bbnx, bbny, bbnz, bblcp, bblcm;
   float h1nx, h1ny, h1nz, h1lcp, h1lcm;
@@ -44,6 +48,43 @@ struct THCache {
   float cst;
   int ok;
 };
+
+// The pair's m^2 = 2 E1 E2 (1 - cos theta_12) window: the values the two jet windows
+// allow (FP64 set-up, once per item).
+__device__ inline void th_pair_window(THCache& c, const ProcConst& P, double lo1, double hi1,
+                                      double lo2, double hi2, double omc) {
+  const double mlo = 2.0 * omc * lo1 * lo2, mhi = 2.0 * omc * hi1 * hi2;
+  c.m_lo = (float)mlo;
+  c.m_rng = (float)(mhi - mlo);
+  c.psi_h = (float)atan2((double)P.mhgh, mhi - (double)P.mh2);
+  c.Lm = (float)log(mhi / mlo);
+}
+
+// Eq. "mhsolve" at a point: with K = E1 E2 = m^2 / (2 (1 - cos)) fixed, E1 runs over
+// [A, B] = [max(lo1, K / hi2), min(hi1, K / lo2)] and f = E1 + K / E1 over its image
+// [f_min, f_max] (f_min = 2 sqrt(K) when sqrt(K) is inside); f = f_min + (f_max - f_min) v^2,
+// whose square cancels the 1/sqrt(f - 2 sqrt(K)) end point of 1 / |d(f, m^2)/d(E1, E2)|.
+// Everything is written as distances from 2 sqrt(K) (no cancellation). Returns false
+// when the windows leave no room; else the larger and smaller energies and the
+// Jacobian (d f / d v) / (2 (1 - cos) |E1 - E2|).
+__device__ __forceinline__ bool th_pair(const THCache& c, float m2, float v, float& e_big,
+                                        float& e_small, float& jac) {
+  const float K = m2 * (0.5f / c.omc_h);
+  const float A = fmaxf(c.h1_lo, K / c.h2_hi), B = fminf(c.h1_hi, K / c.h2_lo);
+  if (!(A < B)) return false;
+  const float r = sqrtf(K);
+  const float dA = (A - r) * (A - r) / A, dB = (B - r) * (B - r) / B;   // f(A) - 2r, f(B) - 2r
+  const float dmn = (A <= r && r <= B) ? 0.f : fminf(dA, dB);
+  const float span = fmaxf(dA, dB) - dmn;
+  const float d = fmaf(span, v * v, dmn);                                // f - 2r
+  const float f = fmaf(2.f, r, d);
+  const float sq = sqrtf(d * (f + 2.f * r));                             // sqrt(f^2 - 4K)
+  if (!(sq > 0.f)) return false;
+  e_big = 0.5f * (f + sq);
+  e_small = K / e_big;
+  jac = 2.f * v * span / (2.f * c.omc_h * sq);
+  return true;
+}
 
 __device__ __forceinline__ Sp sp_scale(float s, const Sp& a) {
   return {s * a.l1, s * a.l2, s * a.r1, s * a.r2};
@@ -175,7 +216,6 @@ struct PhysTTH_ {
       c.ok = c.ok && hi[q] > lo[q];
     }
     const double Lb = c.ok ? log(hi[0] / lo[0]) : 0.0, Lbb = c.ok ? log(hi[1] / lo[1]) : 0.0;
-    const double Lf = c.ok ? log((hi[2] + hi[3]) / (lo[2] + lo[3])) : 0.0;
     c.b_lo = (float)lo[0];
     c.Lb = (float)Lb;
     c.bb_lo = (float)lo[1];
@@ -184,8 +224,6 @@ struct PhysTTH_ {
     c.h1_hi = (float)hi[2];
     c.h2_lo = (float)lo[3];
     c.h2_hi = (float)hi[3];
-    c.f_lo = (float)(lo[2] + lo[3]);
-    c.Lf = (float)Lf;
     float* dirs[4][5] = {{&c.bnx, &c.bny, &c.bnz, &c.blcp, &c.blcm},
                          {&c.bbnx, &c.bbny, &c.bbnz, &c.bblcp, &c.bblcm},
                          {&c.h1nx, &c.h1ny, &c.h1nz, &c.h1lcp, &c.h1lcm},
@@ -221,6 +259,7 @@ struct PhysTTH_ {
     c.omc_bbl = (float)omc(nv[1], nv[5]);
     c.omc_h = (float)omc(nv[2], nv[3]);
     c.ok = c.ok && c.omc_h > 0.f;
+    th_pair_window(c, P, lo[2], hi[2], lo[3], hi[3], omc(nv[2], nv[3]));
     c.psi_w = (float)atan2((double)P.mwgw, (double)P.s - (double)P.mw2);
     c.psi_t = (float)atan2((double)P.mtgt, (double)P.s - (double)P.mt2);
     const double tw = T.jet_tail_w;
@@ -250,14 +289,10 @@ struct PhysTTH_ {
     if (!(lo_t < P.s && lo_tb < P.s)) return 0.f;
     const BW tq = bw_map(lo_t, P.s - lo_t, P.mt2, P.mtgt, x[4], xc[4], c.psi_t);
     const BW tbq = bw_map(lo_tb, P.s - lo_tb, P.mt2, P.mtgt, x[5], xc[5], c.psi_t);
-    // the Higgs pair: f, m_H^2 -> (E1, E2), both orderings
-    const float f = c.f_lo * __expf(x[6] * c.Lf);
-    const float mmax = 0.5f * f * f * c.omc_h;
-    const BW hq = bw_map(0.f, mmax, P.mh2, P.mhgh, x[7], xc[7], atan2_ypos(P.mhgh, mmax - P.mh2));
-    const float rel = (mmax - hq.q2) / mmax;
-    if (!(rel > 0.f)) return 0.f;
-    const float sq = f * sqrtf(rel);
-    const float JH = 1.f / (2.f * c.omc_h * sq);
+    // the Higgs pair: m_H^2 (Breit-Wigner over its window), then f -> (E1, E2)
+    const BW hq = bw_map(c.m_lo, c.m_rng, P.mh2, P.mhgh, x[7], xc[7], c.psi_h);
+    float e_big, e_small, Jf;
+    if (!th_pair(c, hq.q2, x[6], e_big, e_small, Jf)) return 0.f;
     // FP64 momenta in units of DL_UNIT
     const double iu = 1.0 / DL_UNIT, iu2 = iu * iu;
     const double eb = (double)Eb * iu, ebb = (double)Ebb * iu;
@@ -275,7 +310,7 @@ struct PhysTTH_ {
     float total = 0.f;
 #pragma unroll 1
     for (int o = 0; o < 2; ++o) {
-      const float E1 = 0.5f * (o == 0 ? f + sq : f - sq), E2 = 0.5f * (o == 0 ? f - sq : f + sq);
+      const float E1 = o == 0 ? e_big : e_small, E2 = o == 0 ? e_small : e_big;
       if (!(E1 >= c.h1_lo && E1 <= c.h1_hi && E2 >= c.h2_lo && E2 <= c.h2_hi)) continue;
       const double e1 = (double)E1 * iu, e2 = (double)E2 * iu;
       const double mx = -(lp[1] + lm[1] + b[1] + bb[1] + e1 * c.h1nx + e2 * c.h2nx);
@@ -345,9 +380,9 @@ struct PhysTTH_ {
     }
     if (total == 0.f) return 0.f;
     const float gb = dgauss_g(c, c.Ebm, Eb), gbb = dgauss_g(c, c.Ebbm, Ebb);
-    // Higgs decay 2 m_H^2, the f and (E1, E2) Jacobians f L_f and JH
+    // Higgs decay 2 m_H^2, the f map's and the (E1, E2) Jacobians
     return (c.cst * Eb * Ebb * gb * gbb * (wp.R * wm.R) * (tq.R * tbq.R) * hq.R *
-           (2.f * hq.q2) * (f * c.Lf) * JH * total) * TTH_OUT_SCALE;
+           (2.f * hq.q2) * Jf * total) * TTH_OUT_SCALE;
   }
 };
 using PhysTTH = PhysTTH_<PDF_ANY>;

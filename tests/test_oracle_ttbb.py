@@ -134,7 +134,7 @@ def test_ttbb_full_chain_factorises(ora, synth, P, channel):
 
 # ---------------------------------------------------------------------------
 # The dilepton ttbb integrand (process kind 5): the variables of dilepton ttH with the
-# extra b bbar pair in the Higgs pair's place and its mass mapped uniformly.
+# extra b bbar pair in the Higgs pair's place and its mass mapped log-uniformly.
 # ---------------------------------------------------------------------------
 from test_oracle_tth import _phys8, _states, _find_point, _which_object  # noqa: E402
 
@@ -157,7 +157,7 @@ def test_ttbb_integrand_map(ora, synth, ttbb_setup):
     rng = np.random.default_rng(65)
     n_ok = 0
     for rec in recs:
-        for _ in range(40):
+        for _ in range(80):
             x = rng.uniform(0.05, 0.95, size=8)
             perm = int(rng.integers(0, 12))
             for k in _states(ora, P, T, rec, perm, x):
