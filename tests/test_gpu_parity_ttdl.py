@@ -12,25 +12,30 @@ virtualities from the Breit-Wigner maps and the b-jet energies from the log map,
 each with a few 1e-7 of relative rounding. The neutrino momenta move by the
 inverse of d(q^2)/d(nu) times that rounding, so the Jacobian 1/|det| and the
 decay invariants inherit the conditioning of the solution; the double-Gaussian
-jet TF amplifies an energy error by z/sigma ~ 10-50 as in semileptonic ttbar. On
-the host build of the same integrand (two samples of 8 events, ~900 nonzero
-points) 93-95 % of the points agree within 1e-5, 97-98 % within 3e-5, all within
-2e-2, and most of the worst points carry weights far below the mean -- but near
-the branch points, where two solutions merge and the Jacobian peaks, a point
-carrying a sizeable weight can be off by 1e-4 to 2e-2 (one of six 512-point
-batches sums to 3e-5 on both the host build and the GPU). Rule: at least 97 % of
-points within 3e-5, every point within 5e-2 relative or 1e-6 of the mean weight,
-and the sum over 512 points within 1e-4; the integral at a frozen grid within
-1e-4.
+jet TF amplifies an energy error by z/sigma ~ 10-50 as in semileptonic ttbar.
+Most points agree within 1e-5 (92-98 % per batch on the GPU) and 97 % within 3e-5.
+Next to a branch point, where two solutions merge and the Jacobian peaks, the
+weight is ill-conditioned and one point can carry a fifth of a batch; there the
+oracle measures the conditioning itself (s_i, the summed relative change of its
+weight under 2^-24 moves of the point's unit-cube coordinates, see
+test_gpu_parity.check_conditioned) and a point may differ by up to 100 s_i (the
+FP32 rounding of a Breit-Wigner output is worth a move of u up to m / (pi Gamma)
+~ 40 times larger), capped at 5e-2 (a missed or spurious solution is an O(1) change); on the GPU
+such points differ by 0.1-1.5 s_i.
+Rule: >= 97 % of the points within 3e-5, every point within its conditioning
+bound, the sum over the points within 3e-5 or well conditioned within 1e-5 (on
+the GPU: <= 1.3e-6); the frozen-grid integral equals the ratio of its point sums
+to 1e-7 and agrees within 1e-5 plus the bounds of its ill-conditioned points
+(on the GPU: 7.5e-7).
 """
 import numpy as np
 import pytest
 
-from test_gpu_parity import check_points
+from test_gpu_parity import check_conditioned, check_frozen_integral
 
 pytestmark = pytest.mark.gpu
 KIND = 3
-DL_RULE = dict(rel=3e-5, frac=0.97, cap=5e-2, floor=1e-6, sum_rel=1e-4)
+DL_RULE = dict(rel=3e-5, frac=0.97, sum_rel=1e-5)
 
 
 @pytest.fixture(scope="module")
@@ -61,7 +66,7 @@ def test_points_uniform_grid(env):
             w_gpu = integ.eval_points(e, perm, 42, 0, 512)
             w_ora = O.eval_points(P, T, recs[e], e, perm, 42, 0, 512)
             assert np.count_nonzero(w_ora) > 20     # the kinematic region is reached
-            check_points(w_gpu, w_ora, **DL_RULE)
+            check_conditioned(w_gpu, w_ora, (O, P, T, recs[e], e, perm, 42, 0, 6, None), **DL_RULE)
 
 
 def test_points_adapted_grid(env):
@@ -73,7 +78,7 @@ def test_points_adapted_grid(env):
     grid = r["grids"][perm]
     w_gpu = integ.eval_points(e, perm, 43, 10, 768, grid=grid)
     w_ora = O.eval_points(P, T, recs[e], e, perm, 43, 10, 768, grid=grid)
-    check_points(w_gpu, w_ora, **DL_RULE)
+    check_conditioned(w_gpu, w_ora, (O, P, T, recs[e], e, perm, 43, 10, 6, grid), **DL_RULE)
 
 
 def test_integral_frozen_grid(env):
@@ -81,7 +86,11 @@ def test_integral_frozen_grid(env):
     n = 2 * 4096 + 333   # two full sampling chunks and a ragged tail per item
     g = integ.integrate(n, seed=21, opts=abi.make_opts(n_adapt_iters=0))
     o = O.integrate(P, T, recs[:1], seed=21, n_points=n, n_adapt_iters=0)
-    assert g["prob"][0] == pytest.approx(o["prob"][0], rel=1e-4, abs=0)
+    parts = [check_conditioned(integ.eval_points(0, perm, 21, 0, n),
+                               O.eval_points(P, T, recs[0], 0, perm, 21, 0, n),
+                               (O, P, T, recs[0], 0, perm, 21, 0, 6, None), **DL_RULE)
+             for perm in (0, 1)]
+    check_frozen_integral(g["prob"][0], o["prob"][0], parts, DL_RULE["sum_rel"])
     assert g["err"][0] == pytest.approx(o["err"][0], rel=1e-3, abs=0)
     assert g["n_used"][0] == 2 * n and g["status"][0] == 0
 
