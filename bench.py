@@ -47,14 +47,15 @@ from paper_1407_7595_gb300 import synth  # noqa: E402
 # {fadd,fmul,ffma}_pred_on.sum over the evaluations of the launch; see profiles/),
 # re-counted whenever a kernel changes. MUFU, integer (Philox), conversion and
 # memory instructions are not counted as flops. k_adapt adds its shared-memory
-# histogram work to the integrand.
-FLOPS_MAIN_PER_EVAL = {synth.PROC_DY: 157.0, synth.PROC_W: 345.7, synth.PROC_TTBAR: 2834.9}
-FLOPS_ADAPT_PER_EVAL = {synth.PROC_TTBAR: 2817.6}
-# FP64 flops (DADD, DMUL = 1; DFMA = 2) per evaluation of the dilepton kernels (the
-# neutrino solution runs in FP64 and bounds them), ncu instruction counters.
-FP64_FLOPS_PER_EVAL = {synth.PROC_TTBAR_DILEP: 1002.6, synth.PROC_TTH_DILEP: 1223.3}
-FP64_FLOPS_ADAPT_PER_EVAL = {synth.PROC_TTH_DILEP: 942.0}
-FP64_KINDS = (synth.PROC_TTBAR_DILEP, synth.PROC_TTH_DILEP, synth.PROC_TTBB_DILEP)
+# histogram work to the integrand. The dilepton kinds solve for the neutrinos in
+# double-float on the FP32 pipe: their counts include that arithmetic (~20 FP32
+# operations per double-float sum), and they average over the points that exit
+# before the solver.
+FLOPS_MAIN_PER_EVAL = {synth.PROC_DY: 157.0, synth.PROC_W: 345.7, synth.PROC_TTBAR: 2834.9,
+                       synth.PROC_TTBAR_DILEP: 11390.0, synth.PROC_TTH_DILEP: 19896.0,
+                       synth.PROC_TTBB_DILEP: 944900.0}
+FLOPS_ADAPT_PER_EVAL = {synth.PROC_TTBAR: 2817.6, synth.PROC_TTBAR_DILEP: 9892.0,
+                        synth.PROC_TTH_DILEP: 17000.0, synth.PROC_TTBB_DILEP: 703900.0}
 FP32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 FP32 lanes
 # DRAM bytes (read + write) per launch unit from one ncu capture of the current
 # kernels: k_main reads each item's grid and constants once (other CTAs of the item
@@ -78,7 +79,7 @@ WORKLOAD_NAMES = {
     "ttbar": "semileptonic ttbar (gg + qqbar, spin-correlated helicity amplitudes), 7-dim "
              "integral x 24 jet permutations, 4096 events x 2^22 evaluations/event",
     "ttdl": "dilepton ttbar (b l+ nu bbar mu- nubar; both neutrinos from the four "
-            "virtualities, up to 4 solutions, FP64 solve), 6-dim integral x 2 b-jet "
+            "virtualities, up to 4 solutions, double-float solve), 6-dim integral x 2 b-jet "
             "assignments, 1024 events x 2^18 evaluations/event",
     "tth": "dilepton ttH, H -> b bbar (Eq. integrand with Eq. mhsolve): 8-dim integral x 12 "
            "jet assignments, 256 events x 12 x 2^16 evaluations/event",
@@ -376,14 +377,11 @@ def measure_peaks():
     return r
 
 
-def roofline_entry(kernel, kind, evals, ms, peaks, flops_fp32, flops_fp64, sms, clocks):
-    """Achieved flops of one kernel phase against the measured ALU peak of its pipe."""
+def roofline_entry(kernel, kind, evals, ms, peaks, flops_fp32, sms, clocks):
+    """Achieved FP32 flops of one kernel phase against the measured FP32 peak."""
     max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
     derived = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
-    if kind in FP64_KINDS:
-        fpe, peak, pipe = flops_fp64.get(kind), peaks.get("fp64_tflops"), "FP64 DFMA"
-    else:
-        fpe, peak, pipe = flops_fp32.get(kind), peaks.get("fp32_tflops"), "FP32 FFMA"
+    fpe, peak, pipe = flops_fp32.get(kind), peaks.get("fp32_tflops"), "FP32 FFMA"
     achieved = fpe * evals / (ms * 1e-3) / 1e12 if fpe else None
     return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak if (achieved and peak) else None,
@@ -496,10 +494,10 @@ def integrand_leg(abi, torch, name, kind, n_ev, n_pts, seed, steps, warmup, args
         t_main, t_adapt = statistics.mean(main_ms), statistics.mean(adapt_ms)
         t_step = statistics.mean(step_ms)
         r_main = roofline_entry("k_main (frozen-grid sampling)", kind, n_ev * n_perm * n_main,
-                                t_main, peaks, FLOPS_MAIN_PER_EVAL, FP64_FLOPS_PER_EVAL, sms, clk)
+                                t_main, peaks, FLOPS_MAIN_PER_EVAL, sms, clk)
         r_adapt = roofline_entry("k_adapt (VEGAS adaptation + refinement)", kind,
                                  n_ev * n_perm * 5 * n_adapt, t_adapt, peaks,
-                                 FLOPS_ADAPT_PER_EVAL, FP64_FLOPS_ADAPT_PER_EVAL, sms, clk)
+                                 FLOPS_ADAPT_PER_EVAL, sms, clk)
         r_main["share_of_step"] = t_main / t_step
         r_adapt["share_of_step"] = t_adapt / t_step
         dpi = DRAM_BYTES_PER_ITEM_MAIN.get(kind)

@@ -312,7 +312,7 @@ mem_status mem_ttbb_colour_matrices(float* kgg, float* kqq);
  * may not allocate later makes one small call per process kind it will use
  * (e.g. 1 event, 16 points) at start-up, before it reserves its memory pool
  * and before any stream capture; later calls allocate nothing. Kinds 0-3 need
- * at most 752 bytes of per-thread stack, inside the default 1024-byte limit,
+ * at most 928 bytes of per-thread stack, inside the default 1024-byte limit,
  * so no launch grows the context's local memory; kinds 4 and 5 are rejected.
  * All calls share the array: calls that overlap on the GPU (other streams,
  * other host threads) race on it and must be serialised by the caller.
@@ -342,8 +342,9 @@ typedef struct mem_flow mem_flow;
  * massless), MET x, y, q^2 of W+, W-, t, tbar (GeV^2). Writes nsol[n] (0..4), nu
  * [n][4][8] (per solution nu then nubar, GeV; unused slots 0) and jac [n][4]
  * (1 / |det d(q^2_W+, q^2_t, q^2_W-, q^2_tbar)/d(nu_x, nu_y, nu_z, nubar_z)|, GeV^-4):
- * the same FP64 solver stages, checks and de-duplication as the integrand, one
- * GPU thread per system. Synchronous. Errors: MEM_ERR_INVALID_ARG (NULL, n < 1
+ * the same double-float solver stages, checks and de-duplication as the
+ * integrand (the inputs rounded to double-float, ~48 bits), one GPU thread per
+ * system. Synchronous. Errors: MEM_ERR_INVALID_ARG (NULL, n < 1
  * or n > 2^24), MEM_ERR_CUDA. */
 mem_status mem_dilep_solve(const double* in, int64_t n, int32_t* nsol, double* nu, double* jac);
 

@@ -13,7 +13,10 @@ constexpr int MINB_TT = 2;       // adaptation and round kernels: <= 128 registe
 constexpr int MINB_TT_MAIN = 3;  // frozen-grid kernel: <= 80 registers (20 bytes of spill), 24 warps/SM
 
 constexpr int PPT_DL = 16;       // frozen-grid points per thread (dilepton ttbar): 4,096 per CTA
-constexpr int MINB_DL = 1;       // adaptation kernel: one CTA of 256 threads per SM
-constexpr int MINB_DL_MAIN = 2;  // frozen-grid kernel: <= 128 registers
+constexpr int MINB_DL = 3;       // adaptation kernel: 3 CTAs of 256 threads per SM (<= 80 registers)
+constexpr int MINB_DL_MAIN = 4;  // frozen-grid kernel: 4 CTAs per SM (<= 64 registers): the
+                                 // double-float solver is latency-bound, occupancy pays for the spills
+constexpr int MINB_TH = 1;       // dilepton ttH and ttbb adaptation kernels: one CTA per SM
+constexpr int MINB_TH_MAIN = 2;  // dilepton ttH and ttbb frozen-grid kernels: <= 128 registers
 
 }  // namespace mem

@@ -1,5 +1,5 @@
 // Kernel instantiations for the dilepton ttbar process. One build serves the
-// parametric and the tabulated PDFs (chosen per call): the FP64 neutrino solution
+// parametric and the tabulated PDFs (chosen per call): the neutrino solution
 // dominates this integrand, not the PDF lookup.
 #include <string>
 
@@ -31,48 +31,37 @@ namespace {
 
 // One thread per system: the integrand's neutrino solution (dl_system_met, the
 // real roots of the resultant, dl_point with its checks and de-duplication) on
-// FP64 inputs; solutions in GeV with their Jacobians, as the integrand uses them.
+// FP64 inputs rounded to double-float; solutions in GeV with their Jacobians, as
+// the integrand uses them.
 __global__ void k_dilep_solve(const double* __restrict__ in, int64_t n, int32_t* __restrict__ nsol,
                               double* __restrict__ out, double* __restrict__ jac) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double* q = in + i * 22;
-  const double iu = 1.0 / DL_UNIT, iu2 = iu * iu;
-  double b[4], bb[4], lp[4], lm[4];
-  for (int k = 0; k < 4; ++k) {
-    b[k] = q[k] * iu;
-    bb[k] = q[4 + k] * iu;
-    lp[k] = q[8 + k] * iu;
-    lm[k] = q[12 + k] * iu;
-  }
+  const double u = (double)DL_UNIT, u2 = u * u;
+  const DLMom b = dl_mom64(q), bb = dl_mom64(q + 4), lp = dl_mom64(q + 8), lm = dl_mom64(q + 12);
   DLSystem S;
-  double xr[4];
-  const int nr = dl_system_met(b, bb, lp, lm, q[16] * iu, q[17] * iu, q[18] * iu2, q[19] * iu2,
-                               q[20] * iu2, q[21] * iu2, S, xr);
-  double seen[4][2];
+  df xr[4];
+  const int nr = dl_system_met(b, bb, lp, lm, df_from_double(q[16] / u), df_from_double(q[17] / u),
+                               df_from_double(q[18] / u2), df_from_double(q[19] / u2),
+                               df_from_double(q[20] / u2), df_from_double(q[21] / u2), S, xr);
+  df seen[4][2];
   int ns = 0;
   for (int r = 0; r < nr; ++r) {
-    double px, py;
+    df px, py;
     if (!dl_point(S, xr[r], px, py)) continue;
     bool dup = false;
-    for (int k = 0; k < ns; ++k)
-      dup = dup || fabs(seen[k][0] - px) + fabs(seen[k][1] - py) < 1e-9 * (1.0 + fabs(px) + fabs(py));
+    for (int k = 0; k < ns; ++k) dup = dup || dl_same(seen[k][0], seen[k][1], px, py);
     if (dup) continue;
     seen[ns][0] = px;
     seen[ns][1] = py;
-    double nu[4], nub[4];
-    nu[1] = px;
-    nu[2] = py;
-    nu[3] = S.n1.z[0] + S.n1.z[1] * px + S.n1.z[2] * py;
-    nu[0] = sqrt(px * px + py * py + nu[3] * nu[3]);
-    nub[1] = S.mx - px;
-    nub[2] = S.my - py;
-    nub[3] = S.n2.z[0] + S.n2.z[1] * nub[1] + S.n2.z[2] * nub[2];
-    nub[0] = sqrt(nub[1] * nub[1] + nub[2] * nub[2] + nub[3] * nub[3]);
-    jac[i * 4 + ns] = dl_jacobian(b, bb, lp, lm, nu, nub);
+    DLMom nu, nub;
+    dl_neutrinos(S, px, py, nu, nub);
+    const double det = to_double(dl_det(b, bb, lp, lm, nu, nub));
+    jac[i * 4 + ns] = det > 0.0 ? 1.0 / (det * u2 * u2) : 0.0;
     for (int k = 0; k < 4; ++k) {
-      out[(i * 4 + ns) * 8 + k] = nu[k] * DL_UNIT;
-      out[(i * 4 + ns) * 8 + 4 + k] = nub[k] * DL_UNIT;
+      out[(i * 4 + ns) * 8 + k] = to_double(nu.v[k]) * u;
+      out[(i * 4 + ns) * 8 + 4 + k] = to_double(nub.v[k]) * u;
     }
     ++ns;
   }

@@ -20,7 +20,7 @@ cudaError_t prepare_tth() {
 cudaError_t launch_integrate_tth(const IntegrateArgs& a, cudaStream_t st) {
   cudaError_t e = prepare_tth();
   if (e != cudaSuccess) return e;
-  return run_integrate<PhysTTH, PPT_DL, MINB_DL, MINB_DL_MAIN>(a, st);
+  return run_integrate<PhysTTH, PPT_DL, MINB_TH, MINB_TH_MAIN>(a, st);
 }
 cudaError_t launch_eval_tth(const EvalArgs& a, cudaStream_t st) {
   cudaError_t e = prepare_tth();
@@ -36,6 +36,6 @@ size_t cache_size_tth() { return cache_bytes<PhysTTH>(); }
 namespace mem {
 // adaptive rounds; prepare_tth() must have run on this device (outside any capture)
 cudaError_t launch_batch_tth(const BatchArgs& b, cudaStream_t st) {
-  return run_batch<PhysTTH, MINB_DL>(b, st);
+  return run_batch<PhysTTH, MINB_TH>(b, st);
 }
 }  // namespace mem

@@ -572,14 +572,12 @@ struct PhysTTBB_ {
     const float m2p = c.m_lo * __expf(x[7] * c.Lm);
     float e_big, e_small, Jf;
     if (!th_pair(c, m2p, x[6], e_big, e_small, Jf)) return 0.f;
-    // FP64 momenta in units of DL_UNIT
-    const double iu = 1.0 / DL_UNIT, iu2 = iu * iu;
-    const double eb = (double)Eb * iu, ebb = (double)Ebb * iu;
-    const double elp = (double)c.Elp * iu, elm = (double)c.Elm * iu;
-    const double b[4] = {eb, eb * c.bnx, eb * c.bny, eb * c.bnz};
-    const double bb[4] = {ebb, ebb * c.bbnx, ebb * c.bbny, ebb * c.bbnz};
-    const double lp[4] = {elp, elp * c.lpnx, elp * c.lpny, elp * c.lpnz};
-    const double lm[4] = {elm, elm * c.lmnx, elm * c.lmny, elm * c.lmnz};
+    // double-float momenta and virtualities in units of DL_UNIT (exact from FP32)
+    const DLMom b = dl_mom(Eb, c.bnx, c.bny, c.bnz), bb = dl_mom(Ebb, c.bbnx, c.bbny, c.bbnz);
+    const DLMom lp = dl_mom(c.Elp, c.lpnx, c.lpny, c.lpnz), lm = dl_mom(c.Elm, c.lmnx, c.lmny, c.lmnz);
+    constexpr float iu2 = DL_IU * DL_IU;
+    const df vx = ((lp.v[1] + lm.v[1]) + b.v[1]) + bb.v[1];   // visible pT of the four objects
+    const df vy = ((lp.v[2] + lm.v[2]) + b.v[2]) + bb.v[2];
     const float m = sqrtf(P.mt2);
     LCv Lb, Lbb, Llp, Llm;
     Lb.pp = Eb * c.blcp; Lb.pm = Eb * c.blcm; Lb.pt = C(Eb * c.bnx, Eb * c.bny);
@@ -591,50 +589,35 @@ struct PhysTTBB_ {
     for (int o = 0; o < 2; ++o) {
       const float E1 = o == 0 ? e_big : e_small, E2 = o == 0 ? e_small : e_big;
       if (!(E1 >= c.h1_lo && E1 <= c.h1_hi && E2 >= c.h2_lo && E2 <= c.h2_hi)) continue;
-      const double e1 = (double)E1 * iu, e2 = (double)E2 * iu;
-      const double mx = -(lp[1] + lm[1] + b[1] + bb[1] + e1 * c.h1nx + e2 * c.h2nx);
-      const double my = -(lp[2] + lm[2] + b[2] + bb[2] + e1 * c.h1ny + e2 * c.h2ny);
+      const float e1 = E1 * DL_IU, e2 = E2 * DL_IU;
+      const df mx = -((vx + two_prod(e1, c.h1nx)) + two_prod(e2, c.h2nx));
+      const df my = -((vy + two_prod(e1, c.h1ny)) + two_prod(e2, c.h2ny));
       DLSystem S;
-      double xr[4];
-      const int nr = dl_system_met(b, bb, lp, lm, mx, my, (double)wp.q2 * iu2, (double)wm.q2 * iu2,
-                                   (double)tq.q2 * iu2, (double)tbq.q2 * iu2, S, xr);
+      df xr[4];
+      const int nr = dl_system_met(b, bb, lp, lm, mx, my, df(wp.q2 * iu2), df(wm.q2 * iu2),
+                                   df(tq.q2 * iu2), df(tbq.q2 * iu2), S, xr);
       if (nr == 0) continue;
       LCv Lh;
       Lh.pp = fmaf(E1, c.h1lcp, E2 * c.h2lcp);
       Lh.pm = fmaf(E1, c.h1lcm, E2 * c.h2lcm);
       Lh.pt = C(fmaf(E1, c.h1nx, E2 * c.h2nx), fmaf(E1, c.h1ny, E2 * c.h2ny));
-      double seen[4][2];
+      df seen[4][2];
       int ns = 0;
       float acc = 0.f;
 #pragma unroll 1
       for (int r = 0; r < nr; ++r) {
-        double px, py;
+        df px, py;
         if (!dl_point(S, xr[r], px, py)) continue;
         bool dup = false;
-        for (int k = 0; k < ns; ++k)
-          dup = dup || fabs(seen[k][0] - px) + fabs(seen[k][1] - py) < 1e-9 * (1.0 + fabs(px) + fabs(py));
+        for (int k = 0; k < ns; ++k) dup = dup || dl_same(seen[k][0], seen[k][1], px, py);
         if (dup) continue;
         seen[ns][0] = px;
         seen[ns][1] = py;
         ++ns;
-        double nu[4], nub[4];
-        nu[1] = px;
-        nu[2] = py;
-        nu[3] = S.n1.z[0] + S.n1.z[1] * px + S.n1.z[2] * py;
-        nu[0] = sqrt(px * px + py * py + nu[3] * nu[3]);
-        nub[1] = S.mx - px;
-        nub[2] = S.my - py;
-        nub[3] = S.n2.z[0] + S.n2.z[1] * nub[1] + S.n2.z[2] * nub[2];
-        nub[0] = sqrt(nub[1] * nub[1] + nub[2] * nub[2] + nub[3] * nub[3]);
-        const double jnu = dl_jacobian(b, bb, lp, lm, nu, nub);
-        const double pbn = (b[0] * nu[0] - b[1] * nu[1] - b[2] * nu[2] - b[3] * nu[3]) * DL_UNIT * DL_UNIT;
-        const double pbbn = (bb[0] * nub[0] - bb[1] * nub[1] - bb[2] * nub[2] - bb[3] * nub[3]) * DL_UNIT * DL_UNIT;
-        double nug[4], nubg[4];
-        for (int k = 0; k < 4; ++k) {
-          nug[k] = nu[k] * DL_UNIT;
-          nubg[k] = nub[k] * DL_UNIT;
-        }
-        const LCv Ln = dl_lc(nug), Lnb = dl_lc(nubg);
+        DLMom nu, nub;
+        dl_neutrinos(S, px, py, nu, nub);
+        const float dec = dl_decay_factor(b, bb, nu, nub, dl_det(b, bb, lp, lm, nu, nub));
+        const LCv Ln = dl_lc(nu), Lnb = dl_lc(nub);
         LCv tp, tm;
         tp.pp = Lb.pp + Llp.pp + Ln.pp;
         tp.pm = Lb.pm + Llp.pm + Ln.pm;
@@ -661,8 +644,7 @@ struct PhysTTBB_ {
           init += (f1.g * f2.g) * amp.gg * (1.f / 256.f) +
                   2.f * (f1.q * f2.qb * amp.qq12 + f1.qb * f2.q * amp.qq21) * (1.f / 36.f);
         }
-        const float dec = (float)(pbn * pbbn * jnu / (nug[0] * nubg[0]) * TTH_DEC_SCALE);
-        acc += init * (4.f / shat) * dec;
+        acc += init * (4.f / shat) * (dec * (float)TTH_DEC_SCALE);
       }
       if (acc != 0.f) total += acc * dgauss_g(c, c.E1m, E1) * dgauss_g(c, c.E2m, E2);
     }
