@@ -225,7 +225,7 @@ cudaError_t prepare_ttbb() {
 cudaError_t launch_integrate_ttbb(const IntegrateArgs& a, cudaStream_t st) {
   cudaError_t e = prepare_ttbb();
   if (e != cudaSuccess) return e;
-  return run_integrate<PhysTTBB, PPT_DL, MINB_TH, MINB_TH_MAIN>(a, st);
+  return run_integrate<PhysTTBB, PPT_DL, MINB_BB, MINB_BB_MAIN>(a, st);
 }
 cudaError_t launch_eval_ttbb(const EvalArgs& a, cudaStream_t st) {
   cudaError_t e = prepare_ttbb();
@@ -241,7 +241,7 @@ size_t cache_size_ttbb() { return cache_bytes<PhysTTBB>(); }
 namespace mem {
 // adaptive rounds; prepare_ttbb() must have run on this device (outside any capture)
 cudaError_t launch_batch_ttbb(const BatchArgs& b, cudaStream_t st) {
-  return run_batch<PhysTTBB, MINB_TH>(b, st);
+  return run_batch<PhysTTBB, MINB_BB>(b, st);
 }
 }  // namespace mem
 
