@@ -175,17 +175,29 @@ static __device__ __noinline__ df dl_bracket_root(const df* c, int deg, df a, df
   return x;
 }
 
-// sum_k |c_k| |x|^k: the scale of the rounding in p(x)
-__device__ __forceinline__ float dl_poly_mag(const df* c, int deg, float x) {
-  float mag = 0.f, pw = 1.f;
-  const float ax = fabsf(x);
-  for (int k = 0; k <= deg; ++k, pw *= ax) mag = fmaf(fabsf(c[k].hi), pw, mag);
-  return mag;
-}
+// Relative step at which the double-float Newton iterations stop. They divide by an
+// FP32 reciprocal of the derivative, so near a simple root each step contracts the
+// error by ~1e-7: after a step of 1e-11 the error left is ~1e-18, below double-float
+// resolution. (Next to a double root, where the contraction is weaker, the roots are
+// ill-conditioned at the 1e-7 level of the integrand's FP32 inputs anyway.)
+constexpr float DL_DF_TOL = 1e-11f;
 
-// Relative step at which a double-float Newton iteration has converged (~10 times
-// the precision of one operation).
-constexpr float DL_DF_TOL = 3e-14f;
+// p at a bracket end x, where only its sign matters unless it is small: the FP32
+// monic copy cf (p = lead cf) decides when |cf(x)| exceeds 1e-5 of its terms (the
+// copy's rounding and the FP32 evaluation stay below ~3e-7 of them); otherwise the
+// double-float polynomial is evaluated. mag = sum_k |c_k| |x|^k.
+__device__ __forceinline__ df dl_end_value(const df* c, const float* cf, int deg, float lead, df x,
+                                           float& mag) {
+  const float ax = fabsf(x.hi);
+  float m = 0.f, pw = 1.f;
+  for (int k = 0; k <= deg; ++k, pw *= ax) m = fmaf(fabsf(cf[k]), pw, m);
+  mag = m * fabsf(lead);
+  float dp32;
+  const float p32 = dl_horner(cf, deg, x.hi, dp32);
+  if (fabsf(p32) > 1e-5f * m) return df(p32 * lead);
+  df dp;
+  return dl_horner(c, deg, x, dp);
+}
 
 // Real roots (ascending) of c[0] + c[1] x + ... + c[deg] x^deg, 1 <= deg <= 4,
 // c[deg] != 0. The critical points -- the real roots of the derivative chain
@@ -194,8 +206,10 @@ constexpr float DL_DF_TOL = 3e-14f;
 // hold a root is decided by the signs of the double-float polynomial at their ends (at
 // a critical point the polynomial is flat, so an FP32-accurate location gives the
 // exact sign, except next to a double root: see below); each root is located in FP32
-// and finished by double-float Newton steps inside its bracket. A critical point where
-// the polynomial vanishes to rounding is a double root and is kept once.
+// and finished by double-float Newton steps inside its bracket. Where the polynomial is
+// far from zero at a bracket end, the FP32 copy gives its sign (dl_end_value). A
+// critical point where the polynomial vanishes to rounding is a double root and is
+// kept once.
 static __device__ __noinline__ int dl_real_roots(const df* c, int deg, df* roots) {
   const float lead = c[deg].hi;
   const float ilead = 1.f / lead;
@@ -256,17 +270,17 @@ static __device__ __noinline__ int dl_real_roots(const df* c, int deg, df* roots
   // level 0: double-float signs at the bracket ends, FP32 location, double-float finish
   int n = 0;
   const df B(bound);
-  df a = -B, dpa;
-  df fa = dl_horner(c, deg, a, dpa);
+  df a = -B;
+  float mag_a;
+  df fa = dl_end_value(c, cf, deg, lead, a, mag_a);
   // derivative coefficients for refining critical points next to a double root
   df c1[4];
   for (int k = 0; k < deg; ++k) c1[k] = c[k + 1] * (float)(k + 1);
   for (int i = 0; i <= ncrit; ++i) {
     df b = i < ncrit ? df(fminf(fmaxf(crit[i], -bound), bound)) : B;
     df dpb;
-    df fb = dl_horner(c, deg, b, dpb);
-    float mag = 0.f;
-    if (i < ncrit) mag = dl_poly_mag(c, deg, b.hi);
+    float mag;
+    df fb = dl_end_value(c, cf, deg, lead, b, mag);
     if (i < ncrit && deg >= 2 && fabsf(fb.hi) <= 1e-6f * mag) {
       // Where the polynomial is small at a critical point, two roots may lie closer
       // together than the FP32 critical point's error, which would put both on one
