@@ -1,5 +1,7 @@
 // Kernel instantiations for the dilepton ttbb process (fixed-budget integration and
 // point evaluation), and the colour matrices of its production terms.
+#include <algorithm>
+#include <cmath>
 #include <complex>
 #include <mutex>
 #include <vector>
@@ -161,7 +163,7 @@ cd qq_colour(const SU3& S, int n, int iq, int jq, int i, int j, int k, int l) {
   return s;
 }
 
-std::vector<float2> colour_matrix(bool gg) {
+std::vector<cd> colour_matrix_d(bool gg) {
   static const SU3 S;
   const int N = gg ? TTBB_NGG : TTBB_NQQ, ext = gg ? 64 : 9;
   std::vector<cd> Cm((size_t)N * ext * 81);
@@ -175,21 +177,79 @@ std::vector<float2> colour_matrix(bool gg) {
               for (int l = 0; l < 3; ++l)
                 Cm[q++] = gg ? gg_colour(S, n, a, b, i, j, k, l) : qq_colour(S, n, a, b, i, j, k, l);
   }
-  std::vector<float2> K((size_t)N * N);
+  std::vector<cd> K((size_t)N * N);
   for (int n = 0; n < N; ++n)
     for (int m = 0; m < N; ++m) {
       cd s = 0.0;
       for (int q = 0; q < ext * 81; ++q) s += std::conj(Cm[(size_t)n * ext * 81 + q]) * Cm[(size_t)m * ext * 81 + q];
-      K[(size_t)n * N + m] = make_float2((float)s.real(), (float)s.imag());
+      K[(size_t)n * N + m] = s;
     }
   return K;
 }
 
-// The colour matrices in constant memory: uploaded once per device (constant
+std::vector<float2> colour_matrix(bool gg) {
+  const std::vector<cd> K = colour_matrix_d(gg);
+  std::vector<float2> r(K.size());
+  for (size_t q = 0; q < K.size(); ++q) r[q] = make_float2((float)K[q].real(), (float)K[q].imag());
+  return r;
+}
+
+// K = sum_k u_k u_k^dagger by pivoted Cholesky (K is Hermitian positive semidefinite,
+// a Gram matrix): each step takes the largest remaining diagonal element as pivot p,
+// u = K[:, p] / sqrt(K[p][p]), and removes u u^dagger; it stops when every remaining
+// diagonal element is below 1e-12 of the largest initial one (the numerical rank).
+// Returns the rows conj(u_k) (rank x N) and the rank; rank -1 if the factors do not
+// reproduce K to 1e-9 of its largest diagonal element.
+struct ColourFactors {
+  std::vector<float2> w;
+  int rank;
+};
+
+ColourFactors colour_factors(bool gg) {
+  const std::vector<cd> K = colour_matrix_d(gg);
+  const int N = gg ? TTBB_NGG : TTBB_NQQ;
+  std::vector<cd> A(K);
+  double dmax = 0.0;
+  for (int n = 0; n < N; ++n) dmax = std::max(dmax, A[(size_t)n * N + n].real());
+  std::vector<std::vector<cd>> us;
+  for (int k = 0; k < N; ++k) {
+    int p = -1;
+    double best = 1e-12 * dmax;
+    for (int n = 0; n < N; ++n)
+      if (A[(size_t)n * N + n].real() > best) {
+        best = A[(size_t)n * N + n].real();
+        p = n;
+      }
+    if (p < 0) break;
+    const double sq = std::sqrt(best);
+    std::vector<cd> u(N);
+    for (int n = 0; n < N; ++n) u[n] = A[(size_t)n * N + p] / sq;
+    for (int n = 0; n < N; ++n)
+      for (int m = 0; m < N; ++m) A[(size_t)n * N + m] -= u[n] * std::conj(u[m]);
+    us.push_back(u);
+  }
+  ColourFactors r;
+  r.rank = (int)us.size();
+  double err = 0.0;
+  for (int n = 0; n < N; ++n)
+    for (int m = 0; m < N; ++m) {
+      cd s = 0.0;
+      for (const auto& u : us) s += u[n] * std::conj(u[m]);
+      err = std::max(err, std::abs(s - K[(size_t)n * N + m]));
+    }
+  if (!(err <= 1e-9 * dmax)) r.rank = -1;
+  r.w.assign((size_t)N * N, make_float2(0.f, 0.f));
+  for (size_t k = 0; k < us.size(); ++k)
+    for (int m = 0; m < N; ++m) r.w[k * N + m] = make_float2((float)us[k][m].real(), (float)-us[k][m].imag());
+  return r;
+}
+
+// The colour matrices' factors in constant memory: uploaded once per device (constant
 // memory belongs to each device's context), at the first call that launches a
 // ttbb kernel on it, before any stream capture.
 cudaError_t ttbb_colour_upload() {
-  static const std::vector<float2> kgg = colour_matrix(true), kqq = colour_matrix(false);
+  static const ColourFactors ugg = colour_factors(true), uqq = colour_factors(false);
+  if (ugg.rank < 1 || uqq.rank < 1) return cudaErrorInvalidValue;
   static std::mutex lock;
   static bool done[64] = {};
   int dev = 0;
@@ -198,8 +258,10 @@ cudaError_t ttbb_colour_upload() {
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> g(lock);
   if (done[dev]) return cudaSuccess;
-  e = cudaMemcpyToSymbol(c_ttbb_kgg, kgg.data(), kgg.size() * sizeof(float2));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ttbb_kqq, kqq.data(), kqq.size() * sizeof(float2));
+  const int ranks[2] = {ugg.rank, uqq.rank};
+  e = cudaMemcpyToSymbol(c_ttbb_ugg, ugg.w.data(), ugg.w.size() * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ttbb_uqq, uqq.w.data(), uqq.w.size() * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ttbb_rank, ranks, sizeof(ranks));
   if (e == cudaSuccess) done[dev] = true;
   return e;
 }

@@ -32,9 +32,12 @@ namespace mem {
 
 constexpr int TTBB_NGG = 38;
 constexpr int TTBB_NQQ = 7;
-// Colour matrices K_nm = sum over external colours of conj(C_n) C_m (row major).
-__constant__ float2 c_ttbb_kgg[TTBB_NGG * TTBB_NGG];
-__constant__ float2 c_ttbb_kqq[TTBB_NQQ * TTBB_NQQ];
+// Colour matrices K_nm = sum over external colours of conj(C_n) C_m, factorised on the
+// host as K = sum_k u_k u_k^dagger (pivoted Cholesky: K is a Gram matrix, of rank 11 for
+// g g and 4 for q qbar): rows conj(u_k), rank x N, row major, and the ranks.
+__constant__ float2 c_ttbb_ugg[TTBB_NGG * TTBB_NGG];
+__constant__ float2 c_ttbb_uqq[TTBB_NQQ * TTBB_NQQ];
+__constant__ int c_ttbb_rank[2];
 
 struct CV { cf p, m, t, tb; };
 
@@ -115,18 +118,19 @@ __device__ __forceinline__ CV v3(float g, const CV& A, const CV& kA, const CV& B
   return cv_scale(C(g), r);
 }
 
-// |row L/ col|-style quadratic form with a colour matrix in constant memory
+// The colour-summed square L^dagger K L = sum_k |conj(u_k) . L|^2 from the factor rows
+// W (rank x N) in constant memory: rank x N complex products instead of N x N.
 template <int N>
-__device__ __forceinline__ float colour_quad(const cf* L, const float2* K) {
+__device__ __forceinline__ float colour_quad(const cf* L, const float2* W, int rank) {
   float s = 0.f;
 #pragma unroll 1
-  for (int n = 0; n < N; ++n) {
+  for (int k = 0; k < rank; ++k) {
     cf acc = C(0.f);
     for (int mm = 0; mm < N; ++mm) {
-      const float2 k = K[n * N + mm];
-      acc = fma_c(C(k.x, k.y), L[mm], acc);
+      const float2 w = W[k * N + mm];
+      acc = fma_c(C(w.x, w.y), L[mm], acc);
     }
-    s += fmaf(L[n].re, acc.re, L[n].im * acc.im);   // Re(conj(L_n) (K L)_n)
+    s += norm2(acc);
   }
   return s;
 }
@@ -389,7 +393,7 @@ static __device__ __noinline__ TTBBAmp2 ttbb_amp2(const LCv& l, const LCv& d, co
         const CV X2 = cv_scale(C(0.f, -1.f / s2), v3(g, e2, K2, Gt, mP12));
         L[n++] = cvdot(v3(g, e1, K1, Gb, mP34), X2);
       }
-      res.gg += colour_quad<TTBB_NGG>(L, c_ttbb_kgg);
+      res.gg += colour_quad<TTBB_NGG>(L, c_ttbb_ugg, c_ttbb_rank[0]);
     }
     // ---------------- q qbar, the quark along +z (o = 0) or -z (o = 1)
 #pragma unroll 1
@@ -444,7 +448,7 @@ static __device__ __noinline__ TTBBAmp2 ttbb_amp2(const LCv& l, const LCv& d, co
           r = rvtx(r, lo == 0 ? Gb : Gt);
           L[n++] = dot4(r, cq);
         }
-        qsum += colour_quad<TTBB_NQQ>(L, c_ttbb_kqq);
+        qsum += colour_quad<TTBB_NQQ>(L, c_ttbb_uqq, c_ttbb_rank[1]);
       }
       if (o == 0) res.qq12 += qsum;
       else res.qq21 += qsum;
