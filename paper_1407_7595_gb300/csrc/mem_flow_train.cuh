@@ -366,12 +366,16 @@ k_flow_train(const FlowW* __restrict__ W, const FlowB* __restrict__ Bw,
         float d3[8];
         tmem_ld8(tl + FT_COL_DW3, d3);
 #pragma unroll
-        for (int o = 0; o < 8; ++o) atomicAdd(&G->W3[k][row][o], d3[o]);
+        for (int o = 0; o < 8; o += 4)
+          atomicAdd(reinterpret_cast<float4*>(&G->W3[k][row][o]), make_float4(d3[o], d3[o + 1], d3[o + 2], d3[o + 3]));
       }
       float v[64];
       tmem_ld64(tl + FT_COL_DW2 + 64 * half, v);
-#pragma unroll 8
-      for (int i = 0; i < 64; ++i) atomicAdd(&G->W2[k][row][64 * half + i], v[i]);
+      // 16-byte vector atomics: a quarter of the gradient atomics (rows are 512 B aligned)
+#pragma unroll 4
+      for (int i = 0; i < 64; i += 4)
+        atomicAdd(reinterpret_cast<float4*>(&G->W2[k][row][64 * half + i]),
+                  make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]));
       // dL/da1 = dL/dh1 [a1 > 0] for this thread's sample and columns; dL/dz_A partials
       tmem_ld64(tl + FT_COL_GH1 + 64 * half, v);
       float za[4];
