@@ -52,10 +52,10 @@ from paper_1407_7595_gb300 import synth  # noqa: E402
 # operations per double-float sum), and they average over the points that exit
 # before the solver.
 FLOPS_MAIN_PER_EVAL = {synth.PROC_DY: 157.0, synth.PROC_W: 345.7, synth.PROC_TTBAR: 2834.9,
-                       synth.PROC_TTBAR_DILEP: 11390.0, synth.PROC_TTH_DILEP: 19896.0,
+                       synth.PROC_TTBAR_DILEP: 10494.0, synth.PROC_TTH_DILEP: 18805.0,
                        synth.PROC_TTBB_DILEP: 653200.0}
-FLOPS_ADAPT_PER_EVAL = {synth.PROC_TTBAR: 2817.6, synth.PROC_TTBAR_DILEP: 9892.0,
-                        synth.PROC_TTH_DILEP: 17000.0, synth.PROC_TTBB_DILEP: 486600.0}
+FLOPS_ADAPT_PER_EVAL = {synth.PROC_TTBAR: 2817.6, synth.PROC_TTBAR_DILEP: 9119.0,
+                        synth.PROC_TTH_DILEP: 16004.0, synth.PROC_TTBB_DILEP: 486600.0}
 FP32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 FP32 lanes
 # DRAM bytes (read + write) per launch unit from one ncu capture of the current
 # kernels: k_main reads each item's grid and constants once (other CTAs of the item
