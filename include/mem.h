@@ -285,6 +285,17 @@ mem_status mem_discriminant(int64_t n, const double* prob_s, const double* err_s
  * Errors: MEM_ERR_INVALID_ARG (NULL pointers). */
 mem_status mem_ttbb_colour_matrices(float* kgg, float* kqq);
 
+/* The factors the ttbb kernels use for their colour sums: K = sum_k u_k u_k^dagger
+ * for each colour matrix above, by pivoted Cholesky (K is a Gram matrix, so the
+ * colour-summed square L^dagger K L of an amplitude vector L is sum_k |u_k^dagger L|^2
+ * with rank(K) terms). Writes the rows conj(u_k), k < rank, as interleaved (real,
+ * imaginary) float pairs, row major, the rows beyond the rank zero: ugg 38 x 38 x 2 and
+ * uqq 7 x 7 x 2 floats, and ranks[2] (g g, q qbar); host memory, caller-owned. Host
+ * computation; no device needed; no paper counterpart (a cheaper evaluation of the
+ * same colour sums). Errors: MEM_ERR_INVALID_ARG (NULL pointers; or the factors do
+ * not reproduce K to 1e-9 of its largest diagonal element). */
+mem_status mem_ttbb_colour_factors(float* ugg, float* uqq, int32_t* ranks);
+
 /* Working memory of mem_integrate_noalloc, fixed at build time (32 MiB per GPU). */
 #define MEM_NOALLOC_SCRATCH_BYTES (32u << 20)
 

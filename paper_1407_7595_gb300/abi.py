@@ -103,6 +103,7 @@ SIGNATURES = [
                                            C.c_double, C.c_double, C.c_double]),
     ("mem_discriminant", C.c_int, [C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("mem_ttbb_colour_matrices", C.c_int, [_vp, _vp]),
+    ("mem_ttbb_colour_factors", C.c_int, [_vp, _vp, _vp]),
     ("mem_destroy", None, [_vp]),
     ("mem_last_error", C.c_char_p, []),
     ("mem_eval_points", C.c_int, [_vp, _vp, C.POINTER(mem_tf_desc), C.c_int64, C.c_int32,
@@ -255,6 +256,18 @@ def mem_ttbb_colour_matrices():
     kqq = np.zeros(7 * 7 * 2, dtype=np.float32)
     _check(lib().mem_ttbb_colour_matrices(kgg.ctypes.data, kqq.ctypes.data))
     return (kgg.view(np.complex64).reshape(38, 38), kqq.view(np.complex64).reshape(7, 7))
+
+
+def mem_ttbb_colour_factors():
+    """The factor rows conj(u_k) of the ttbb colour matrices, K = sum_k u_k u_k^dagger:
+    ((38, 38) complex64, (7, 7) complex64, (rank_gg, rank_qq)); rows beyond the rank
+    are zero."""
+    ugg = np.zeros(38 * 38 * 2, dtype=np.float32)
+    uqq = np.zeros(7 * 7 * 2, dtype=np.float32)
+    ranks = np.zeros(2, dtype=np.int32)
+    _check(lib().mem_ttbb_colour_factors(ugg.ctypes.data, uqq.ctypes.data, ranks.ctypes.data))
+    return (ugg.view(np.complex64).reshape(38, 38), uqq.view(np.complex64).reshape(7, 7),
+            (int(ranks[0]), int(ranks[1])))
 
 
 def mem_process_set_pdf_grid(proc, grid):

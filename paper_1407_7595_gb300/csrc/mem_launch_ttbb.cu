@@ -320,3 +320,20 @@ extern "C" mem_status mem_ttbb_colour_matrices(float* kgg, float* kqq) {
   }
   return MEM_OK;
 }
+
+extern "C" mem_status mem_ttbb_colour_factors(float* ugg, float* uqq, int32_t* ranks) {
+  if (!ugg || !uqq || !ranks) return MEM_ERR_INVALID_ARG;
+  const mem::ColourFactors a = mem::colour_factors(true), b = mem::colour_factors(false);
+  if (a.rank < 1 || b.rank < 1) return MEM_ERR_INVALID_ARG;
+  for (size_t q = 0; q < a.w.size(); ++q) {
+    ugg[2 * q] = a.w[q].x;
+    ugg[2 * q + 1] = a.w[q].y;
+  }
+  for (size_t q = 0; q < b.w.size(); ++q) {
+    uqq[2 * q] = b.w[q].x;
+    uqq[2 * q + 1] = b.w[q].y;
+  }
+  ranks[0] = a.rank;
+  ranks[1] = b.rank;
+  return MEM_OK;
+}

@@ -63,6 +63,30 @@ def test_host_only_entry_points(libmem):
     abi.mem_destroy(None)
 
 
+def test_ttbb_colour_factors_reproduce_the_oracle_matrices(libmem, ora):
+    """The kernels evaluate the colour sums as sum_k |u_k^dagger L|^2 with the library's
+    factors K = sum_k u_k u_k^dagger: those factors, rebuilt into a matrix, equal the
+    oracle's colour matrices to FP32 rounding (so L^dagger K L is unchanged), and their
+    number is the matrices' rank (the oracle's eigenvalues above 1e-10 of the largest:
+    11 for g g, 4 for q qbar)."""
+    import numpy as np
+    from paper_1407_7595_gb300 import abi
+    ugg, uqq, ranks = abi.mem_ttbb_colour_factors()
+    ogg, oqq = ora.ttbb_colour_matrices()
+    for w, o, r in ((ugg, ogg, ranks[0]), (uqq, oqq, ranks[1])):
+        ev = np.linalg.eigvalsh(o)
+        assert r == int(np.sum(ev > 1e-10 * ev.max()))
+        assert np.all(w[r:] == 0)
+        u = w[:r].astype(np.complex128).conj()          # rows u_k
+        rebuilt = u.T @ u.conj()                        # sum_k u_k u_k^dagger
+        scale = np.max(np.abs(o))
+        assert np.max(np.abs(rebuilt - o)) < 1e-6 * scale
+        rng = np.random.default_rng(3)
+        L = rng.normal(size=o.shape[0]) + 1j * rng.normal(size=o.shape[0])
+        assert np.sum(np.abs(w[:r].astype(np.complex128) @ L) ** 2) == pytest.approx(
+            np.real(L.conj() @ o @ L), rel=1e-5)
+
+
 def test_ttbb_colour_matrices_match_the_oracle(libmem, ora):
     """The colour matrices the GPU kernels use (computed on the host by the library, with
     its own SU(3) code) equal the oracle's, term by term, to FP32 rounding: the term
