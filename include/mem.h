@@ -323,7 +323,7 @@ mem_status mem_ttbb_colour_factors(float* ugg, float* uqq, int32_t* ranks);
  * may not allocate later makes one small call per process kind it will use
  * (e.g. 1 event, 16 points) at start-up, before it reserves its memory pool
  * and before any stream capture; later calls allocate nothing. Kinds 0-3 need
- * at most 1008 bytes of per-thread stack, inside the default 1024-byte limit,
+ * at most 1024 bytes of per-thread stack (callees included), the default limit,
  * so no launch grows the context's local memory; kinds 4 and 5 are rejected.
  * All calls share the array: calls that overlap on the GPU (other streams,
  * other host threads) race on it and must be serialised by the caller.

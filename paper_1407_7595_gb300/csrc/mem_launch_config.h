@@ -16,7 +16,7 @@ constexpr int PPT_DL = 16;       // frozen-grid points per thread (dilepton ttba
 constexpr int MINB_DL = 4;       // adaptation kernel: 4 CTAs of 256 threads per SM (<= 64 registers)
 constexpr int MINB_DL_MAIN = 5;  // frozen-grid kernel: 5 CTAs per SM (<= 48 registers): the double-float
                                  // solver is latency-bound and occupancy pays for the spills (measured
-                                 // against 1/2, 2/2-4, 3/4); the stack stays <= 1008 bytes, inside the
+                                 // against 1/2, 2/2-4, 3/4); the stack stays <= 1024 bytes, within the
                                  // default per-thread limit (5/6 would exceed it)
 constexpr int MINB_TH = 3;       // dilepton ttH adaptation kernel: 3 CTAs per SM
 constexpr int MINB_TH_MAIN = 4;  // dilepton ttH frozen-grid kernel: 4 CTAs per SM (measured against

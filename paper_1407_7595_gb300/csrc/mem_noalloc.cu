@@ -18,7 +18,7 @@
 // per process kind it uses at start-up, before it reserves its memory pool
 // and before any stream capture; later calls allocate nothing.
 //
-// Stack: the kernels of kinds 0-3 need at most 1008 bytes of per-thread stack
+// Stack: the kernels of kinds 0-3 need at most 1024 bytes of per-thread stack
 // (ptxas), within the context's default 1024-byte limit, so no launch grows
 // the context's local memory; the dilepton ttH and ttbb kernels need more and
 // are rejected.
