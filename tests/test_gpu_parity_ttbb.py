@@ -21,7 +21,7 @@ bounds.
 import numpy as np
 import pytest
 
-from test_gpu_parity import check_conditioned, check_frozen_integral
+from parity_rules import check_conditioned, check_frozen_integral
 from test_gpu_parity_tth import TH_RULE, check_nonzero_points
 
 pytestmark = pytest.mark.gpu

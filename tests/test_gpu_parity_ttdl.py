@@ -18,7 +18,7 @@ Next to a branch point, where two solutions merge and the Jacobian peaks, the
 weight is ill-conditioned and one point can carry a fifth of a batch; there the
 oracle measures the conditioning itself (s_i, the summed relative change of its
 weight under 2^-24 moves of the point's unit-cube coordinates, see
-test_gpu_parity.check_conditioned) and a point may differ by up to 100 s_i (the
+parity_rules.check_conditioned) and a point may differ by up to 100 s_i (the
 FP32 rounding of a Breit-Wigner output is worth a move of u up to m / (pi Gamma)
 ~ 40 times larger), capped at 5e-2 (a missed or spurious solution is an O(1) change); on the GPU
 such points differ by 0.1-1.5 s_i.
@@ -31,7 +31,7 @@ to 1e-7 and agrees within 1e-5 plus the bounds of its ill-conditioned points
 import numpy as np
 import pytest
 
-from test_gpu_parity import check_conditioned, check_frozen_integral
+from parity_rules import check_conditioned, check_frozen_integral
 
 pytestmark = pytest.mark.gpu
 KIND = 3

@@ -9,7 +9,7 @@ the uniform-grid points of the assignments below reach the kinematic region (bot
 neutrinos real; the Higgs-pair map lands inside both jet windows by construction).
 
 Tolerance: as for dilepton ttbar (FP32 virtualities and jet energies feeding the
-FP64 neutrino solution, double-Gaussian TFs; test_gpu_parity.check_conditioned),
+FP64 neutrino solution, double-Gaussian TFs; parity_rules.check_conditioned),
 with two more jets and the Higgs pair's energies from (m_H^2, f) in FP32 and the
 longer FP32 spinor chains: >= 95 % of the points within 1e-4 (98-99.5 % on the GPU),
 every point within max(1e-4, 100 s_i) capped at 5e-2 (s_i the oracle's own
@@ -23,7 +23,7 @@ frozen-grid integral equals the ratio of its point sums to 1e-7 and agrees withi
 import numpy as np
 import pytest
 
-from test_gpu_parity import check_conditioned, check_frozen_integral
+from parity_rules import check_conditioned, check_frozen_integral
 
 pytestmark = pytest.mark.gpu
 KIND = 4
